@@ -1,0 +1,61 @@
+"""Pins of the oracle's integrator (eqs. 27-30, 35) and constant of motion (eq. 26)."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import hamiltonian as ham, dynamics as dyn
+
+TAB = synth.synthetic_table(1)
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_damping_coefficients_cancel_on_linear_trajectories():
+    """sum c_k = 0 and sum k c_k = 0: the damping term of eq. 29 vanishes for X(t) linear in t."""
+    k = np.arange(dyn.KMAX + 1)
+    assert dyn.CK.sum() == 0.0
+    assert (k * dyn.CK).sum() == 0.0
+    assert len(dyn.CK) == dyn.KMAX + 1 == 7
+
+
+def test_damped_recursion_is_stable_for_minus_identity_kernel():
+    """With K = -I, e(t+dt) = (2 - kappa) e(t) - e(t-dt) + alpha sum c_k e(t-k dt) is a contraction."""
+    a, c = dyn.ALPHA, dyn.CK
+    coef = np.zeros(dyn.KMAX + 2)
+    coef[0] = 1.0
+    coef[1] = -(2.0 - dyn.KAPPA) - a * c[0]
+    coef[2] = 1.0 - a * c[1]
+    for j in range(2, dyn.KMAX + 1):
+        coef[j + 1] = -a * c[j]
+    roots = np.roots(coef)
+    assert np.abs(roots).max() < 0.96
+    # without damping the recursion is only marginally stable
+    assert np.abs(np.roots([1.0, -(2.0 - dyn.KAPPA), 1.0])).max() == pytest.approx(1.0, abs=1e-12)
+
+
+@pytest.mark.slow
+def test_energy_conservation_and_dt_squared_scaling():
+    """E_tot (eq. 26) fluctuates ~dt^2 and does not drift (Results, Gramicidin S NVE)."""
+    mol = synth.c4h6(1)
+    R0 = np.loadtxt(os.path.join(GOLDEN, "c4h6_seed1_relaxed.txt"))
+    V0 = synth.maxwell_boltzmann(mol.Z, 300.0, seed=1)
+    sysm = ham.System(mol.Z, TAB)
+    stds, drifts = [], []
+    for dt in (0.5, 0.25):
+        cfg = dyn.Config(Te=1000.0, dt=dt, m=4)
+        st = dyn.State(sysm, R0, V0, cfg)
+        E = [st.total_energy()]
+        for _ in range(int(60 / dt)):
+            st.step()
+            E.append(st.total_energy())
+            X = st.X[0]
+            assert np.array_equal(X, X.T)
+        E = np.array(E)
+        stds.append(E.std())
+        drifts.append(dyn.energy_drift(np.arange(len(E)) * dt, E, sysm.N))
+    assert 3.0 < stds[0] / stds[1] < 5.5
+    # no systematic drift beyond the fluctuation over the 60 fs window
+    for s, d in zip(stds, drifts):
+        assert abs(d) * sysm.N * 0.060 < s
+    assert stds[0] < 2e-3
