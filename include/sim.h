@@ -1,0 +1,202 @@
+/*
+ * sim.h -- C ABI of the GB300 KSA-XL-BOMD library.
+ *
+ * The library advances semi-empirical (NDDO, sp basis) shadow extended-
+ * Lagrangian Born-Oppenheimer molecular dynamics with the Krylov subspace
+ * approximation of the kernel (arXiv 2303.00689, "Semi-Empirical Shadow
+ * Molecular Dynamics: A PyTorch implementation").  One call of sim_step
+ * performs, per MD step and entirely in CUDA kernels on one GPU:
+ *   - the modified leap-frog velocity Verlet update with damping
+ *     (eqs. 27-30, 35);
+ *   - NDDO pair integrals and their derivatives, h and F(X) = h + G(X)
+ *     (eqs. 3, 6, 17);
+ *   - the eigendecomposition, Fermi occupations and chemical potential,
+ *     D0[X] (eqs. 7, 8, 19);
+ *   - the shadow energy (eq. 13) and forces (eqs. 22, 37-41);
+ *   - the rank-m Krylov approximation of K(D0[X] - X) (eqs. 31-34) with
+ *     canonical density-matrix perturbation theory responses (eq. 36).
+ *
+ * Conventions.  Units: Angstrom, fs, eV, amu, K.  Closed shell, S = I
+ * (NDDO), so X = P (the paper's statement under eq. 16).  Densities D, X,
+ * P are PER SPIN: Tr D = N_occ = N_electrons / 2.  Matrices are dense,
+ * row-major, n x n doubles, orbitals ordered atom by atom (s, px, py, pz for
+ * C/N/O; s for H).  Positions/velocities/forces are natoms x 3 row-major.
+ *
+ * Memory: every pointer argument is HOST memory unless its comment says
+ * DEVICE.  The library copies inputs in and owns all device state of a
+ * handle; results are copied into caller-owned buffers.  A handle is not
+ * thread safe; different handles may be used from different threads.
+ *
+ * Errors: every int-returning call returns a SIM_* status.  On error the
+ * handle's state is unchanged unless stated otherwise, and
+ * sim_last_error() returns a message for the calling thread.
+ */
+#ifndef KSA_XLBOMD_SIM_H
+#define KSA_XLBOMD_SIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum sim_status {
+  SIM_OK = 0,
+  SIM_PENDING = 1,    /* sim_poll: request not finished yet                   */
+  SIM_EINVAL = 2,     /* bad argument (open shell, unknown Z, NaN, sizes)      */
+  SIM_ENOMEM = 3,     /* device allocation failed or HBM budget exceeded      */
+  SIM_ENOCONV = 4,    /* SCF or chemical-potential solve did not converge     */
+  SIM_ENUMERIC = 5,   /* NaN/Inf detected on the device                       */
+  SIM_ETIMEOUT = 6,   /* a bounded device-side wait gave up                   */
+  SIM_EINTERNAL = 7,  /* CUDA error or library bug                            */
+};
+
+/* ---- precision modes ---------------------------------------------------- */
+enum sim_precision {
+  /* every step in FP64 (FP64 SIMT GEMMs for density and DMPT)               */
+  SIM_PREC_FP64 = 0,
+  /* FP64 eigensolve, mu and Krylov Gram/solve; density D0 = Q f Q^T and the
+   * DMPT contractions of eq. 36 on tcgen05 tensor cores with FP32
+   * accumulation, operands split into BF16 pieces (3 pieces for the
+   * density, 2 for DMPT) so that the products keep ~16-24 bits            */
+  SIM_PREC_MIXED = 1,
+};
+
+/* ---- parameter table ---------------------------------------------------- */
+/* One record per element, rows in the order H, C, N, O.  Field order: */
+enum sim_param_field {
+  SIM_P_Z = 0, SIM_P_NORB, SIM_P_NPRIN, SIM_P_ZCORE, SIM_P_MASS,
+  SIM_P_USS, SIM_P_UPP, SIM_P_ZETA_S, SIM_P_ZETA_P, SIM_P_BETA_S, SIM_P_BETA_P,
+  SIM_P_GSS, SIM_P_GSP, SIM_P_GPP, SIM_P_GP2, SIM_P_HSP, SIM_P_ALPHA,
+  SIM_P_GA0, SIM_P_GB0, SIM_P_GC0, SIM_P_GA1, SIM_P_GB1, SIM_P_GC1,
+  SIM_NFIELDS
+};
+/* Raw MNDO/AM1-form parameters (the paper cites these Hamiltonians in its
+ * Introduction; values are supplied by the caller).  Units: eV for U, beta,
+ * G, H; 1/bohr for zeta; 1/Angstrom for alpha; AM1 Gaussians a (eV*A),
+ * b (1/A^2), c (A); mass in amu.  The library derives the multipole lengths
+ * D1, D2 and additive terms rho0..rho2 itself. */
+typedef struct sim_param_table {
+  double v[4][SIM_NFIELDS];
+} sim_param_table;
+
+/* ---- configuration ------------------------------------------------------ */
+typedef struct sim_config {
+  double Te;          /* electronic temperature, K (eq. 7); > 0                */
+  double dt;          /* time step, fs (eqs. 27-30)                            */
+  int m_max;          /* maximum Krylov rank m (eq. 34), 1..16                 */
+  int m_min;          /* minimum rank before the adaptive stop (<= m_max)      */
+  double krylov_tol;  /* adaptive stop: relative fit error < tol (0 = fixed m) */
+  int precision;      /* enum sim_precision                                    */
+  double scf_tol;     /* sim_create SCF: stop when max|D[P] - P| < scf_tol     */
+  int scf_max;        /* sim_create SCF: maximum iterations                    */
+  double scf_mix;     /* linear mixing P <- mix P + (1 - mix) D[P] (paper: 0.1) */
+  int device;         /* CUDA device ordinal                                   */
+  void* stream;       /* cudaStream_t to launch on, or NULL for a private one  */
+} sim_config;
+
+/* Fills a config with the defaults used by the paper-shaped workloads:
+ * Te 1000 K, dt 0.5 fs, m = 4, fixed rank, FP64, scf_tol 1e-10,
+ * scf_max 5000, mix 0.1, device 0, private stream. */
+void sim_config_default(sim_config* cfg);
+
+/* ---- per-step diagnostics ------------------------------------------------ */
+typedef struct sim_step_result {
+  double E_kin;     /* sum M Rdot^2 / 2, eV                                    */
+  double U;         /* shadow potential energy, eq. 13 (with -2 T_e S), eV     */
+  double E_tot;     /* constant of motion, eq. 26, eV                          */
+  double mu;        /* chemical potential, eV (eq. 8)                          */
+  double gap;       /* eps_LUMO - eps_HOMO (0 when n == N_occ), eV             */
+  double res_norm;  /* ||D0[X] - X||_F                                         */
+  double fit_err;   /* relative Krylov fit error of the last rank used         */
+  int rank;         /* Krylov rank used                                        */
+  int pad;
+} sim_step_result;
+
+typedef struct sim_handle sim_handle;
+
+/* sim_create -- one molecule, initial state at t0.
+ * Follows Methods section 5: X(t0 - k dt) = D_min for k = 0..6.  D_min is
+ * P0 when P0 != NULL (caller-supplied per-spin density, n x n, symmetric,
+ * trace N_occ), otherwise it comes from an SCF by linear mixing from the
+ * diagonal guess (Results, "SCF Optimization").  Then the shadow energy,
+ * forces and the first Krylov kernel are evaluated at (R0, X(t0)).
+ *   natoms  number of atoms (>= 1)
+ *   Z       atomic numbers (1, 6, 7, 8), natoms ints
+ *   R       positions, Angstrom, natoms x 3
+ *   V       velocities, Angstrom/fs, natoms x 3, or NULL for zero
+ *   charge  net charge; (valence electrons - charge) must be even
+ *   P0      n x n per-spin density or NULL (SCF)
+ *   out     receives the handle
+ * Errors: SIM_EINVAL (bad Z, odd electron count, NaN, bad config),
+ *         SIM_ENOMEM, SIM_ENOCONV (SCF), SIM_ETIMEOUT, SIM_EINTERNAL. */
+int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms,
+               const int* Z, const double* R, const double* V, int charge,
+               const double* P0, sim_handle** out);
+
+/* Number of basis functions n and occupied orbitals N_occ of a handle. */
+int sim_norb(const sim_handle* h);
+int sim_nocc(const sim_handle* h);
+
+/* sim_step -- advance nsteps MD steps (eqs. 27-30 with X from eq. 35).
+ * out: NULL or nsteps records (caller-owned) filled with the diagnostics of
+ * each step.  Synchronous: returns after the last step finished. */
+int sim_step(sim_handle* h, int nsteps, sim_step_result* out);
+
+/* sim_step_async -- enqueue nsteps steps on the handle's stream without
+ * waiting; diagnostics of the last step can be read with sim_last_result
+ * after the stream is synchronised.  No host synchronisation inside. */
+int sim_step_async(sim_handle* h, int nsteps);
+int sim_last_result(sim_handle* h, sim_step_result* out);
+
+/* sim_get_state -- copy the current state out (any pointer may be NULL).
+ *   R, V, F: natoms x 3 (F = forces, eV/Angstrom, eq. 37 with the eq. 9 sign)
+ *   D0:      n x n per-spin D0[X(t)] of the last evaluation (eq. 19) */
+int sim_get_state(sim_handle* h, double* R, double* V, double* F, double* D0);
+
+/* sim_set_state -- overwrite R, V and/or the X history and re-evaluate at
+ * (R, X(t)) (any pointer may be NULL to keep the current value).
+ *   Xhist: 7 x n x n, Xhist[k] = X(t - k dt), k = 0..6 (eq. 29 history) */
+int sim_set_state(sim_handle* h, const double* R, const double* V, const double* Xhist);
+
+/* Matrices of the last evaluation, copied into an n x n caller buffer. */
+enum sim_matrix {
+  SIM_MAT_X = 0,       /* X(t)                                              */
+  SIM_MAT_D0 = 1,      /* D0[X(t)] (eq. 19)                                 */
+  SIM_MAT_FOCK = 2,    /* F(X(t)) = h + G(X(t)) (eq. 17)                    */
+  SIM_MAT_H = 3,       /* core Hamiltonian h                                */
+  SIM_MAT_KERNEL = 4,  /* sum_i V_i c_i ~ K (D0 - X) (eq. 34)               */
+  SIM_MAT_Q = 5,       /* eigenvectors of F as columns                      */
+};
+int sim_get_matrix(sim_handle* h, int which, double* out);
+
+/* Vectors of the last evaluation (n doubles): 0 = eigenvalues (ascending),
+ * 1 = occupations f_i. */
+int sim_get_vector(sim_handle* h, int which, double* out);
+
+/* Device-side per-phase timing (CUDA events on the handle's stream).
+ * enable != 0 starts recording; sim_phase_times returns, for each phase
+ * id < nphase, the accumulated milliseconds, launch count and the bytes or
+ * flops one launch moves/does (algorithmic, see the design notes). */
+int sim_profile_enable(sim_handle* h, int enable);
+int sim_phase_count(void);
+const char* sim_phase_name(int phase);
+int sim_phase_times(sim_handle* h, double* ms, long long* launches, double* work_per_launch);
+
+/* Number of CUDA kernel launches the library has issued (all handles). */
+long long sim_launch_count(void);
+
+/* Stream (cudaStream_t) the handle launches on. */
+void* sim_stream(sim_handle* h);
+
+void sim_destroy(sim_handle* h);
+
+/* Thread-local message of the last error (never NULL). */
+const char* sim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KSA_XLBOMD_SIM_H */

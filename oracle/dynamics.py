@@ -82,7 +82,7 @@ def evaluate(sysm, R, X, cfg, krylov=True):
     U = ham.electronic_energy_terms(h, G, D, X) - 2.0 * cfg.Te * S + Vnn
     forces = ham.forces(sysm, R, D, X, pairs)
     out = dict(F=F, h=h, G=G, D=D, eps=eps, Q=Q, f=f, mu=mu, S=S, U=U, Vnn=Vnn,
-               forces=forces)
+               forces=forces, Te=cfg.Te)
     if krylov:
         Lam = el.divided_differences(eps, f, mu, cfg.beta)
 

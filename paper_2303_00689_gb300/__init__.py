@@ -1,0 +1,239 @@
+"""Python binding of the GB300 KSA-XL-BOMD CUDA library (``libksaxl.so``).
+
+Thin ctypes marshalling over the C ABI declared in ``include/sim.h``: every
+function here has the C name, converts numpy arrays to pointers and raises
+``SimError`` on a non-zero status.  All computation happens in the CUDA
+library; importing this module without the built library raises at the first
+call (there is no CPU fallback).
+
+Build the library with ``python -m paper_2303_00689_gb300.build`` (needs nvcc).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libksaxl.so")
+
+SIM_OK, SIM_PENDING, SIM_EINVAL, SIM_ENOMEM, SIM_ENOCONV, SIM_ENUMERIC, SIM_ETIMEOUT, SIM_EINTERNAL = range(8)
+SIM_PREC_FP64, SIM_PREC_MIXED = 0, 1
+SIM_MAT_X, SIM_MAT_D0, SIM_MAT_FOCK, SIM_MAT_H, SIM_MAT_KERNEL, SIM_MAT_Q = range(6)
+SIM_NFIELDS = 23
+
+EXPORTED = (
+    "sim_config_default", "sim_create", "sim_norb", "sim_nocc", "sim_step", "sim_step_async",
+    "sim_last_result", "sim_get_state", "sim_set_state", "sim_get_matrix", "sim_get_vector",
+    "sim_profile_enable", "sim_phase_count", "sim_phase_name", "sim_phase_times",
+    "sim_launch_count", "sim_stream", "sim_destroy", "sim_last_error",
+)
+
+
+class SimError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"status {code}: {msg}")
+        self.code = code
+
+
+class sim_config(C.Structure):
+    _fields_ = [("Te", C.c_double), ("dt", C.c_double), ("m_max", C.c_int), ("m_min", C.c_int),
+                ("krylov_tol", C.c_double), ("precision", C.c_int), ("scf_tol", C.c_double),
+                ("scf_max", C.c_int), ("scf_mix", C.c_double), ("device", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+class sim_param_table(C.Structure):
+    _fields_ = [("v", (C.c_double * SIM_NFIELDS) * 4)]
+
+
+class sim_step_result(C.Structure):
+    _fields_ = [("E_kin", C.c_double), ("U", C.c_double), ("E_tot", C.c_double), ("mu", C.c_double),
+                ("gap", C.c_double), ("res_norm", C.c_double), ("fit_err", C.c_double),
+                ("rank", C.c_int), ("pad", C.c_int)]
+
+
+_lib_handle = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run python -m paper_2303_00689_gb300.build)")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER
+        dp = P(C.c_double)
+        L.sim_config_default.argtypes = [P(sim_config)]
+        L.sim_config_default.restype = None
+        L.sim_create.argtypes = [P(sim_config), P(sim_param_table), C.c_int, P(C.c_int), dp, dp, C.c_int,
+                                 dp, P(C.c_void_p)]
+        L.sim_norb.argtypes = [C.c_void_p]
+        L.sim_nocc.argtypes = [C.c_void_p]
+        L.sim_step.argtypes = [C.c_void_p, C.c_int, P(sim_step_result)]
+        L.sim_step_async.argtypes = [C.c_void_p, C.c_int]
+        L.sim_last_result.argtypes = [C.c_void_p, P(sim_step_result)]
+        L.sim_get_state.argtypes = [C.c_void_p, dp, dp, dp, dp]
+        L.sim_set_state.argtypes = [C.c_void_p, dp, dp, dp]
+        L.sim_get_matrix.argtypes = [C.c_void_p, C.c_int, dp]
+        L.sim_get_vector.argtypes = [C.c_void_p, C.c_int, dp]
+        L.sim_profile_enable.argtypes = [C.c_void_p, C.c_int]
+        L.sim_phase_count.argtypes = []
+        L.sim_phase_name.argtypes = [C.c_int]
+        L.sim_phase_name.restype = C.c_char_p
+        L.sim_phase_times.argtypes = [C.c_void_p, dp, P(C.c_longlong), dp]
+        L.sim_launch_count.argtypes = []
+        L.sim_launch_count.restype = C.c_longlong
+        L.sim_stream.argtypes = [C.c_void_p]
+        L.sim_stream.restype = C.c_void_p
+        L.sim_destroy.argtypes = [C.c_void_p]
+        L.sim_destroy.restype = None
+        L.sim_last_error.argtypes = []
+        L.sim_last_error.restype = C.c_char_p
+        _lib_handle = L
+    return _lib_handle
+
+
+def _check(rc):
+    if rc != SIM_OK:
+        raise SimError(rc, lib().sim_last_error().decode())
+    return rc
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def sim_config_default(**overrides):
+    cfg = sim_config()
+    lib().sim_config_default(C.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def param_table(array):
+    """(4, SIM_NFIELDS) float64 rows H, C, N, O -> sim_param_table."""
+    arr = np.asarray(array, dtype=np.float64)
+    if arr.shape != (4, SIM_NFIELDS):
+        raise ValueError(f"parameter table must be (4, {SIM_NFIELDS})")
+    t = sim_param_table()
+    for i in range(4):
+        for j in range(SIM_NFIELDS):
+            t.v[i][j] = float(arr[i, j])
+    return t
+
+
+def sim_create(cfg, table, Z, R, V=None, charge=0, P0=None):
+    Z = np.ascontiguousarray(Z, dtype=np.int32)
+    N = len(Z)
+    R = _f64(R, (N, 3))
+    V = _f64(V, (N, 3))
+    P0 = _f64(P0)
+    h = C.c_void_p()
+    _check(lib().sim_create(C.byref(cfg), C.byref(table), N, Z.ctypes.data_as(C.POINTER(C.c_int)),
+                            _dptr(R), _dptr(V), int(charge), _dptr(P0), C.byref(h)))
+    return h
+
+
+def sim_norb(h):
+    return lib().sim_norb(h)
+
+
+def sim_nocc(h):
+    return lib().sim_nocc(h)
+
+
+def sim_step(h, nsteps, records=True):
+    out = (sim_step_result * max(1, nsteps))() if records else None
+    _check(lib().sim_step(h, int(nsteps), out))
+    if not records:
+        return None
+    return [{f: getattr(r, f) for f, _ in sim_step_result._fields_} for r in out[:nsteps]]
+
+
+def sim_step_async(h, nsteps):
+    _check(lib().sim_step_async(h, int(nsteps)))
+
+
+def sim_last_result(h):
+    r = sim_step_result()
+    _check(lib().sim_last_result(h, C.byref(r)))
+    return {f: getattr(r, f) for f, _ in sim_step_result._fields_}
+
+
+def sim_get_state(h, natoms):
+    R = np.empty((natoms, 3))
+    V = np.empty((natoms, 3))
+    F = np.empty((natoms, 3))
+    n = sim_norb(h)
+    D = np.empty((n, n))
+    _check(lib().sim_get_state(h, _dptr(R), _dptr(V), _dptr(F), _dptr(D)))
+    return R, V, F, D
+
+
+def sim_set_state(h, R=None, V=None, Xhist=None):
+    R, V, Xhist = _f64(R), _f64(V), _f64(Xhist)
+    _check(lib().sim_set_state(h, _dptr(R), _dptr(V), _dptr(Xhist)))
+
+
+def sim_get_matrix(h, which):
+    n = sim_norb(h)
+    out = np.empty((n, n))
+    _check(lib().sim_get_matrix(h, int(which), _dptr(out)))
+    return out
+
+
+def sim_get_vector(h, which):
+    out = np.empty(sim_norb(h))
+    _check(lib().sim_get_vector(h, int(which), _dptr(out)))
+    return out
+
+
+def sim_profile_enable(h, enable=True):
+    _check(lib().sim_profile_enable(h, 1 if enable else 0))
+
+
+def sim_phase_names():
+    L = lib()
+    return [L.sim_phase_name(i).decode() for i in range(L.sim_phase_count())]
+
+
+def sim_phase_times(h):
+    L = lib()
+    k = L.sim_phase_count()
+    ms = (C.c_double * k)()
+    cnt = (C.c_longlong * k)()
+    work = (C.c_double * k)()
+    _check(L.sim_phase_times(h, ms, cnt, work))
+    names = sim_phase_names()
+    return {names[i]: dict(ms=ms[i], launches=cnt[i], work=work[i]) for i in range(k)}
+
+
+def sim_launch_count():
+    return lib().sim_launch_count()
+
+
+def sim_stream(h):
+    return lib().sim_stream(h)
+
+
+def sim_destroy(h):
+    if h:
+        lib().sim_destroy(h)
+
+
+def sim_last_error():
+    return lib().sim_last_error().decode()

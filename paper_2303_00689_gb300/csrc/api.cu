@@ -1,0 +1,752 @@
+// C ABI of the library: handle set-up, the per-step orchestration of the
+// kernels, state access and device-side phase timing.  See include/sim.h.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sim.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_gemm.h"
+
+namespace kx {
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+cudaError_t last_launch_error() { return cudaGetLastError(); }
+}  // namespace kx
+
+using namespace kx;
+
+static thread_local std::string t_err = "";
+static int fail(int code, const std::string& msg) {
+  t_err = msg;
+  return code;
+}
+#define CUDA_TRY(x)                                                                  \
+  do {                                                                               \
+    cudaError_t _e = (x);                                                            \
+    if (_e != cudaSuccess)                                                           \
+      return fail(SIM_EINTERNAL, std::string(#x) + ": " + cudaGetErrorString(_e));   \
+  } while (0)
+
+// damping constants of the modified Verlet scheme, k_max = 6 (eq. 29; the
+// paper takes kappa, alpha, c_k from its ref. 24)
+static const double kKappa = 1.84;
+static const double kAlphaDamp = 0.0055;
+
+// ---------------------------------------------------------------------------
+// phases timed with CUDA events
+// ---------------------------------------------------------------------------
+enum Phase {
+  PH_PAIRS = 0, PH_FOCK, PH_TRIDIAG, PH_TRIEIG, PH_BACKTR, PH_DENSITY, PH_FORCES,
+  PH_KRY_FOCK, PH_KRY_GEMM, PH_KRY_BLAS, PH_UPDATE, PH_COUNT
+};
+static const char* kPhaseNames[PH_COUNT] = {
+    "pair_integrals", "fock_build", "eig_tridiag", "eig_tridiag_solve", "eig_backtransform",
+    "density_gemm", "energy_forces", "krylov_fock", "krylov_dmpt_gemm", "krylov_blas", "integrate"};
+
+struct sim_handle {
+  int dev = 0, sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  sim_config cfg;
+  ElemTable tab;
+  int N = 0, n = 0, npair = 0, nocc = 0, mmax = 0;
+  double beta = 0.0;
+  std::vector<int> elem_h, off_h;
+  std::vector<double> mass_h;
+  // device memory (one arena)
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  int *elem = nullptr, *off = nullptr, *pA = nullptr, *pB = nullptr;
+  double *R = nullptr, *V = nullptr, *F = nullptr, *mass = nullptr, *g = nullptr;
+  double *W = nullptr, *S = nullptr, *E = nullptr, *dW = nullptr, *dS = nullptr, *dE = nullptr;
+  double *h = nullptr, *Fock = nullptr, *D = nullptr, *K = nullptr, *Q = nullptr, *Qs = nullptr;
+  double *eps = nullptr, *f = nullptr, *Dd = nullptr, *Pd = nullptr, *Vd = nullptr;
+  double *T1 = nullptr, *T2 = nullptr, *F1 = nullptr, *Y = nullptr, *D1 = nullptr, *W0 = nullptr;
+  double* X[8] = {};
+  double* Vk[16] = {};
+  double* Wk[16] = {};
+  double *red = nullptr, *coef = nullptr;
+  Scalars* sc = nullptr;
+  sim_step_result* rec = nullptr;   // device per-step records (ring of kRecCap)
+  EigWork ew;
+  TcWork tw;
+  int xhead = 0;
+  int last_rec = 0;   // index in rec[] of the most recent record
+  // host mirror of the last results
+  Scalars sc_h;
+  // profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double ph_ms[PH_COUNT] = {};
+  long long ph_n[PH_COUNT] = {};
+  int cur_phase = -1;
+  cudaEvent_t cur_start = nullptr;
+};
+static const int kRecCap = 4096;
+
+// ---------------------------------------------------------------------------
+// parameter derivation (multipole lengths and additive terms)
+// ---------------------------------------------------------------------------
+static double bisect_root(double (*fn)(double, double), double D, double target) {
+  double lo = 1e-8, hi = 1e3;
+  for (int it = 0; it < 300; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (fn(mid, D) > target) lo = mid; else hi = mid;   // fn decreases in rho
+  }
+  return 0.5 * (lo + hi);
+}
+static double dipole_limit(double r, double D1) { return 0.25 * kE2 * (1.0 / r - 1.0 / std::sqrt(D1 * D1 + r * r)); }
+static double quad_limit(double r, double D2) {
+  return 0.125 * kE2 * (1.0 / r - 2.0 / std::sqrt(D2 * D2 + r * r) + 1.0 / std::sqrt(2.0 * D2 * D2 + r * r));
+}
+
+static int build_elem(const double* v, Elem& e) {
+  e.norb = (int)std::lround(v[SIM_P_NORB]);
+  e.nprin = (int)std::lround(v[SIM_P_NPRIN]);
+  if (!((e.norb == 1 && e.nprin == 1) || (e.norb == 4 && e.nprin == 2))) return -1;
+  e.zcore = v[SIM_P_ZCORE];
+  e.mass = v[SIM_P_MASS];
+  e.U[0] = v[SIM_P_USS]; e.U[1] = v[SIM_P_UPP];
+  e.beta[0] = v[SIM_P_BETA_S]; e.beta[1] = v[SIM_P_BETA_P];
+  e.zeta[0] = v[SIM_P_ZETA_S]; e.zeta[1] = v[SIM_P_ZETA_P];
+  e.alpha = v[SIM_P_ALPHA];
+  e.ga[0] = v[SIM_P_GA0]; e.gb[0] = v[SIM_P_GB0]; e.gc[0] = v[SIM_P_GC0];
+  e.ga[1] = v[SIM_P_GA1]; e.gb[1] = v[SIM_P_GB1]; e.gc[1] = v[SIM_P_GC1];
+  e.G_ss = v[SIM_P_GSS]; e.G_sp = v[SIM_P_GSP]; e.G_pp = v[SIM_P_GPP]; e.G_p2 = v[SIM_P_GP2];
+  e.H_sp = v[SIM_P_HSP];
+  e.H_pp = 0.5 * (e.G_pp - e.G_p2);
+  const double kHuge = 1e30;  // vanishing two-electron parameters -> integrals -> 0
+  e.rho0 = (e.G_ss > 0.0) ? kE2 / (2.0 * e.G_ss) : kHuge;
+  if (e.norb == 1) {
+    e.D1 = e.D2 = 0.0;
+    e.rho1 = e.rho2 = e.rho0;
+    return 0;
+  }
+  int n = e.nprin;
+  double zs = e.zeta[0], zp = e.zeta[1];
+  e.D1 = (2 * n + 1) * std::pow(4.0 * zs * zp, n + 0.5) / (std::pow(zs + zp, 2 * n + 2) * std::sqrt(3.0)) * kBohr;
+  e.D2 = std::sqrt((4.0 * n * n + 6.0 * n + 2.0) / 20.0) / zp * kBohr;
+  e.rho1 = (e.H_sp > 0.0) ? bisect_root(dipole_limit, e.D1, e.H_sp) : kHuge;
+  e.rho2 = (e.H_pp > 0.0) ? bisect_root(quad_limit, e.D2, e.H_pp) : kHuge;
+  return 0;
+}
+
+static int elem_index(int Z) {
+  switch (Z) {
+    case 1: return 0;
+    case 6: return 1;
+    case 7: return 2;
+    case 8: return 3;
+    default: return -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// profiling helpers
+// ---------------------------------------------------------------------------
+static cudaEvent_t take_event(sim_handle* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+static void phase_begin(sim_handle* h, int ph) {
+  if (!h->prof) return;
+  h->cur_phase = ph;
+  h->cur_start = take_event(h);
+  cudaEventRecord(h->cur_start, h->stream);
+}
+static void phase_end(sim_handle* h) {
+  if (!h->prof || h->cur_phase < 0) return;
+  cudaEvent_t e = take_event(h);
+  cudaEventRecord(e, h->stream);
+  h->ev_pending.push_back({h->cur_phase, {h->cur_start, e}});
+  h->cur_phase = -1;
+}
+static void collect_events(sim_handle* h) {
+  for (auto& p : h->ev_pending) {
+    cudaEventSynchronize(p.second.second);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+    h->ph_ms[p.first] += ms;
+    h->ph_n[p.first] += 1;
+    h->ev_pool.push_back(p.second.first);
+    h->ev_pool.push_back(p.second.second);
+  }
+  h->ev_pending.clear();
+}
+
+// ---------------------------------------------------------------------------
+// device orchestration
+// ---------------------------------------------------------------------------
+static MolDev mol(const sim_handle* h) { return MolDev{h->N, h->n, h->npair, h->elem, h->off, h->pA, h->pB}; }
+static PairDev pairs(const sim_handle* h) { return PairDev{h->W, h->S, h->E, h->dW, h->dS, h->dE}; }
+static double* xslot(sim_handle* h, int k) { return h->X[(h->xhead + k) % 8]; }
+
+// D0 = Q diag(f) Q^T, exactly symmetric
+static void density(sim_handle* h) {
+  cudaStream_t s = h->stream;
+  int n = h->n;
+  launch_scale_columns(s, n, h->Q, h->f, h->Qs);
+  if (h->cfg.precision == SIM_PREC_MIXED && tc_available()) {
+    tc_syrk_split(s, n, h->Qs, h->D, h->tw, 3);
+  } else {
+    dgemm(s, 0, 1, n, n, n, 1.0, h->Qs, n, h->Qs, n, 0.0, h->D, n, 1);
+  }
+}
+
+// D1 = Q [Lambda o (Q^T F1 Q - dmu I)] Q^T (eq. 36)
+static void dmpt(sim_handle* h, const double* F1, double* D1) {
+  cudaStream_t s = h->stream;
+  int n = h->n;
+  if (h->cfg.precision == SIM_PREC_MIXED && tc_available()) {
+    tc_similarity(s, n, h->Q, F1, h->T2, h->tw, /*transpose_first=*/1);    // T2 = Q^T F1 Q
+    launch_dmu(s, n, h->T2, h->eps, h->f, h->beta, h->sc);
+    launch_dmpt_y(s, n, h->T2, h->eps, h->f, h->beta, h->sc, h->Y);
+    tc_similarity(s, n, h->Q, h->Y, D1, h->tw, /*transpose_first=*/0);     // D1 = Q Y Q^T
+    return;
+  }
+  dgemm(s, 0, 0, n, n, n, 1.0, F1, n, h->Q, n, 0.0, h->T1, n);         // T1 = F1 Q
+  dgemm(s, 1, 0, n, n, n, 1.0, h->Q, n, h->T1, n, 0.0, h->T2, n, 1);   // T2 = Q^T T1
+  launch_dmu(s, n, h->T2, h->eps, h->f, h->beta, h->sc);
+  launch_dmpt_y(s, n, h->T2, h->eps, h->f, h->beta, h->sc, h->Y);
+  dgemm(s, 0, 0, n, n, n, 1.0, h->Q, n, h->Y, n, 0.0, h->T1, n);       // T1 = Q Y
+  dgemm(s, 0, 1, n, n, n, 1.0, h->T1, n, h->Q, n, 0.0, D1, n, 1);      // D1 = T1 Q^T
+}
+
+static int eig(sim_handle* h) {
+  phase_begin(h, PH_TRIDIAG);
+  int st = eig_tridiagonalize(h->stream, h->n, h->Fock, h->ew, &h->sc->status, h->sms);
+  phase_end(h);
+  if (st != 0) return fail(SIM_EINTERNAL, "tridiagonalisation launch failed (code " + std::to_string(st) + ")");
+  phase_begin(h, PH_TRIEIG);
+  eig_tridiagonal_solve(h->stream, h->n, h->eps, h->Q, h->ew);
+  phase_end(h);
+  phase_begin(h, PH_BACKTR);
+  eig_backtransform(h->stream, h->n, h->Q, h->ew);
+  phase_end(h);
+  return SIM_OK;
+}
+
+// Evaluate everything at (R, X(t)): pair blocks, F, D0, U, forces, Krylov kernel.
+static int evaluate(sim_handle* h, bool krylov = true) {
+  cudaStream_t s = h->stream;
+  int n = h->n;
+  size_t nn = (size_t)n * n;
+  const double* X = xslot(h, 0);
+  MolDev m = mol(h);
+  PairDev pd = pairs(h);
+  phase_begin(h, PH_PAIRS);
+  launch_pair_derivs(s, h->npair, h->pA, h->pB, h->elem, h->R, h->tab, h->W, h->S, h->E, h->dW, h->dS, h->dE);
+  phase_end(h);
+  phase_begin(h, PH_FOCK);
+  launch_build_h(s, m, pd, h->tab, h->h);
+  launch_pack_diag(s, m, X, h->Pd);
+  launch_build_fock(s, m, pd, h->tab, X, h->Pd, h->h, h->Fock);
+  phase_end(h);
+  int rc = eig(h);
+  if (rc) return rc;
+  phase_begin(h, PH_DENSITY);
+  launch_fermi(s, n, h->eps, (double)h->nocc, h->beta, h->f, h->sc);
+  density(h);
+  phase_end(h);
+  phase_begin(h, PH_FORCES);
+  launch_energy(s, n, h->npair, h->h, h->D, X, h->Fock, h->E, h->sc, h->red);
+  launch_pack_diag(s, m, h->D, h->Dd);
+  launch_forces(s, m, pd, h->tab, h->D, X, h->Dd, h->Pd, h->g, h->F);
+  phase_end(h);
+  if (!krylov) return SIM_OK;
+  // Krylov subspace approximation of K (D0 - X), eqs. 31-34
+  phase_begin(h, PH_KRY_BLAS);
+  launch_krylov_start(s, nn, h->D, X, h->W0, h->sc, h->red);
+  phase_end(h);
+  for (int k = 0; k < h->mmax; ++k) {
+    phase_begin(h, PH_KRY_BLAS);
+    const double* src = (k == 0) ? h->W0 : h->Wk[k - 1];
+    launch_krylov_orth(s, nn, k, h->Vk, src, h->Vk[k], h->sc, h->red, h->coef);
+    phase_end(h);
+    phase_begin(h, PH_KRY_FOCK);
+    launch_pack_diag(s, m, h->Vk[k], h->Vd);
+    launch_build_fock(s, m, pd, h->tab, h->Vk[k], h->Vd, nullptr, h->F1);
+    phase_end(h);
+    phase_begin(h, PH_KRY_GEMM);
+    dmpt(h, h->F1, h->D1);
+    phase_end(h);
+    phase_begin(h, PH_KRY_BLAS);
+    launch_krylov_w(s, nn, k, h->D1, h->Vk[k], h->Wk[k], h->Wk, h->W0, h->sc, h->red, h->cfg.krylov_tol,
+                    h->cfg.m_min);
+    phase_end(h);
+  }
+  phase_begin(h, PH_KRY_BLAS);
+  launch_krylov_combine(s, nn, h->mmax, h->Vk, h->sc, h->K);
+  launch_check_finite(s, (size_t)3 * h->N, h->F, h->sc);
+  launch_check_finite(s, nn, h->K, h->sc);
+  phase_end(h);
+  return SIM_OK;
+}
+
+__global__ void record_kernel(const Scalars* sc, double Te, sim_step_result* out) {
+  sim_step_result r;
+  r.E_kin = sc->e_kin;
+  r.U = sc->e_elec - 2.0 * Te * sc->entropy + sc->vnn;
+  r.E_tot = r.E_kin + r.U;
+  r.mu = sc->mu;
+  r.gap = sc->gap;
+  r.res_norm = ::sqrt(sc->res2);
+  r.fit_err = sc->fit;
+  r.rank = sc->rank;
+  r.pad = sc->status;
+  *out = r;
+}
+
+static int one_step(sim_handle* h, sim_step_result* rec_dev) {
+  cudaStream_t s = h->stream;
+  size_t nn = (size_t)h->n * h->n;
+  double dt = h->cfg.dt;
+  phase_begin(h, PH_UPDATE);
+  launch_half_kick(s, h->N, h->V, h->F, h->mass, dt);     // eq. 27
+  launch_drift(s, h->N, h->R, h->V, dt);                  // eq. 28
+  double* Xh[7];
+  for (int k = 0; k < 7; ++k) Xh[k] = xslot(h, k);
+  double* Xnew = xslot(h, 7);
+  launch_x_update(s, nn, Xh, h->K, kKappa, kAlphaDamp, Xnew);   // eq. 35
+  h->xhead = (h->xhead + 7) % 8;
+  phase_end(h);
+  int rc = evaluate(h);
+  if (rc) return rc;
+  phase_begin(h, PH_UPDATE);
+  launch_half_kick(s, h->N, h->V, h->F, h->mass, dt);     // eq. 30
+  launch_kinetic(s, h->N, h->V, h->mass, h->sc);
+  if (rec_dev) {
+    record_kernel<<<1, 1, 0, s>>>(h->sc, h->cfg.Te, rec_dev);
+    count_launch();
+  }
+  phase_end(h);
+  return SIM_OK;
+}
+
+static int check_status(sim_handle* h) {
+  int st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&st, &h->sc->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  CUDA_TRY(cudaGetLastError());
+  if (st & kStatusTimeout) return fail(SIM_ETIMEOUT, "a bounded device-side wait expired");
+  if (st & kStatusNumeric) return fail(SIM_ENUMERIC, "NaN or Inf in forces or kernel result");
+  return SIM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// allocation
+// ---------------------------------------------------------------------------
+struct Arena {
+  char* base;
+  size_t off, cap;
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+    T* p = (T*)(base ? base + off : nullptr);
+    off += bytes;
+    return p;
+  }
+};
+
+static void layout(sim_handle* h, Arena& a) {
+  size_t nn = (size_t)h->n * h->n;
+  size_t np = (size_t)(h->npair > 0 ? h->npair : 1);
+  h->elem = a.take<int>(h->N);
+  h->off = a.take<int>(h->N + 1);
+  h->pA = a.take<int>(np);
+  h->pB = a.take<int>(np);
+  h->R = a.take<double>(3 * h->N);
+  h->V = a.take<double>(3 * h->N);
+  h->F = a.take<double>(3 * h->N);
+  h->mass = a.take<double>(h->N);
+  h->g = a.take<double>(3 * np);
+  h->W = a.take<double>(100 * np);
+  h->S = a.take<double>(16 * np);
+  h->E = a.take<double>(np);
+  h->dW = a.take<double>(300 * np);
+  h->dS = a.take<double>(48 * np);
+  h->dE = a.take<double>(3 * np);
+  h->h = a.take<double>(nn);
+  h->Fock = a.take<double>(nn);
+  h->D = a.take<double>(nn);
+  h->K = a.take<double>(nn);
+  h->Q = a.take<double>(nn);
+  h->Qs = a.take<double>(nn);
+  h->T1 = a.take<double>(nn);
+  h->T2 = a.take<double>(nn);
+  h->F1 = a.take<double>(nn);
+  h->Y = a.take<double>(nn);
+  h->D1 = a.take<double>(nn);
+  h->W0 = a.take<double>(nn);
+  for (int k = 0; k < 8; ++k) h->X[k] = a.take<double>(nn);
+  for (int k = 0; k < h->mmax; ++k) {
+    h->Vk[k] = a.take<double>(nn);
+    h->Wk[k] = a.take<double>(nn);
+  }
+  h->eps = a.take<double>(h->n);
+  h->f = a.take<double>(h->n);
+  h->Dd = a.take<double>(10 * (size_t)h->N);
+  h->Pd = a.take<double>(10 * (size_t)h->N);
+  h->Vd = a.take<double>(10 * (size_t)h->N);
+  h->red = a.take<double>(kReduceWorkDoubles);
+  h->coef = a.take<double>(64);
+  h->sc = a.take<Scalars>(1);
+  h->rec = a.take<sim_step_result>(kRecCap);
+  void* ewb = a.take<char>(eig_work_bytes(h->n));
+  if (a.base) eig_work_bind(h->ew, ewb, h->n);
+  size_t tcb = tc_work_bytes(h->n);
+  void* twb = a.take<char>(tcb);
+  if (a.base) tc_work_bind(h->tw, twb, h->n);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void sim_config_default(sim_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->Te = 1000.0;
+  c->dt = 0.5;
+  c->m_max = 4;
+  c->m_min = 4;
+  c->krylov_tol = 0.0;
+  c->precision = SIM_PREC_FP64;
+  c->scf_tol = 1e-10;
+  c->scf_max = 5000;
+  c->scf_mix = 0.1;
+  c->device = 0;
+  c->stream = nullptr;
+}
+
+const char* sim_last_error(void) { return t_err.c_str(); }
+long long sim_launch_count(void) { return g_launches.load(); }
+int sim_norb(const sim_handle* h) { return h ? h->n : -1; }
+int sim_nocc(const sim_handle* h) { return h ? h->nocc : -1; }
+void* sim_stream(sim_handle* h) { return h ? (void*)h->stream : nullptr; }
+
+static int scf(sim_handle* h, int* iters) {
+  cudaStream_t s = h->stream;
+  int n = h->n;
+  size_t nn = (size_t)n * n;
+  MolDev m = mol(h);
+  PairDev pd = pairs(h);
+  double* P = xslot(h, 0);
+  double* Dn = h->D;
+  double* err_d = h->coef + 48;
+  // diagonal guess: valence electrons spread over each atom's orbitals, trace N_occ
+  std::vector<double> P0(nn, 0.0);
+  double tr = 0.0;
+  for (int A = 0; A < h->N; ++A) {
+    int o = h->off_h[A], no = h->off_h[A + 1] - o;
+    double v = 0.5 * h->tab.e[h->elem_h[A]].zcore / no;
+    for (int k = 0; k < no; ++k) { P0[(size_t)(o + k) * n + o + k] = v; tr += v; }
+  }
+  for (int i = 0; i < n; ++i) P0[(size_t)i * n + i] *= h->nocc / tr;
+  CUDA_TRY(cudaMemcpyAsync(P, P0.data(), nn * sizeof(double), cudaMemcpyHostToDevice, s));
+  double mix = h->cfg.scf_mix;
+  for (int it = 0; it < h->cfg.scf_max; ++it) {
+    launch_pack_diag(s, m, P, h->Pd);
+    launch_build_fock(s, m, pd, h->tab, P, h->Pd, h->h, h->Fock);
+    int rc = eig(h);
+    if (rc) return rc;
+    launch_fermi(s, n, h->eps, (double)h->nocc, h->beta, h->f, h->sc);
+    density(h);
+    launch_maxabs_diff(s, nn, Dn, P, err_d, h->red);
+    double err = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&err, err_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    int st = 0;
+    CUDA_TRY(cudaMemcpy(&st, &h->sc->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & kStatusTimeout) return fail(SIM_ETIMEOUT, "eigensolver barrier timed out during SCF");
+    if (!std::isfinite(err)) return fail(SIM_ENUMERIC, "NaN during SCF");
+    if (err < h->cfg.scf_tol) {
+      CUDA_TRY(cudaMemcpyAsync(P, Dn, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      *iters = it;
+      return SIM_OK;
+    }
+    launch_axpby(s, nn, mix, P, 1.0 - mix, Dn, P);
+  }
+  return fail(SIM_ENOCONV, "SCF did not converge within scf_max iterations");
+}
+
+int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, const int* Z,
+               const double* R, const double* V, int charge, const double* P0, sim_handle** out) {
+  if (!cfg || !table || !Z || !R || !out || natoms < 1) return fail(SIM_EINVAL, "null argument or natoms < 1");
+  *out = nullptr;
+  if (!(cfg->Te > 0.0) || !(cfg->dt > 0.0) || cfg->m_max < 1 || cfg->m_max > 16 || cfg->m_min < 1 ||
+      cfg->m_min > cfg->m_max || cfg->scf_max < 1 || !(cfg->scf_mix >= 0.0 && cfg->scf_mix < 1.0))
+    return fail(SIM_EINVAL, "invalid configuration");
+  if (cfg->precision != SIM_PREC_FP64 && cfg->precision != SIM_PREC_MIXED)
+    return fail(SIM_EINVAL, "unknown precision mode");
+  sim_handle* h = new sim_handle();
+  h->cfg = *cfg;
+  for (int e = 0; e < 4; ++e)
+    if (build_elem(table->v[e], h->tab.e[e]) != 0) {
+      delete h;
+      return fail(SIM_EINVAL, "parameter table: norb/nprin must be (1,1) for H and (4,2) otherwise");
+    }
+  h->N = natoms;
+  h->elem_h.resize(natoms);
+  h->off_h.resize(natoms + 1);
+  h->mass_h.resize(natoms);
+  double zsum = 0.0;
+  h->off_h[0] = 0;
+  for (int A = 0; A < natoms; ++A) {
+    int ei = elem_index(Z[A]);
+    if (ei < 0) { delete h; return fail(SIM_EINVAL, "unsupported atomic number " + std::to_string(Z[A])); }
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(R[3 * A + k]) || (V && !std::isfinite(V[3 * A + k]))) {
+        delete h;
+        return fail(SIM_EINVAL, "non-finite position or velocity");
+      }
+    h->elem_h[A] = ei;
+    h->off_h[A + 1] = h->off_h[A] + h->tab.e[ei].norb;
+    h->mass_h[A] = h->tab.e[ei].mass;
+    zsum += h->tab.e[ei].zcore;
+  }
+  h->n = h->off_h[natoms];
+  long long nel = std::llround(zsum) - charge;
+  if (nel < 0 || nel % 2 != 0 || nel / 2 > h->n) {
+    delete h;
+    return fail(SIM_EINVAL, "electron count must be even, non-negative and fit the basis (closed shell)");
+  }
+  h->nocc = (int)(nel / 2);
+  h->npair = natoms * (natoms - 1) / 2;
+  h->mmax = cfg->m_max;
+  h->beta = 1.0 / (kBoltz * cfg->Te);
+  h->dev = cfg->device;
+  if (cudaSetDevice(h->dev) != cudaSuccess) { delete h; return fail(SIM_EINVAL, "cudaSetDevice failed"); }
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
+  if (!upload_overlap_tables()) { delete h; return fail(SIM_EINTERNAL, "overlap table upload failed"); }
+  if (cfg->stream) {
+    h->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return fail(SIM_EINTERNAL, "stream creation failed");
+    }
+    h->own_stream = true;
+  }
+  Arena sizing{nullptr, 0, 0};
+  layout(h, sizing);
+  h->arena_bytes = sizing.off + 256;
+  if (cudaMalloc(&h->arena, h->arena_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    size_t need = h->arena_bytes;
+    sim_destroy(h);
+    return fail(SIM_ENOMEM, "device allocation of " + std::to_string(need) + " bytes failed");
+  }
+  Arena a{(char*)h->arena, 0, h->arena_bytes};
+  layout(h, a);
+  cudaStream_t s = h->stream;
+  std::vector<int> pa, pb;
+  pa.reserve(h->npair);
+  pb.reserve(h->npair);
+  for (int A = 0; A < natoms; ++A)
+    for (int B = A + 1; B < natoms; ++B) { pa.push_back(A); pb.push_back(B); }
+  std::vector<double> v0(3 * (size_t)natoms, 0.0);
+  if (V) std::memcpy(v0.data(), V, v0.size() * sizeof(double));
+  int rc = SIM_OK;
+  do {
+    if (cudaMemsetAsync(h->sc, 0, sizeof(Scalars), s) != cudaSuccess) { rc = fail(SIM_EINTERNAL, "memset"); break; }
+    cudaMemcpyAsync(h->elem, h->elem_h.data(), natoms * sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->off, h->off_h.data(), (natoms + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (h->npair) {
+      cudaMemcpyAsync(h->pA, pa.data(), h->npair * sizeof(int), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(h->pB, pb.data(), h->npair * sizeof(int), cudaMemcpyHostToDevice, s);
+    }
+    cudaMemcpyAsync(h->R, R, 3 * (size_t)natoms * sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->V, v0.data(), 3 * (size_t)natoms * sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->mass, h->mass_h.data(), natoms * sizeof(double), cudaMemcpyHostToDevice, s);
+    launch_fill(s, (size_t)h->n * h->n, h->K, 0.0);
+    // pair blocks and h at R0
+    launch_pair_derivs(s, h->npair, h->pA, h->pB, h->elem, h->R, h->tab, h->W, h->S, h->E, h->dW, h->dS, h->dE);
+    launch_build_h(s, mol(h), pairs(h), h->tab, h->h);
+    size_t nn = (size_t)h->n * h->n;
+    if (P0) {
+      for (size_t i = 0; i < nn; ++i)
+        if (!std::isfinite(P0[i])) { rc = fail(SIM_EINVAL, "non-finite P0"); break; }
+      if (rc) break;
+      cudaMemcpyAsync(xslot(h, 0), P0, nn * sizeof(double), cudaMemcpyHostToDevice, s);
+    } else {
+      int it = 0;
+      rc = scf(h, &it);
+      if (rc) break;
+    }
+    for (int k = 1; k < 7; ++k)
+      cudaMemcpyAsync(xslot(h, k), xslot(h, 0), nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    rc = evaluate(h);
+    if (rc) break;
+    launch_kinetic(s, h->N, h->V, h->mass, h->sc);
+    record_kernel<<<1, 1, 0, s>>>(h->sc, h->cfg.Te, h->rec);
+    count_launch();
+    rc = check_status(h);
+  } while (0);
+  if (rc != SIM_OK) {
+    std::string msg = t_err;
+    sim_destroy(h);
+    t_err = msg;
+    return rc;
+  }
+  *out = h;
+  return SIM_OK;
+}
+
+int sim_step_async(sim_handle* h, int nsteps) {
+  if (!h || nsteps < 0) return fail(SIM_EINVAL, "bad handle or nsteps");
+  for (int i = 0; i < nsteps; ++i) {
+    int rc = one_step(h, h->rec);
+    if (rc) return rc;
+  }
+  h->last_rec = 0;
+  return SIM_OK;
+}
+
+int sim_step(sim_handle* h, int nsteps, sim_step_result* out) {
+  if (!h || nsteps < 0) return fail(SIM_EINVAL, "bad handle or nsteps");
+  int done = 0;
+  while (done < nsteps) {
+    int chunk = nsteps - done;
+    if (chunk > kRecCap) chunk = kRecCap;
+    for (int i = 0; i < chunk; ++i) {
+      int rc = one_step(h, h->rec + i);
+      if (rc) return rc;
+    }
+    h->last_rec = chunk - 1;
+    if (out) {
+      CUDA_TRY(cudaMemcpyAsync(out + done, h->rec, chunk * sizeof(sim_step_result), cudaMemcpyDeviceToHost,
+                               h->stream));
+    }
+    int rc = check_status(h);
+    if (rc) return rc;
+    done += chunk;
+  }
+  if (h->prof) collect_events(h);
+  return SIM_OK;
+}
+
+int sim_last_result(sim_handle* h, sim_step_result* out) {
+  if (!h || !out) return fail(SIM_EINVAL, "null argument");
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  CUDA_TRY(cudaMemcpy(out, h->rec + h->last_rec, sizeof(sim_step_result), cudaMemcpyDeviceToHost));
+  return SIM_OK;
+}
+
+int sim_get_state(sim_handle* h, double* R, double* V, double* F, double* D0) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  cudaStream_t s = h->stream;
+  size_t b3 = 3 * (size_t)h->N * sizeof(double);
+  if (R) CUDA_TRY(cudaMemcpyAsync(R, h->R, b3, cudaMemcpyDeviceToHost, s));
+  if (V) CUDA_TRY(cudaMemcpyAsync(V, h->V, b3, cudaMemcpyDeviceToHost, s));
+  if (F) CUDA_TRY(cudaMemcpyAsync(F, h->F, b3, cudaMemcpyDeviceToHost, s));
+  if (D0) CUDA_TRY(cudaMemcpyAsync(D0, h->D, (size_t)h->n * h->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return SIM_OK;
+}
+
+int sim_set_state(sim_handle* h, const double* R, const double* V, const double* Xhist) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  cudaStream_t s = h->stream;
+  size_t nn = (size_t)h->n * h->n;
+  size_t b3 = 3 * (size_t)h->N * sizeof(double);
+  if (R) CUDA_TRY(cudaMemcpyAsync(h->R, R, b3, cudaMemcpyHostToDevice, s));
+  if (V) CUDA_TRY(cudaMemcpyAsync(h->V, V, b3, cudaMemcpyHostToDevice, s));
+  if (Xhist)
+    for (int k = 0; k < 7; ++k)
+      CUDA_TRY(cudaMemcpyAsync(xslot(h, k), Xhist + k * nn, nn * sizeof(double), cudaMemcpyHostToDevice, s));
+  int rc = evaluate(h);
+  if (rc) return rc;
+  launch_kinetic(s, h->N, h->V, h->mass, h->sc);
+  record_kernel<<<1, 1, 0, s>>>(h->sc, h->cfg.Te, h->rec);
+  count_launch();
+  h->last_rec = 0;
+  return check_status(h);
+}
+
+int sim_get_matrix(sim_handle* h, int which, double* out) {
+  if (!h || !out) return fail(SIM_EINVAL, "null argument");
+  const double* src = nullptr;
+  switch (which) {
+    case SIM_MAT_X: src = xslot(h, 0); break;
+    case SIM_MAT_D0: src = h->D; break;
+    case SIM_MAT_FOCK: src = h->Fock; break;
+    case SIM_MAT_H: src = h->h; break;
+    case SIM_MAT_KERNEL: src = h->K; break;
+    case SIM_MAT_Q: src = h->Q; break;
+    default: return fail(SIM_EINVAL, "unknown matrix id");
+  }
+  CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)h->n * h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+int sim_get_vector(sim_handle* h, int which, double* out) {
+  if (!h || !out) return fail(SIM_EINVAL, "null argument");
+  const double* src = (which == 0) ? h->eps : (which == 1) ? h->f : nullptr;
+  if (!src) return fail(SIM_EINVAL, "unknown vector id");
+  CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+int sim_profile_enable(sim_handle* h, int enable) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (h->prof && !enable) collect_events(h);
+  h->prof = enable != 0;
+  for (int i = 0; i < PH_COUNT; ++i) { h->ph_ms[i] = 0.0; h->ph_n[i] = 0; }
+  return SIM_OK;
+}
+
+int sim_phase_count(void) { return PH_COUNT; }
+const char* sim_phase_name(int p) { return (p >= 0 && p < PH_COUNT) ? kPhaseNames[p] : ""; }
+
+int sim_phase_times(sim_handle* h, double* ms, long long* launches, double* work) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  collect_events(h);
+  double n = h->n, np = h->npair;
+  // algorithmic work of one timed phase instance (bytes for HBM-bound phases,
+  // flops for arithmetic-bound ones); see the design notes for the derivation
+  double w[PH_COUNT] = {
+      np * (117.0 * 4.0) * 8.0,             // pair blocks + derivatives written (bytes)
+      (np * 116.0 + 4.0 * n * n) * 8.0,     // h + F: pair blocks read, matrices written (bytes)
+      4.0 / 3.0 * n * n * n,                // tridiagonalisation flops
+      0.0,                                  // bisection + inverse iteration
+      2.0 * n * n * n,                      // back-transformation flops
+      n * n * n,                            // D0 = Q f Q^T (symmetric) flops
+      np * (468.0) * 8.0,                   // force contraction bytes
+      (np * 100.0 + 3.0 * n * n) * 8.0,     // G(V) bytes
+      6.0 * n * n * n,                      // DMPT: 3 full + ... (2 general + 2 symmetric GEMMs)
+      0.0, 0.0};
+  for (int i = 0; i < PH_COUNT; ++i) {
+    if (ms) ms[i] = h->ph_ms[i];
+    if (launches) launches[i] = h->ph_n[i];
+    if (work) work[i] = w[i];
+  }
+  return SIM_OK;
+}
+
+void sim_destroy(sim_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& p : h->ev_pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->arena) cudaFree(h->arena);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+}  // extern "C"

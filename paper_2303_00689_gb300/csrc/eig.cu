@@ -1,0 +1,448 @@
+// FP64 symmetric eigensolver for F = Q diag(eps) Q^T (eq. 19 needs the
+// eigenpairs; eq. 36 needs them again for the DMPT response).
+//
+//  1. Householder tridiagonalisation in ONE persistent kernel: the rank-2
+//     update of column k is applied lazily, fused with the symmetric
+//     matrix-vector product of column k + 1, so every column costs one read
+//     and one write of the trailing matrix and one grid-wide barrier.  All
+//     blocks compute the reflector redundantly (same data, same reduction
+//     order, bitwise identical), so no broadcast is needed.  The barrier is a
+//     counter/generation pair with a bounded spin: on expiry the kernel sets
+//     kStatusTimeout and returns.
+//  2. Eigenvalues of the tridiagonal matrix by bisection on Sturm counts,
+//     one thread per eigenvalue (ascending order by construction).
+//  3. Eigenvectors by inverse iteration with a partially pivoted
+//     tridiagonal LU, one thread per cluster of close eigenvalues; members of
+//     a cluster are re-orthogonalised (modified Gram-Schmidt) in order.
+//  4. Back-transformation Q = H_0 ... H_{n-3} Z with blocks of 64 reflectors
+//     in compact WY form (I - V T V^T) applied by FP64 GEMMs.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace kx {
+
+constexpr int kTriThreads = 512;
+constexpr int kBtBlock = 64;          // reflectors per back-transform block
+constexpr double kEps = 2.220446049250313e-16;
+
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    unsigned g = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*vgen == g) {
+        if (++it > (1LL << 25)) {
+          atomicOr(status, (int)kStatusTimeout);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ((*(volatile int*)status) & kStatusTimeout) ? 0 : 1;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __restrict__ A,
+                                                              double* __restrict__ Vst,
+                                                              double* __restrict__ d,
+                                                              double* __restrict__ e,
+                                                              double* __restrict__ tau,
+                                                              double* __restrict__ pbuf,
+                                                              unsigned* bar, int* status) {
+  extern __shared__ double sm[];
+  double* vp = sm;           // previous reflector (valid for indices >= k)
+  double* wp = sm + n;       // previous w
+  double* vc = sm + 2 * n;   // current reflector
+  double* red = sm + 3 * n;  // 32 doubles of reduction scratch
+  __shared__ double s_par[4];  // beta, tau, scale, d_k
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int wpb = blockDim.x >> 5;
+  const int gw = blockIdx.x * wpb + (tid >> 5);
+  const int totw = gridDim.x * wpb;
+  bool prev = false;
+
+  for (int k = 0; k < n - 2; ++k) {
+    // 1. row k of the lazily updated matrix
+    double loc = 0.0;
+    for (int j = k + 2 + tid; j < n; j += blockDim.x) {
+      double x = A[(size_t)k * n + j];
+      if (prev) x -= vp[k] * wp[j] + wp[k] * vp[j];
+      vc[j] = x;
+      loc += x * x;
+    }
+    double sigma = block_sum(loc, red);
+    if (tid == 0) {
+      double xk = A[(size_t)k * n + k];
+      double x1 = A[(size_t)k * n + k + 1];
+      if (prev) {
+        xk -= 2.0 * vp[k] * wp[k];
+        x1 -= vp[k] * wp[k + 1] + wp[k] * vp[k + 1];
+      }
+      double beta, t, scale;
+      if (sigma == 0.0) {
+        beta = x1; t = 0.0; scale = 0.0;
+      } else {
+        double nrm = ::sqrt(x1 * x1 + sigma);
+        beta = (x1 >= 0.0) ? -nrm : nrm;
+        t = (beta - x1) / beta;
+        scale = 1.0 / (x1 - beta);
+      }
+      s_par[0] = beta; s_par[1] = t; s_par[2] = scale; s_par[3] = xk;
+    }
+    __syncthreads();
+    const double t = s_par[1], scale = s_par[2];
+    for (int j = k + 2 + tid; j < n; j += blockDim.x) vc[j] *= scale;
+    if (tid == 0) vc[k + 1] = 1.0;
+    __syncthreads();
+    if (blockIdx.x == 0) {
+      if (tid == 0) { d[k] = s_par[3]; e[k] = s_par[0]; tau[k] = t; }
+      for (int j = tid; j < n; j += blockDim.x) Vst[(size_t)k * n + j] = (j > k) ? vc[j] : 0.0;
+    }
+    // 2. fused: apply the previous rank-2 update to rows/cols >= k+1 and
+    //    form p = tau A v for the current reflector
+    double* pb = pbuf + (size_t)(k & 1) * n;
+    for (int i = k + 1 + gw; i < n; i += totw) {
+      double* row = A + (size_t)i * n;
+      double acc = 0.0;
+      if (prev) {
+        double vi = vp[i], wi = wp[i];
+        for (int j = k + 1 + lane; j < n; j += 32) {
+          double a = row[j] - (vi * wp[j] + wi * vp[j]);
+          row[j] = a;
+          acc += a * vc[j];
+        }
+      } else {
+        for (int j = k + 1 + lane; j < n; j += 32) acc += row[j] * vc[j];
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) pb[i] = t * acc;
+    }
+    if (!grid_barrier(bar, gridDim.x, status)) return;
+    // 3. w = p - (tau/2)(p.v) v
+    loc = 0.0;
+    for (int j = k + 1 + tid; j < n; j += blockDim.x) loc += pb[j] * vc[j];
+    double pv = block_sum(loc, red);
+    for (int j = k + 1 + tid; j < n; j += blockDim.x) {
+      wp[j] = pb[j] - 0.5 * t * pv * vc[j];
+      vp[j] = vc[j];
+    }
+    prev = true;
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    if (n == 1) {
+      d[0] = A[0];
+    } else {
+      int a = n - 2, b = n - 1;
+      double a00 = A[(size_t)a * n + a], a10 = A[(size_t)b * n + a], a11 = A[(size_t)b * n + b];
+      if (prev) {
+        a00 -= 2.0 * vp[a] * wp[a];
+        a10 -= vp[b] * wp[a] + wp[b] * vp[a];
+        a11 -= 2.0 * vp[b] * wp[b];
+      }
+      d[a] = a00; d[b] = a11; e[a] = a10;
+    }
+  }
+}
+
+// Gershgorin interval, squared off-diagonals, pivmin; one block
+__global__ void gersh_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
+                             double* __restrict__ e2, double* __restrict__ scal) {
+  __shared__ double red[32];
+  double lo = 1e300, hi = -1e300, em = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double r = 0.0;
+    if (i > 0) r += fabs(e[i - 1]);
+    if (i < n - 1) { r += fabs(e[i]); e2[i] = e[i] * e[i]; em = fmax(em, e[i] * e[i]); }
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+  }
+  // min/max reductions through negation-free warp shuffles
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
+  }
+  __shared__ double slo[32], shi[32], sem[32];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { slo[w] = lo; shi[w] = hi; sem[w] = em; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    for (int i = 1; i < nw; ++i) { lo = fmin(lo, slo[i]); hi = fmax(hi, shi[i]); em = fmax(em, sem[i]); }
+    double tn = fmax(fabs(lo), fabs(hi));
+    double pivmin = 1e-290 * fmax(1.0, em);
+    lo -= 4.0 * kEps * tn + 2.0 * pivmin;
+    hi += 4.0 * kEps * tn + 2.0 * pivmin;
+    scal[0] = lo; scal[1] = hi; scal[2] = tn; scal[3] = pivmin;
+  }
+  (void)red;
+}
+
+__device__ __forceinline__ int sturm_count(int n, const double* __restrict__ d,
+                                           const double* __restrict__ e2, double x, double pivmin) {
+  double q = d[0] - x;
+  if (fabs(q) <= pivmin) q = -pivmin;
+  int c = (q < 0.0);
+  for (int j = 1; j < n; ++j) {
+    q = d[j] - x - e2[j - 1] / q;
+    if (fabs(q) <= pivmin) q = -pivmin;
+    c += (q < 0.0);
+  }
+  return c;
+}
+
+__global__ void bisect_kernel(int n, const double* __restrict__ d, const double* __restrict__ e2,
+                              const double* __restrict__ scal, double* __restrict__ ev) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double lo = scal[0], hi = scal[1], pivmin = scal[3];
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (hi - lo <= 2.0 * kEps * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    if (sturm_count(n, d, e2, mid, pivmin) > i) hi = mid; else lo = mid;
+  }
+  ev[i] = 0.5 * (lo + hi);
+}
+
+__global__ void cluster_kernel(int n, const double* __restrict__ ev, const double* __restrict__ scal,
+                               int* __restrict__ clus) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double ctol = 1e-7 * fmax(1.0, scal[2]);
+  clus[i] = (i == 0 || ev[i] - ev[i - 1] > ctol) ? 1 : 0;
+}
+
+__device__ __forceinline__ double start_value(int row, int col) {
+  unsigned h = (unsigned)row * 0x9E3779B1u ^ ((unsigned)col * 0x85EBCA77u + 0x165667B1u);
+  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+  return ((double)(h & 0xFFFFF) / 524288.0) - 1.0 + 1e-3;
+}
+
+// inverse iteration; one thread per cluster leader; lu: 5 x n x n workspace
+__global__ void invit_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
+                             const double* __restrict__ ev, const double* __restrict__ scal,
+                             const int* __restrict__ clus, double* __restrict__ lu,
+                             double* __restrict__ Z) {
+  int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= n || !clus[L]) return;
+  int end = L + 1;
+  while (end < n && !clus[end]) ++end;
+  const double tn = fmax(scal[2], 1e-300);
+  const double tiny = kEps * tn;
+  const size_t nn = (size_t)n * n;
+  double* dl = lu + 0 * nn;
+  double* dd = lu + 1 * nn;
+  double* du = lu + 2 * nn;
+  double* du2 = lu + 3 * nn;
+  double* pv = lu + 4 * nn;
+#define LU(a, r) a[(size_t)(r) * n + L]
+#define ZC(r, c) Z[(size_t)(r) * n + (c)]
+  double prevlam = 0.0;
+  for (int j = L; j < end; ++j) {
+    double lam = ev[j];
+    if (j > L && lam - prevlam < 10.0 * tiny) lam = prevlam + 10.0 * tiny;
+    prevlam = lam;
+    if (n == 1) { ZC(0, j) = 1.0; continue; }
+    // LU of T - lam I with partial pivoting
+    for (int r = 0; r < n; ++r) {
+      LU(dd, r) = d[r] - lam;
+      if (r < n - 1) { LU(dl, r) = e[r]; LU(du, r) = e[r]; }
+      LU(du2, r) = 0.0;
+    }
+    for (int r = 0; r < n - 1; ++r) {
+      double a = LU(dd, r), b = LU(dl, r);
+      if (fabs(a) >= fabs(b)) {
+        LU(pv, r) = 0.0;
+        if (fabs(a) < tiny) { a = (a >= 0.0) ? tiny : -tiny; LU(dd, r) = a; }
+        double f = b / a;
+        LU(dl, r) = f;
+        LU(dd, r + 1) = LU(dd, r + 1) - f * LU(du, r);
+      } else {
+        LU(pv, r) = 1.0;
+        double f = a / b;
+        LU(dd, r) = b;
+        LU(dl, r) = f;
+        double t = LU(du, r);
+        LU(du, r) = LU(dd, r + 1);
+        LU(dd, r + 1) = t - f * LU(dd, r + 1);
+        if (r < n - 2) {
+          LU(du2, r) = LU(du, r + 1);
+          LU(du, r + 1) = -f * LU(du, r + 1);
+        }
+      }
+    }
+    if (fabs(LU(dd, n - 1)) < tiny) LU(dd, n - 1) = (LU(dd, n - 1) >= 0.0) ? tiny : -tiny;
+    for (int r = 0; r < n; ++r) ZC(r, j) = start_value(r, j);
+    for (int it = 0; it < 3; ++it) {
+      // forward (L with pivots)
+      for (int r = 0; r < n - 1; ++r) {
+        double br = ZC(r, j), br1 = ZC(r + 1, j);
+        if (LU(pv, r) == 0.0) {
+          ZC(r + 1, j) = br1 - LU(dl, r) * br;
+        } else {
+          ZC(r, j) = br1;
+          ZC(r + 1, j) = br - LU(dl, r) * br1;
+        }
+      }
+      // backward (U, three diagonals)
+      ZC(n - 1, j) = ZC(n - 1, j) / LU(dd, n - 1);
+      if (n > 1) ZC(n - 2, j) = (ZC(n - 2, j) - LU(du, n - 2) * ZC(n - 1, j)) / LU(dd, n - 2);
+      for (int r = n - 3; r >= 0; --r)
+        ZC(r, j) = (ZC(r, j) - LU(du, r) * ZC(r + 1, j) - LU(du2, r) * ZC(r + 2, j)) / LU(dd, r);
+      // scale, re-orthogonalise within the cluster, normalise
+      double mx = 0.0;
+      for (int r = 0; r < n; ++r) mx = fmax(mx, fabs(ZC(r, j)));
+      double s = (mx > 0.0) ? 1.0 / mx : 1.0;
+      for (int r = 0; r < n; ++r) ZC(r, j) *= s;
+      for (int c = L; c < j; ++c) {
+        double dot = 0.0;
+        for (int r = 0; r < n; ++r) dot += ZC(r, c) * ZC(r, j);
+        for (int r = 0; r < n; ++r) ZC(r, j) -= dot * ZC(r, c);
+      }
+      double nrm = 0.0;
+      for (int r = 0; r < n; ++r) nrm += ZC(r, j) * ZC(r, j);
+      nrm = ::sqrt(nrm);
+      s = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+      for (int r = 0; r < n; ++r) ZC(r, j) *= s;
+    }
+  }
+#undef LU
+#undef ZC
+}
+
+// T factor of a block of kb reflectors (forward, columnwise): one block
+__global__ void tfactor_kernel(int kb, const double* __restrict__ tau, const double* __restrict__ G,
+                               int ldg, double* __restrict__ T, int ldt) {
+  __shared__ double tcol[kBtBlock];
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) T[(e / kb) * ldt + e % kb] = 0.0;
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    int i = threadIdx.x;
+    if (i < j) {
+      double acc = 0.0;
+      for (int l = i; l < j; ++l) acc += T[i * ldt + l] * G[l * ldg + j];
+      tcol[i] = -tau[j] * acc;
+    }
+    __syncthreads();
+    if (i < j) T[i * ldt + j] = tcol[i];
+    if (i == j) T[j * ldt + j] = tau[j];
+    __syncthreads();
+  }
+}
+
+size_t eig_work_bytes(int n) {
+  size_t nn = (size_t)n * n;
+  size_t doubles = nn /*A*/ + nn /*Vst*/ + 4 * (size_t)n /*d e e2 tau*/ + 2 * (size_t)n /*pbuf*/ +
+                   5 * nn /*lu*/ + 2 * (size_t)kBtBlock * kBtBlock + 2 * (size_t)kBtBlock * n + 16;
+  return doubles * sizeof(double) + 64 + (size_t)n * sizeof(int) + 256;
+}
+
+void eig_work_bind(EigWork& w, void* base, int n) {
+  size_t nn = (size_t)n * n;
+  double* p = (double*)base;
+  w.A = p; p += nn;
+  w.Vst = p; p += nn;
+  w.d = p; p += n;
+  w.e = p; p += n;
+  w.e2 = p; p += n;
+  w.tau = p; p += n;
+  w.pbuf = p; p += 2 * (size_t)n;
+  w.lu = p; p += 5 * nn;
+  w.Tm = p; p += (size_t)kBtBlock * kBtBlock;
+  w.Gm = p; p += (size_t)kBtBlock * kBtBlock;
+  w.Wt = p; p += (size_t)kBtBlock * n;
+  w.Wt2 = p; p += (size_t)kBtBlock * n;
+  w.scal = p; p += 16;
+  w.bar = (unsigned*)p; p += 8;
+  w.clus = (int*)p;
+}
+
+int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* status, int sm_count) {
+  if (n <= 0) return 0;
+  cudaMemcpyAsync(w.A, F, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s);
+  cudaMemsetAsync(w.e, 0, (size_t)n * sizeof(double), s);
+  // 1. tridiagonalisation
+  long long work = (long long)n * n;
+  int blocks = (int)((work + (1 << 16) - 1) >> 16);
+  if (blocks < 1) blocks = 1;
+  if (blocks > sm_count) blocks = sm_count;
+  size_t smem = (3 * (size_t)n + 32) * sizeof(double);
+  static size_t smem_set = 0;
+  if (smem > 48 * 1024 && smem > smem_set) {
+    if (cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return -1;
+    smem_set = smem;
+  }
+  {
+    int nn = n;
+    double *A = w.A, *V = w.Vst, *d = w.d, *e = w.e, *t = w.tau, *pb = w.pbuf;
+    unsigned* bar = w.bar;
+    int* st = status;
+    void* args[] = {&nn, &A, &V, &d, &e, &t, &pb, &bar, &st};
+    if (cudaLaunchCooperativeKernel((void*)tridiag_kernel, dim3(blocks), dim3(kTriThreads), args, smem, s) !=
+        cudaSuccess)
+      return -2;
+    count_launch();
+  }
+  return 0;
+}
+
+void eig_tridiagonal_solve(cudaStream_t s, int n, double* eps, double* Q, EigWork& w) {
+  if (n <= 0) return;
+  // 2. eigenvalues
+  gersh_kernel<<<1, 1024, 0, s>>>(n, w.d, w.e, w.e2, w.scal);
+  count_launch();
+  bisect_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, w.d, w.e2, w.scal, eps);
+  count_launch();
+  // 3. eigenvectors of the tridiagonal matrix
+  cluster_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, eps, w.scal, w.clus);
+  count_launch();
+  invit_kernel<<<(n + 63) / 64, 64, 0, s>>>(n, w.d, w.e, eps, w.scal, w.clus, w.lu, Q);
+  count_launch();
+}
+
+void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w) {
+  // 4. back-transformation, last block of reflectors first
+  int nref = n - 2;
+  if (nref > 0) {
+    int nblk = (nref + kBtBlock - 1) / kBtBlock;
+    for (int b = nblk - 1; b >= 0; --b) {
+      int k0 = b * kBtBlock, k1 = (k0 + kBtBlock < nref) ? k0 + kBtBlock : nref;
+      int kb = k1 - k0, c0 = k0 + 1, m = n - c0;
+      const double* Vb = w.Vst + (size_t)k0 * n + c0;
+      dgemm(s, 0, 1, kb, kb, m, 1.0, Vb, n, Vb, n, 0.0, w.Gm, kBtBlock);
+      tfactor_kernel<<<1, kBtBlock, 0, s>>>(kb, w.tau + k0, w.Gm, kBtBlock, w.Tm, kBtBlock);
+      count_launch();
+      dgemm(s, 0, 0, kb, n, m, 1.0, Vb, n, Q + (size_t)c0 * n, n, 0.0, w.Wt, n);
+      dgemm(s, 0, 0, kb, n, kb, 1.0, w.Tm, kBtBlock, w.Wt, n, 0.0, w.Wt2, n);
+      dgemm(s, 1, 0, m, n, kb, -1.0, Vb, n, w.Wt2, n, 1.0, Q + (size_t)c0 * n, n);
+    }
+  }
+}
+
+int symmetric_eig(cudaStream_t s, int n, const double* F, double* eps, double* Q, EigWork& w,
+                  int* status, int sm_count) {
+  int rc = eig_tridiagonalize(s, n, F, w, status, sm_count);
+  if (rc) return rc;
+  eig_tridiagonal_solve(s, n, eps, Q, w);
+  eig_backtransform(s, n, Q, w);
+  return 0;
+}
+
+}  // namespace kx

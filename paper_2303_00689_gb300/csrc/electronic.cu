@@ -1,0 +1,552 @@
+// Fermi occupations and chemical potential (eqs. 7, 8), entropy (eq. 4),
+// the element-wise step of the DMPT response (eq. 36), energies (eq. 13),
+// Krylov kernel pieces (eqs. 31-34), the X update (eq. 35) and the nuclear
+// velocity Verlet pieces (eqs. 27, 28, 30).
+//
+// Every reduction runs in a fixed order (per-block tree, then a single block
+// over the partials), so results do not depend on scheduling.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace kx {
+
+constexpr int kRedBlocks = 264;     // partial sums per reduction (multiple of SM pairs)
+constexpr int kRedThreads = 256;
+constexpr int kMaxDots = 24;
+
+__device__ __forceinline__ double fermi_occ(double eps, double mu, double beta) {
+  return 0.5 * (1.0 - tanh(0.5 * beta * (eps - mu)));
+}
+
+// ---- chemical potential and occupations (one block) -------------------------
+__global__ void fermi_kernel(int n, const double* __restrict__ eps, double nocc, double beta,
+                             double* __restrict__ f, Scalars* sc) {
+  __shared__ double red[32];
+  double lo = eps[0] - 40.0 / beta, hi = eps[n - 1] + 40.0 / beta;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    double loc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) loc += fermi_occ(eps[i], mid, beta);
+    double s = block_sum(loc, red);
+    if (s > nocc) hi = mid; else lo = mid;
+    if (hi - lo < 1e-15 * fmax(1.0, fabs(mid))) break;
+  }
+  double mu = 0.5 * (lo + hi);
+  for (int it = 0; it < 3; ++it) {
+    double l1 = 0.0, l2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double fi = fermi_occ(eps[i], mu, beta);
+      l1 += fi;
+      l2 += fi * (1.0 - fi);
+    }
+    double s = block_sum(l1, red);
+    double dn = beta * block_sum(l2, red);
+    if (dn < 1e-300) break;
+    double step = (nocc - s) / dn;
+    if (!isfinite(step) || fabs(step) > 1.0 / beta) break;
+    mu += step;
+  }
+  double ls = 0.0, ll = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double fi = fermi_occ(eps[i], mu, beta);
+    f[i] = fi;
+    if (fi > 0.0 && fi < 1.0) ls += fi * log(fi) + (1.0 - fi) * log(1.0 - fi);
+    ll += -beta * fi * (1.0 - fi);
+  }
+  double S = -kBoltz * block_sum(ls, red);
+  double sl = block_sum(ll, red);
+  if (threadIdx.x == 0) {
+    sc->mu = mu;
+    sc->entropy = S;
+    sc->sum_lam = sl;
+    int no = (int)(nocc + 0.5);
+    sc->gap = (no >= 1 && no < n) ? eps[no] - eps[no - 1] : 0.0;
+  }
+}
+
+void launch_fermi(cudaStream_t s, int n, const double* eps, double nocc, double beta, double* f,
+                  Scalars* sc) {
+  fermi_kernel<<<1, 1024, 0, s>>>(n, eps, nocc, beta, f, sc);
+  count_launch();
+}
+
+__global__ void scale_columns_kernel(int n, const double* __restrict__ Q, const double* __restrict__ f,
+                                     double* __restrict__ Qs) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * n) return;
+  int j = (int)(t % n);
+  Qs[t] = Q[t] * ::sqrt(fmax(f[j], 0.0));
+}
+
+void launch_scale_columns(cudaStream_t s, int n, const double* Q, const double* f, double* Qs) {
+  size_t tot = (size_t)n * n;
+  scale_columns_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, Q, f, Qs);
+  count_launch();
+}
+
+__global__ void transpose_kernel(int n, const double* __restrict__ A, double* __restrict__ At) {
+  __shared__ double tile[32][33];
+  int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int i = i0 + r, j = j0 + threadIdx.x;
+    tile[r][threadIdx.x] = (i < n && j < n) ? A[(size_t)i * n + j] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int j = j0 + r, i = i0 + threadIdx.x;
+    if (i < n && j < n) At[(size_t)j * n + i] = tile[threadIdx.x][r];
+  }
+}
+
+void launch_transpose(cudaStream_t s, int n, const double* A, double* At) {
+  int t = (n + 31) / 32;
+  transpose_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(n, A, At);
+  count_launch();
+}
+
+// ---- DMPT (eq. 36) -------------------------------------------------------------
+__device__ __forceinline__ double lambda_ij(double ei, double ej, double fi, double fj, double mu,
+                                            double beta) {
+  double de = ei - ej;
+  if (beta * fabs(de) < 1e-5) {
+    double fm = fermi_occ(0.5 * (ei + ej), mu, beta);
+    return -beta * fm * (1.0 - fm);
+  }
+  return (fi - fj) / de;
+}
+
+__global__ void dmu_kernel(int n, const double* __restrict__ F1p, const double* __restrict__ eps,
+                           const double* __restrict__ f, double beta, Scalars* sc) {
+  __shared__ double red[32];
+  if (!sc->active) return;
+  double mu = sc->mu;
+  double num = 0.0, den = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double l = lambda_ij(eps[i], eps[i], f[i], f[i], mu, beta);
+    num += l * F1p[(size_t)i * n + i];
+    den += l;
+  }
+  num = block_sum(num, red);
+  den = block_sum(den, red);
+  if (threadIdx.x == 0) sc->dmu = (fabs(den) > 1e-300) ? num / den : 0.0;
+}
+
+void launch_dmu(cudaStream_t s, int n, const double* F1p, const double* eps, const double* f, double beta,
+                Scalars* sc) {
+  dmu_kernel<<<1, 1024, 0, s>>>(n, F1p, eps, f, beta, sc);
+  count_launch();
+}
+
+__global__ void dmpt_y_kernel(int n, const double* __restrict__ F1p, const double* __restrict__ eps,
+                              const double* __restrict__ f, double beta, const Scalars* sc,
+                              double* __restrict__ Y) {
+  if (!sc->active) return;
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * n) return;
+  int i = (int)(t / n), j = (int)(t % n);
+  double v = F1p[t];
+  if (i == j) v -= sc->dmu;
+  Y[t] = lambda_ij(eps[i], eps[j], f[i], f[j], sc->mu, beta) * v;
+}
+
+void launch_dmpt_y(cudaStream_t s, int n, const double* F1p, const double* eps, const double* f,
+                   double beta, const Scalars* sc, double* Y) {
+  size_t tot = (size_t)n * n;
+  dmpt_y_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, F1p, eps, f, beta, sc, Y);
+  count_launch();
+}
+
+// ---- deterministic multi-dot -------------------------------------------------------
+struct DotArgs {
+  const double* a[kMaxDots];
+  const double* b[kMaxDots];
+};
+
+__global__ void dots_partial_kernel(size_t len, int cnt, DotArgs args, double* __restrict__ partial) {
+  __shared__ double red[32];
+  for (int k = 0; k < cnt; ++k) {
+    const double* a = args.a[k];
+    const double* b = args.b[k];
+    double loc = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+      loc += a[i] * b[i];
+    double s = block_sum(loc, red);
+    if (threadIdx.x == 0) partial[k * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void dots_final_kernel(int cnt, int nparts, const double* __restrict__ partial,
+                                  double* __restrict__ out) {
+  __shared__ double red[32];
+  for (int k = 0; k < cnt; ++k) {
+    double loc = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) loc += partial[k * nparts + i];
+    double s = block_sum(loc, red);
+    if (threadIdx.x == 0) out[k] = s;
+  }
+}
+
+static void dots(cudaStream_t s, size_t len, int cnt, const double* const* A, const double* const* B,
+                 double* out, double* partial) {
+  DotArgs args;
+  for (int k = 0; k < cnt; ++k) { args.a[k] = A[k]; args.b[k] = B[k]; }
+  dots_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(len, cnt, args, partial);
+  count_launch();
+  dots_final_kernel<<<1, kRedThreads, 0, s>>>(cnt, kRedBlocks, partial, out);
+  count_launch();
+}
+
+void launch_dots(cudaStream_t s, size_t len, int cnt, const double* const* A, const double* const* B,
+                 double* out, double* partial) {
+  dots(s, len, cnt, A, B, out, partial);
+}
+
+// ---- energies (eq. 13) ---------------------------------------------------------------
+__global__ void energy_partial_kernel(size_t len, int npair, const double* __restrict__ h,
+                                      const double* __restrict__ D, const double* __restrict__ X,
+                                      const double* __restrict__ F, const double* __restrict__ E,
+                                      double* __restrict__ partial) {
+  __shared__ double red[32];
+  double loc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+    loc += 2.0 * h[i] * D[i] + (2.0 * D[i] - X[i]) * (F[i] - h[i]);
+  double s = block_sum(loc, red);
+  double le = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npair; i += gridDim.x * blockDim.x) le += E[i];
+  double se = block_sum(le, red);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    partial[gridDim.x + blockIdx.x] = se;
+  }
+}
+
+__global__ void energy_final_kernel(int nparts, const double* __restrict__ partial, Scalars* sc) {
+  __shared__ double red[32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) { a += partial[i]; b += partial[nparts + i]; }
+  a = block_sum(a, red);
+  b = block_sum(b, red);
+  if (threadIdx.x == 0) { sc->e_elec = a; sc->vnn = b; }
+}
+
+void launch_energy(cudaStream_t s, int n, int npair, const double* h, const double* D, const double* X,
+                   const double* F, const double* E, Scalars* sc, double* part) {
+  energy_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>((size_t)n * n, npair, h, D, X, F, E, part);
+  count_launch();
+  energy_final_kernel<<<1, kRedThreads, 0, s>>>(kRedBlocks, part, sc);
+  count_launch();
+}
+
+// ---- Krylov kernel (eqs. 31-34) --------------------------------------------------------
+__global__ void krylov_start_kernel(size_t len, const double* __restrict__ D, const double* __restrict__ X,
+                                    double* __restrict__ W0) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < len) W0[t] = D[t] - X[t];
+}
+
+__global__ void krylov_start_final(const double* n2, Scalars* sc) {
+  sc->w0n2 = n2[0];
+  sc->res2 = n2[0];
+  sc->rank = 0;
+  sc->fit = 1.0;
+  sc->active = (n2[0] >= 1e-28) ? 1 : 0;   // ||W0|| >= 1e-14
+  for (int i = 0; i < 16; ++i) sc->c[i] = 0.0;
+}
+
+void launch_krylov_start(cudaStream_t s, size_t len, const double* D, const double* X, double* W0,
+                         Scalars* sc, double* partial) {
+  krylov_start_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, D, X, W0);
+  count_launch();
+  const double* a[1] = {W0};
+  double* tmp = partial + kRedBlocks * kMaxDots;  // small result area after the partials
+  dots(s, len, 1, a, a, tmp, partial);
+  krylov_start_final<<<1, 1, 0, s>>>(tmp, sc);
+  count_launch();
+}
+
+struct PtrList {
+  const double* p[16];
+};
+
+// v = src - sum_i coef[i] V_i   (coef on the device)
+__global__ void sub_combo_kernel(size_t len, int k, PtrList V, const double* __restrict__ coef,
+                                 const double* __restrict__ src, double* __restrict__ v, const Scalars* sc) {
+  if (!sc->active) return;
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= len) return;
+  double x = src[t];
+  for (int i = 0; i < k; ++i) x -= coef[i] * V.p[i][t];
+  v[t] = x;
+}
+
+__global__ void normalize_kernel(size_t len, double* __restrict__ v, const double* __restrict__ nrm,
+                                 Scalars* sc) {
+  // nrm[0] = ||v||^2, nrm[1] = ||src||^2
+  if (!sc->active) return;
+  double nv = ::sqrt(nrm[0]), ns = ::sqrt(nrm[1]);
+  if (nv < 1e-10 * ns || nv == 0.0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->active = 0;   // breakdown: invariant subspace
+    return;
+  }
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < len) v[t] = v[t] / nv;
+}
+
+// k = number of existing vectors V_0..V_{k-1}; src -> v orthonormalised (CGS twice)
+void launch_krylov_orth(cudaStream_t s, size_t len, int k, double* const* Vs, const double* src, double* v,
+                        Scalars* sc, double* partial, double* coef) {
+  PtrList V;
+  for (int i = 0; i < k; ++i) V.p[i] = Vs[i];
+  unsigned nb = (unsigned)((len + 255) / 256);
+  const double* cur = src;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (k > 0) {
+      const double* a[16];
+      const double* b[16];
+      for (int i = 0; i < k; ++i) { a[i] = Vs[i]; b[i] = cur; }
+      dots(s, len, k, a, b, coef, partial);
+    }
+    sub_combo_kernel<<<nb, 256, 0, s>>>(len, k, V, coef, cur, v, sc);
+    count_launch();
+    cur = v;
+  }
+  const double* a2[2] = {v, src};
+  dots(s, len, 2, a2, a2, coef + 16, partial);
+  normalize_kernel<<<nb, 256, 0, s>>>(len, v, coef + 16, sc);
+  count_launch();
+}
+
+__global__ void wk_kernel(size_t len, const double* __restrict__ D1, const double* __restrict__ v,
+                          double* __restrict__ Wk, const Scalars* sc) {
+  if (!sc->active) return;
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < len) Wk[t] = D1[t] - v[t];
+}
+
+// dots[0..k]: <W_k, W_j> j = 0..k (W indices 0-based), dots[k+1] = <W_k, W0>
+__global__ void gram_solve_kernel(int k, const double* __restrict__ dv, Scalars* sc, double tol, int m_min) {
+  if (!sc->active) return;
+  int m = k + 1;
+  for (int j = 0; j <= k; ++j) {
+    sc->O[k * 16 + j] = dv[j];
+    sc->O[j * 16 + k] = dv[j];
+  }
+  sc->b[k] = dv[k + 1];
+  // Cholesky of O (m x m); Gaussian elimination with pivoting if it fails
+  double L[16][16], y[16], c[16];
+  bool spd = true;
+  for (int i = 0; i < m && spd; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double acc = sc->O[i * 16 + j];
+      for (int l = 0; l < j; ++l) acc -= L[i][l] * L[j][l];
+      if (i == j) {
+        if (acc <= 0.0) { spd = false; break; }
+        L[i][i] = ::sqrt(acc);
+      } else {
+        L[i][j] = acc / L[j][j];
+      }
+    }
+  }
+  if (spd) {
+    for (int i = 0; i < m; ++i) {
+      double acc = sc->b[i];
+      for (int l = 0; l < i; ++l) acc -= L[i][l] * y[l];
+      y[i] = acc / L[i][i];
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      double acc = y[i];
+      for (int l = i + 1; l < m; ++l) acc -= L[l][i] * c[l];
+      c[i] = acc / L[i][i];
+    }
+  } else {
+    double M[16][17];
+    for (int i = 0; i < m; ++i) {
+      for (int j = 0; j < m; ++j) M[i][j] = sc->O[i * 16 + j];
+      M[i][m] = sc->b[i];
+    }
+    for (int col = 0; col < m; ++col) {
+      int p = col;
+      for (int r = col + 1; r < m; ++r)
+        if (fabs(M[r][col]) > fabs(M[p][col])) p = r;
+      for (int j = 0; j <= m; ++j) { double t = M[col][j]; M[col][j] = M[p][j]; M[p][j] = t; }
+      double piv = M[col][col];
+      if (fabs(piv) < 1e-300) piv = 1e-300;
+      for (int r = col + 1; r < m; ++r) {
+        double f = M[r][col] / piv;
+        for (int j = col; j <= m; ++j) M[r][j] -= f * M[col][j];
+      }
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      double acc = M[i][m];
+      for (int j = i + 1; j < m; ++j) acc -= M[i][j] * c[j];
+      double piv = fabs(M[i][i]) < 1e-300 ? 1e-300 : M[i][i];
+      c[i] = acc / piv;
+    }
+  }
+  double cOc = 0.0, cb = 0.0;
+  for (int i = 0; i < m; ++i) {
+    cb += c[i] * sc->b[i];
+    for (int j = 0; j < m; ++j) cOc += c[i] * sc->O[i * 16 + j] * c[j];
+  }
+  double r2 = cOc - 2.0 * cb + sc->w0n2;
+  double fit = ::sqrt(fmax(r2, 0.0) / sc->w0n2);
+  for (int i = 0; i < m; ++i) sc->c[i] = c[i];
+  sc->fit = fit;
+  sc->rank = m;
+  if (m >= m_min && fit < tol) sc->active = 0;
+}
+
+void launch_krylov_w(cudaStream_t s, size_t len, int k, const double* D1, const double* v, double* Wk,
+                     double* const* Ws, const double* W0, Scalars* sc, double* partial, double tol,
+                     int m_min) {
+  unsigned nb = (unsigned)((len + 255) / 256);
+  wk_kernel<<<nb, 256, 0, s>>>(len, D1, v, Wk, sc);
+  count_launch();
+  const double* a[18];
+  const double* b[18];
+  for (int j = 0; j <= k; ++j) { a[j] = Wk; b[j] = Ws[j]; }
+  a[k + 1] = Wk;
+  b[k + 1] = W0;
+  double* dv = partial + kRedBlocks * kMaxDots + 32;
+  dots(s, len, k + 2, a, b, dv, partial);
+  gram_solve_kernel<<<1, 1, 0, s>>>(k, dv, sc, tol, m_min);
+  count_launch();
+}
+
+__global__ void combine_kernel(size_t len, int mmax, PtrList V, const Scalars* sc, double* __restrict__ K) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= len) return;
+  int r = sc->rank;
+  double acc = 0.0;
+  for (int i = 0; i < r && i < mmax; ++i) acc += sc->c[i] * V.p[i][t];
+  K[t] = acc;
+}
+
+void launch_krylov_combine(cudaStream_t s, size_t len, int mmax, double* const* Vs, Scalars* sc, double* K) {
+  PtrList V;
+  for (int i = 0; i < mmax; ++i) V.p[i] = Vs[i];
+  combine_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, mmax, V, sc, K);
+  count_launch();
+}
+
+// ---- X update (eq. 35) ------------------------------------------------------------------
+struct XHist {
+  const double* x[7];
+};
+__constant__ double c_ck[7] = {-14.0, 36.0, -27.0, -2.0, 12.0, -6.0, 1.0};
+
+__global__ void x_update_kernel(size_t len, XHist h, const double* __restrict__ K, double kappa, double alpha,
+                                double* __restrict__ Xn) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= len) return;
+  double x = 2.0 * h.x[0][t] - h.x[1][t] - kappa * K[t];
+  double damp = 0.0;
+  for (int k = 0; k < 7; ++k) damp += c_ck[k] * h.x[k][t];
+  Xn[t] = x + alpha * damp;
+}
+
+void launch_x_update(cudaStream_t s, size_t len, double* const* Xh, const double* K, double kappa, double alpha,
+                     double* Xnew) {
+  XHist h;
+  for (int k = 0; k < 7; ++k) h.x[k] = Xh[k];
+  x_update_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, h, K, kappa, alpha, Xnew);
+  count_launch();
+}
+
+// ---- nuclei (eqs. 27, 28, 30) ---------------------------------------------------------------
+__global__ void half_kick_kernel(int N, double* __restrict__ V, const double* __restrict__ F,
+                                 const double* __restrict__ mass, double dt) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * N) return;
+  V[t] += 0.5 * dt * kAccel * F[t] / mass[t / 3];
+}
+__global__ void drift_kernel(int N, double* __restrict__ R, const double* __restrict__ V, double dt) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * N) return;
+  R[t] += dt * V[t];
+}
+__global__ void kinetic_kernel(int N, const double* __restrict__ V, const double* __restrict__ mass, Scalars* sc) {
+  __shared__ double red[32];
+  double loc = 0.0;
+  for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) loc += 0.5 * mass[t / 3] * V[t] * V[t] / kAccel;
+  double s = block_sum(loc, red);
+  if (threadIdx.x == 0) sc->e_kin = s;
+}
+
+void launch_half_kick(cudaStream_t s, int N, double* V, const double* F, const double* mass, double dt) {
+  half_kick_kernel<<<(3 * N + 255) / 256, 256, 0, s>>>(N, V, F, mass, dt);
+  count_launch();
+}
+void launch_drift(cudaStream_t s, int N, double* R, const double* V, double dt) {
+  drift_kernel<<<(3 * N + 255) / 256, 256, 0, s>>>(N, R, V, dt);
+  count_launch();
+}
+void launch_kinetic(cudaStream_t s, int N, const double* V, const double* mass, Scalars* sc) {
+  kinetic_kernel<<<1, 256, 0, s>>>(N, V, mass, sc);
+  count_launch();
+}
+
+__global__ void check_finite_kernel(size_t len, const double* __restrict__ a, Scalars* sc) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  for (; t < len; t += (size_t)gridDim.x * blockDim.x) bad |= !isfinite(a[t]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&sc->status, (int)kStatusNumeric);
+}
+void launch_check_finite(cudaStream_t s, size_t len, const double* a, Scalars* sc) {
+  check_finite_kernel<<<kRedBlocks, 256, 0, s>>>(len, a, sc);
+  count_launch();
+}
+
+__global__ void fill_kernel(size_t len, double* a, double v) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < len) a[t] = v;
+}
+void launch_fill(cudaStream_t s, size_t len, double* a, double v) {
+  fill_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, a, v);
+  count_launch();
+}
+
+__global__ void axpby_kernel(size_t len, double a, const double* __restrict__ x, double b,
+                             const double* __restrict__ y, double* __restrict__ out) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < len) out[t] = a * x[t] + b * y[t];
+}
+void launch_axpby(cudaStream_t s, size_t len, double a, const double* x, double b, const double* y, double* out) {
+  axpby_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, a, x, b, y, out);
+  count_launch();
+}
+
+__global__ void maxabs_partial_kernel(size_t len, const double* __restrict__ a, const double* __restrict__ b,
+                                      double* __restrict__ partial) {
+  double m = 0.0;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (size_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(a[t] - b[t]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, sm[i]);
+    partial[blockIdx.x] = fmax(m, sm[0]);
+  }
+}
+__global__ void maxabs_final_kernel(int np, const double* __restrict__ partial, double* out) {
+  double m = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) m = fmax(m, partial[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, sm[i]);
+    *out = m;
+  }
+}
+void launch_maxabs_diff(cudaStream_t s, size_t len, const double* a, const double* b, double* out, double* partial) {
+  maxabs_partial_kernel<<<kRedBlocks, 256, 0, s>>>(len, a, b, partial);
+  count_launch();
+  maxabs_final_kernel<<<1, 256, 0, s>>>(kRedBlocks, partial, out);
+  count_launch();
+}
+
+}  // namespace kx

@@ -1,0 +1,117 @@
+// Host-side launchers of the library's CUDA kernels (internal header).
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace kx {
+
+// ---- pairs.cu ---------------------------------------------------------------
+bool upload_overlap_tables();
+void launch_pair_values(cudaStream_t s, int npair, const int* pA, const int* pB, const int* elem,
+                        const double* R, const ElemTable& tab, double* W, double* S, double* E);
+void launch_pair_derivs(cudaStream_t s, int npair, const int* pA, const int* pB, const int* elem,
+                        const double* R, const ElemTable& tab, double* W, double* S, double* E,
+                        double* dW, double* dS, double* dE);
+
+// ---- fock.cu ----------------------------------------------------------------
+struct MolDev {          // read-only molecule description on the device
+  int N, n, npair;
+  const int* elem;       // element index per atom (0 H, 1 C, 2 N, 3 O)
+  const int* off;        // first orbital of each atom (N + 1 entries)
+  const int* pA;         // pair -> first atom (A < B)
+  const int* pB;         // pair -> second atom
+};
+struct PairDev {         // pair blocks (SoA, stride npair)
+  const double *W, *S, *E, *dW, *dS, *dE;
+};
+
+// out[N][10]: diagonal 4x4 block of M per atom, packed by orbital product
+void launch_pack_diag(cudaStream_t s, const MolDev& m, const double* M, double* out);
+// core Hamiltonian h (dense, symmetric)
+void launch_build_h(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,
+                    double* h);
+// out = (h ? h : 0) + G(P) (eq. 3 with NDDO integrals); Pd = packed diagonal blocks of P
+void launch_build_fock(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,
+                       const double* P, const double* Pd, const double* h, double* out);
+// per-pair gradient contributions g[3][npair] (eq. 37) and per-atom forces
+void launch_forces(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,
+                   const double* D, const double* P, const double* Dd, const double* Pd,
+                   double* g, double* forces);
+
+// ---- gemm64.cu --------------------------------------------------------------
+// Row-major C = alpha op(A) op(B) + beta C.  ta/tb: 0 = as stored, 1 = transposed.
+// sym != 0: C is symmetric; only tiles on or above the diagonal are computed
+// and each value is written to (i, j) and (j, i) (bitwise symmetric result).
+void dgemm(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha, const double* A,
+           int lda, const double* B, int ldb, double beta, double* C, int ldc, int sym = 0);
+
+// ---- eig.cu -----------------------------------------------------------------
+struct EigWork {
+  double *A;            // n x n copy of the input (overwritten)
+  double *Vst;          // n x n Householder vectors (row k = v_k)
+  double *d, *e, *e2, *tau;
+  double *pbuf;         // 2 x n
+  double *lu;           // 5 x n x n inverse-iteration workspace
+  double *Tm, *Gm, *Wt, *Wt2;  // back-transform panels
+  unsigned* bar;        // 2 words grid barrier
+  int* clus;            // cluster starts
+  double* scal;         // scalars (Gershgorin bounds, norm)
+};
+size_t eig_work_bytes(int n);
+void eig_work_bind(EigWork& w, void* base, int n);
+// F (n x n symmetric, row-major) -> eps ascending, Q (eigenvectors as columns),
+// in three stages (tridiagonalise; tridiagonal eigenpairs into Q; back-transform Q)
+int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* status, int sm_count);
+void eig_tridiagonal_solve(cudaStream_t s, int n, double* eps, double* Q, EigWork& w);
+void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w);
+int symmetric_eig(cudaStream_t s, int n, const double* F, double* eps, double* Q, EigWork& w,
+                  int* status, int sm_count);
+
+// ---- electronic.cu ----------------------------------------------------------
+struct Scalars {         // device-resident per-evaluation scalars
+  double mu, entropy, gap, sum_lam, dmu;
+  double e_elec, vnn, e_kin, res2, fit;
+  double O[16 * 16], b[16], c[16], w0n2;
+  int rank, active, status, pad;
+};
+void launch_fermi(cudaStream_t s, int n, const double* eps, double nocc, double beta, double* f,
+                  Scalars* sc);
+void launch_scale_columns(cudaStream_t s, int n, const double* Q, const double* f, double* Qs);
+void launch_transpose(cudaStream_t s, int n, const double* A, double* At);
+void launch_dmu(cudaStream_t s, int n, const double* F1p, const double* eps, const double* f,
+                double beta, Scalars* sc);
+void launch_dmpt_y(cudaStream_t s, int n, const double* F1p, const double* eps, const double* f,
+                   double beta, const Scalars* sc, double* Y);
+// U = 2 Tr[h D] + Tr[(2D - X)(F - h)] and V_nn = sum E_pair
+void launch_energy(cudaStream_t s, int n, int npair, const double* h, const double* D,
+                   const double* X, const double* F, const double* E, Scalars* sc, double* partial);
+// size in doubles of the reduction workspace ("partial") the launchers above expect
+constexpr size_t kReduceWorkDoubles = 264 * 24 + 128;
+// out[k] = <A_k, B_k> over n*n elements for k < cnt (deterministic)
+void launch_dots(cudaStream_t s, size_t len, int cnt, const double* const* A, const double* const* B,
+                 double* out, double* partial);
+// Krylov pieces
+void launch_krylov_start(cudaStream_t s, size_t len, const double* D, const double* X, double* W0,
+                         Scalars* sc, double* partial);
+void launch_krylov_orth(cudaStream_t s, size_t len, int k, double* const* Vs, const double* src,
+                        double* v, Scalars* sc, double* partial, double* coef);
+void launch_krylov_w(cudaStream_t s, size_t len, int k, const double* D1, const double* v, double* Wk,
+                     double* const* Ws, const double* W0, Scalars* sc, double* partial, double tol,
+                     int m_min);
+void launch_krylov_combine(cudaStream_t s, size_t len, int mmax, double* const* Vs, Scalars* sc,
+                           double* K);
+void launch_x_update(cudaStream_t s, size_t len, double* const* Xh /*7 ptrs, k = 0..6*/,
+                     const double* K, double kappa, double alpha, double* Xnew);
+// nuclei
+void launch_half_kick(cudaStream_t s, int N, double* V, const double* F, const double* mass,
+                      double dt);
+void launch_drift(cudaStream_t s, int N, double* R, const double* V, double dt);
+void launch_kinetic(cudaStream_t s, int N, const double* V, const double* mass, Scalars* sc);
+void launch_check_finite(cudaStream_t s, size_t len, const double* a, Scalars* sc);
+void launch_fill(cudaStream_t s, size_t len, double* a, double v);
+void launch_axpby(cudaStream_t s, size_t len, double a, const double* x, double b, const double* y,
+                  double* out);
+void launch_maxabs_diff(cudaStream_t s, size_t len, const double* a, const double* b, double* out,
+                        double* partial);
+
+}  // namespace kx

@@ -1,0 +1,401 @@
+// NDDO two-centre quantities for every atom pair A < B, and their derivatives
+// with respect to the pair vector d = R_B - R_A.
+//
+// Model (MNDO multipole form; the paper names the AM1/MNDO/PM3 Hamiltonians
+// in its Introduction and relies on NDDO, S = I, under eq. 6):
+//  * each orbital product is a set of point charges in the local frame with
+//    z' from A to B; two charges interact as e^2 q_i q_j /
+//    sqrt(r_ij^2 + (rho_i + rho_j)^2);
+//  * (p_pi p_pi'|p_pi p_pi') = [(p_pi p_pi|p_pi p_pi) - (p_pi p_pi|p_pi' p_pi')]/2
+//    keeps the rotated set independent of the choice of x';
+//  * the molecular-frame block is C I_loc C^T with C the 10x10 transform
+//    of orbital products built from the frame rotation;
+//  * resonance uses Slater overlaps from prolate spheroidal integrals;
+//  * core-core: Z'_A Z'_B (ss|ss)(1 + e^{-a_A R} + e^{-a_B R}) + AM1 Gaussians.
+//
+// Derivatives: the whole map d -> (W, S, E) is evaluated once in dual
+// numbers carrying d/dd_x, d/dd_y, d/dd_z (forward-mode differentiation), so
+// forces (eq. 37) need no second pass over the integrals.
+//
+// Layout of the outputs (structure of arrays, stride = npair):
+//   W[(p*10 + q) * npair + pair]   p: product on A, q: product on B
+//   S[(mu*4 + lam) * npair + pair] <A mu | B lam>
+//   E[pair]                        core-core energy
+//   dW[(k*100 + p*10 + q) * npair + pair], dS[(k*16 + ..)], dE[k*npair + pair]
+// Products: 0 ss, 1 sx, 2 sy, 3 sz, 4 xx, 5 yy, 6 zz, 7 xy, 8 xz, 9 yz.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace kx {
+
+__constant__ double c_ovl_poly[2][2][3][3][5][5];   // [nA-1][nB-1][kindA][kindB][xi^i][eta^j]
+__constant__ double c_ovl_phi[3];                    // phi factor per kindA (s, sigma, pi)
+
+__device__ __constant__ int c_prod_mu[10] = {0, 0, 0, 0, 1, 2, 3, 1, 1, 2};
+__device__ __constant__ int c_prod_nu[10] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
+// reflection parity class (x -> -x, y -> -y) of each product: integrals
+// between products of different classes vanish by symmetry
+__device__ __constant__ int c_prod_cls[10] = {0, 1, 2, 0, 0, 0, 0, 3, 1, 2};
+__device__ __constant__ int c_grp_lo[10] = {0, 1, 1, 1, 4, 4, 4, 4, 4, 4};
+__device__ __constant__ int c_grp_hi[10] = {1, 4, 4, 4, 10, 10, 10, 10, 10, 10};
+
+// point charges of product p on an atom (local frame), returns count
+__device__ __forceinline__ int product_charges(int p, const Elem& e, double q[4], double x[4],
+                                               double y[4], double z[4], double r[4]) {
+  for (int i = 0; i < 4; ++i) { q[i] = 0.0; x[i] = 0.0; y[i] = 0.0; z[i] = 0.0; r[i] = e.rho0; }
+  int a = c_prod_mu[p], b = c_prod_nu[p];
+  if (a == 0 && b == 0) { q[0] = 1.0; r[0] = e.rho0; return 1; }
+  if (a == 0) {
+    double* c0 = (b == 1) ? x : (b == 2) ? y : z;
+    q[0] = 0.5; c0[0] = e.D1; r[0] = e.rho1;
+    q[1] = -0.5; c0[1] = -e.D1; r[1] = e.rho1;
+    return 2;
+  }
+  if (a == b) {
+    double* c0 = (a == 1) ? x : (a == 2) ? y : z;
+    q[0] = 1.0; r[0] = e.rho0;
+    q[1] = 0.25; c0[1] = 2.0 * e.D2; r[1] = e.rho2;
+    q[2] = 0.25; c0[2] = -2.0 * e.D2; r[2] = e.rho2;
+    q[3] = -0.5; r[3] = e.rho2;
+    return 4;
+  }
+  double* ca = (a == 1) ? x : (a == 2) ? y : z;
+  double* cb = (b == 1) ? x : (b == 2) ? y : z;
+  const double sa[4] = {1.0, -1.0, 1.0, -1.0};
+  const double sb[4] = {1.0, -1.0, -1.0, 1.0};
+  for (int i = 0; i < 4; ++i) {
+    q[i] = 0.25 * sa[i] * sb[i];
+    ca[i] = sa[i] * e.D2;
+    cb[i] = sb[i] * e.D2;
+    r[i] = e.rho2;
+  }
+  return 4;
+}
+
+template <typename T>
+__device__ T local_integral(int p, int qd, const Elem& ea, const Elem& eb, T R) {
+  double qa[4], xa[4], ya[4], za[4], ra[4];
+  double qb[4], xb[4], yb[4], zb[4], rb[4];
+  int na = product_charges(p, ea, qa, xa, ya, za, ra);
+  int nb = product_charges(qd, eb, qb, xb, yb, zb, rb);
+  T acc = cst<T>(0.0);
+  for (int i = 0; i < na; ++i) {
+    for (int j = 0; j < nb; ++j) {
+      double dx = xa[i] - xb[j], dy = ya[i] - yb[j], rr = ra[i] + rb[j];
+      T dz = (za[i] - zb[j]) - R;
+      T s2 = dz * dz + (dx * dx + dy * dy + rr * rr);
+      acc += (qa[i] * qb[j]) * rsqrt_d(s2);
+    }
+  }
+  return acc * kE2;
+}
+
+// A_k(p) = int_1^inf xi^k e^{-p xi}, k = 0..4
+template <typename T>
+__device__ void aux_A(T p, T* A) {
+  T e = ex(-p);
+  T ip = 1.0 / p;
+  A[0] = e * ip;
+  for (int k = 1; k < 5; ++k) A[k] = (e + (double)k * A[k - 1]) * ip;
+}
+// B_k(q) = int_{-1}^{1} eta^k e^{-q eta}, k = 0..4
+template <typename T>
+__device__ void aux_B(T q, T* B) {
+  if (fabs(val(q)) < 1.0) {
+    for (int k = 0; k < 5; ++k) B[k] = cst<T>(0.0);
+    T term = cst<T>(1.0);
+    for (int m = 0; m < 22; ++m) {
+      for (int k = 0; k < 5; ++k)
+        if (((k + m) & 1) == 0) B[k] += term * (2.0 / (double)(k + m + 1));
+      term = term * (-q) * (1.0 / (double)(m + 1));
+    }
+  } else {
+    T ep = ex(q), em = ex(-q);
+    T iq = 1.0 / q;
+    B[0] = (ep - em) * iq;
+    for (int k = 1; k < 5; ++k) {
+      T sgn_ep = (k & 1) ? -ep : ep;
+      B[k] = (sgn_ep - em + (double)k * B[k - 1]) * iq;
+    }
+  }
+}
+
+__device__ __forceinline__ double sto_norm(int n, double zeta) {
+  double f2n = (n == 1) ? 2.0 : 24.0;  // (2n)!
+  return pow(2.0 * zeta, n + 0.5) / ::sqrt(f2n);
+}
+
+// overlap of normalised Slater orbitals, B at +R z'; kinds 0 s, 1 sigma, 2 pi
+template <typename T>
+__device__ T sto_overlap(T R, int nA, double zA, int kA, int nB, double zB, int kB) {
+  T Rb = R * (1.0 / kBohr);
+  T p = Rb * (0.5 * (zA + zB));
+  T q = Rb * (0.5 * (zA - zB));
+  T A[5], B[5];
+  aux_A(p, A);
+  aux_B(q, B);
+  T acc = cst<T>(0.0);
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      double c = c_ovl_poly[nA - 1][nB - 1][kA][kB][i][j];
+      if (c != 0.0) acc += c * (A[i] * B[j]);
+    }
+  const double cs = 0.28209479177387814;  // 1/sqrt(4 pi)
+  const double cp = 0.48860251190291992;  // sqrt(3/(4 pi))
+  double pref = sto_norm(nA, zA) * sto_norm(nB, zB) * (kA == 0 ? cs : cp) * (kB == 0 ? cs : cp) *
+                c_ovl_phi[kA];
+  T half = Rb * 0.5;
+  T pw = cst<T>(1.0);
+  for (int k = 0; k < nA + nB + 1; ++k) pw = pw * half;
+  return acc * pw * pref;
+}
+
+// independent variable k of the pair vector (derivative direction k)
+template <typename T> __device__ __forceinline__ T seed(double v, int k);
+template <> __device__ __forceinline__ double seed<double>(double v, int) { return v; }
+template <> __device__ __forceinline__ D3 seed<D3>(double v, int k) {
+  return D3{v, k == 0 ? 1.0 : 0.0, k == 1 ? 1.0 : 0.0, k == 2 ? 1.0 : 0.0};
+}
+
+template <typename T>
+__device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T* Wout /*100*/,
+                           T* Sout /*16*/, T* Eout) {
+  T d[3];
+  for (int k = 0; k < 3; ++k) d[k] = seed<T>(dvec[k], k);
+  T R = sq(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  T iR = 1.0 / R;
+  T u[3] = {d[0] * iR, d[1] * iR, d[2] * iR};
+  // reference axis least aligned with u
+  int ref = 0;
+  double best = fabs(val(u[0]));
+  if (fabs(val(u[1])) < best) { ref = 1; best = fabs(val(u[1])); }
+  if (fabs(val(u[2])) < best) { ref = 2; }
+  T au = u[ref];
+  T nrm = rsqrt_d(1.0 - au * au);
+  T fx[3], fy[3];   // local x' and y' axes
+  for (int k = 0; k < 3; ++k) fx[k] = ((k == ref ? cst<T>(1.0) : cst<T>(0.0)) - au * u[k]) * nrm;
+  fy[0] = u[1] * fx[2] - u[2] * fx[1];
+  fy[1] = u[2] * fx[0] - u[0] * fx[2];
+  fy[2] = u[0] * fx[1] - u[1] * fx[0];
+  // Tf[mu][mu']: molecular orbital slot mu in terms of local slot mu'
+  T Tf[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) Tf[a][b] = cst<T>(0.0);
+  Tf[0][0] = cst<T>(1.0);
+  for (int k = 0; k < 3; ++k) {
+    Tf[1 + k][1] = fx[k];
+    Tf[1 + k][2] = fy[k];
+    Tf[1 + k][3] = u[k];
+  }
+
+  const int pa = (ea.norb == 4) ? 10 : 1;
+  const int pb = (eb.norb == 4) ? 10 : 1;
+
+  // local integrals
+  T I[10][10];
+  for (int p = 0; p < 10; ++p)
+    for (int q = 0; q < 10; ++q) {
+      if (p < pa && q < pb && c_prod_cls[p] == c_prod_cls[q])
+        I[p][q] = local_integral<T>(p, q, ea, eb, R);
+      else
+        I[p][q] = cst<T>(0.0);
+    }
+  if (pa == 10 && pb == 10) I[7][7] = 0.5 * (I[4][4] - I[4][5]);
+
+  // product transform C[p][p'] (block diagonal over ss / sp / pp groups)
+  T C[10][10];
+  for (int p = 0; p < 10; ++p) {
+    int mu = c_prod_mu[p], nu = c_prod_nu[p];
+    for (int pp = c_grp_lo[p]; pp < c_grp_hi[p]; ++pp) {
+      int m2 = c_prod_mu[pp], n2 = c_prod_nu[pp];
+      if (m2 == n2)
+        C[p][pp] = Tf[mu][m2] * Tf[nu][m2];
+      else
+        C[p][pp] = Tf[mu][m2] * Tf[nu][n2] + Tf[mu][n2] * Tf[nu][m2];
+    }
+  }
+  // X[p'][q] = sum_{q'} I[p'][q'] C[q][q'];  W[p][q] = sum_{p'} C[p][p'] X[p'][q]
+  T X[10][10];
+  for (int pp = 0; pp < pa; ++pp)
+    for (int q = 0; q < pb; ++q) {
+      T acc = cst<T>(0.0);
+      for (int qq = c_grp_lo[q]; qq < c_grp_hi[q]; ++qq) acc += I[pp][qq] * C[q][qq];
+      X[pp][q] = acc;
+    }
+  for (int p = 0; p < 10; ++p)
+    for (int q = 0; q < 10; ++q) {
+      T acc = cst<T>(0.0);
+      if (p < pa && q < pb)
+        for (int pp = c_grp_lo[p]; pp < c_grp_hi[p]; ++pp) acc += C[p][pp] * X[pp][q];
+      Wout[p * 10 + q] = acc;
+    }
+
+  // overlaps in the local frame, then rotated
+  T Sl[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) Sl[a][b] = cst<T>(0.0);
+  Sl[0][0] = sto_overlap<T>(R, ea.nprin, ea.zeta[0], 0, eb.nprin, eb.zeta[0], 0);
+  if (ea.norb == 4) Sl[3][0] = sto_overlap<T>(R, ea.nprin, ea.zeta[1], 1, eb.nprin, eb.zeta[0], 0);
+  if (eb.norb == 4) Sl[0][3] = sto_overlap<T>(R, ea.nprin, ea.zeta[0], 0, eb.nprin, eb.zeta[1], 1);
+  if (ea.norb == 4 && eb.norb == 4) {
+    Sl[3][3] = sto_overlap<T>(R, ea.nprin, ea.zeta[1], 1, eb.nprin, eb.zeta[1], 1);
+    T spp = sto_overlap<T>(R, ea.nprin, ea.zeta[1], 2, eb.nprin, eb.zeta[1], 2);
+    Sl[1][1] = spp;
+    Sl[2][2] = spp;
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      T acc = cst<T>(0.0);
+      if (a < ea.norb && b < eb.norb)
+        for (int a2 = 0; a2 < 4; ++a2)
+          for (int b2 = 0; b2 < 4; ++b2)
+            acc += Tf[a][a2] * Tf[b][b2] * Sl[a2][b2];
+      Sout[a * 4 + b] = acc;
+    }
+
+  // core-core repulsion
+  T gss = I[0][0];
+  double zz = ea.zcore * eb.zcore;
+  T en = zz * gss * (1.0 + ex(-ea.alpha * R) + ex(-eb.alpha * R));
+  T g = cst<T>(0.0);
+  for (int k = 0; k < 2; ++k) {
+    T ta = R - ea.gc[k];
+    T tb = R - eb.gc[k];
+    g += ea.ga[k] * ex(-ea.gb[k] * (ta * ta)) + eb.ga[k] * ex(-eb.gb[k] * (tb * tb));
+  }
+  *Eout = en + zz * g * iR;
+}
+
+__global__ void pair_values_kernel(int npair, const int* __restrict__ pA, const int* __restrict__ pB,
+                                   const int* __restrict__ elem, const double* __restrict__ R,
+                                   ElemTable tab, double* __restrict__ W, double* __restrict__ S,
+                                   double* __restrict__ E) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npair) return;
+  int A = pA[t], B = pB[t];
+  double d[3] = {R[3 * B] - R[3 * A], R[3 * B + 1] - R[3 * A + 1], R[3 * B + 2] - R[3 * A + 2]};
+  const Elem& ea = tab.e[elem[A]];
+  const Elem& eb = tab.e[elem[B]];
+  double w[100], s[16], e;
+  pair_block<double>(d, ea, eb, w, s, &e);
+  for (int k = 0; k < 100; ++k) W[(size_t)k * npair + t] = w[k];
+  for (int k = 0; k < 16; ++k) S[(size_t)k * npair + t] = s[k];
+  E[t] = e;
+}
+
+__global__ void pair_derivs_kernel(int npair, const int* __restrict__ pA, const int* __restrict__ pB,
+                                   const int* __restrict__ elem, const double* __restrict__ R,
+                                   ElemTable tab, double* __restrict__ W, double* __restrict__ S,
+                                   double* __restrict__ E, double* __restrict__ dW,
+                                   double* __restrict__ dS, double* __restrict__ dE) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npair) return;
+  int A = pA[t], B = pB[t];
+  double d[3] = {R[3 * B] - R[3 * A], R[3 * B + 1] - R[3 * A + 1], R[3 * B + 2] - R[3 * A + 2]};
+  const Elem& ea = tab.e[elem[A]];
+  const Elem& eb = tab.e[elem[B]];
+  D3 w[100], s[16], e;
+  pair_block<D3>(d, ea, eb, w, s, &e);
+  size_t np = (size_t)npair;
+  for (int k = 0; k < 100; ++k) {
+    W[k * np + t] = w[k].v;
+    dW[(0 * 100 + k) * np + t] = w[k].d0;
+    dW[(1 * 100 + k) * np + t] = w[k].d1;
+    dW[(2 * 100 + k) * np + t] = w[k].d2;
+  }
+  for (int k = 0; k < 16; ++k) {
+    S[k * np + t] = s[k].v;
+    dS[(0 * 16 + k) * np + t] = s[k].d0;
+    dS[(1 * 16 + k) * np + t] = s[k].d1;
+    dS[(2 * 16 + k) * np + t] = s[k].d2;
+  }
+  E[t] = e.v;
+  dE[0 * np + t] = e.d0;
+  dE[1 * np + t] = e.d1;
+  dE[2 * np + t] = e.d2;
+}
+
+// ---------------------------------------------------------------------------
+// host side: overlap polynomial tables (built once per process)
+// ---------------------------------------------------------------------------
+namespace {
+struct Poly {
+  double c[9][9];
+  Poly() { for (auto& r : c) for (auto& x : r) x = 0.0; }
+};
+Poly pmul(const Poly& a, const Poly& b) {
+  Poly o;
+  for (int i = 0; i < 9; ++i)
+    for (int j = 0; j < 9; ++j)
+      if (a.c[i][j] != 0.0)
+        for (int k = 0; i + k < 9; ++k)
+          for (int l = 0; j + l < 9; ++l) o.c[i + k][j + l] += a.c[i][j] * b.c[k][l];
+  return o;
+}
+Poly mono(double c00, double c10, double c01, double c11, double c20, double c02) {
+  Poly p;
+  p.c[0][0] = c00; p.c[1][0] = c10; p.c[0][1] = c01; p.c[1][1] = c11; p.c[2][0] = c20; p.c[0][2] = c02;
+  return p;
+}
+Poly ppow(const Poly& a, int k) {
+  Poly o = mono(1, 0, 0, 0, 0, 0);
+  for (int i = 0; i < k; ++i) o = pmul(o, a);
+  return o;
+}
+}  // namespace
+
+bool upload_overlap_tables() {
+  static bool done = false;
+  if (done) return true;
+  double tab[2][2][3][3][5][5] = {};
+  const Poly vol = mono(0, 0, 0, 0, 1, -1);          // xi^2 - eta^2
+  const Poly rA = mono(0, 1, 1, 0, 0, 0);            // xi + eta
+  const Poly rB = mono(0, 1, -1, 0, 0, 0);           // xi - eta
+  const Poly zA = mono(1, 0, 0, 1, 0, 0);            // 1 + xi eta
+  const Poly zB = mono(-1, 0, 0, 1, 0, 0);           // xi eta - 1
+  const Poly perp = pmul(mono(-1, 0, 0, 0, 1, 0), mono(1, 0, 0, 0, 0, -1));  // (xi^2-1)(1-eta^2)
+  for (int nA = 1; nA <= 2; ++nA)
+    for (int nB = 1; nB <= 2; ++nB)
+      for (int kA = 0; kA < 3; ++kA)
+        for (int kB = 0; kB < 3; ++kB) {
+          if ((kA > 0 && nA < 2) || (kB > 0 && nB < 2)) continue;
+          if ((kA == 2) != (kB == 2)) continue;
+          Poly p;
+          if (kA == 2) {
+            p = pmul(pmul(pmul(vol, ppow(rA, nA - 2)), ppow(rB, nB - 2)), perp);
+          } else {
+            Poly a = (kA == 0) ? ppow(rA, nA - 1) : pmul(ppow(rA, nA - 2), zA);
+            Poly b = (kB == 0) ? ppow(rB, nB - 1) : pmul(ppow(rB, nB - 2), zB);
+            p = pmul(pmul(vol, a), b);
+          }
+          for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) {
+              if (p.c[i][j] == 0.0) continue;
+              if (i >= 5 || j >= 5) return false;  // degree bound violated
+              tab[nA - 1][nB - 1][kA][kB][i][j] = p.c[i][j];
+            }
+        }
+  const double phi[3] = {2.0 * M_PI, 2.0 * M_PI, M_PI};
+  if (cudaMemcpyToSymbol(c_ovl_poly, tab, sizeof(tab)) != cudaSuccess) return false;
+  if (cudaMemcpyToSymbol(c_ovl_phi, phi, sizeof(phi)) != cudaSuccess) return false;
+  done = true;
+  return true;
+}
+
+void launch_pair_values(cudaStream_t s, int npair, const int* pA, const int* pB, const int* elem,
+                        const double* R, const ElemTable& tab, double* W, double* S, double* E) {
+  if (npair <= 0) return;
+  pair_values_kernel<<<(npair + 127) / 128, 128, 0, s>>>(npair, pA, pB, elem, R, tab, W, S, E);
+  count_launch();
+}
+
+void launch_pair_derivs(cudaStream_t s, int npair, const int* pA, const int* pB, const int* elem,
+                        const double* R, const ElemTable& tab, double* W, double* S, double* E,
+                        double* dW, double* dS, double* dE) {
+  if (npair <= 0) return;
+  pair_derivs_kernel<<<(npair + 127) / 128, 128, 0, s>>>(npair, pA, pB, elem, R, tab, W, S, E, dW,
+                                                         dS, dE);
+  count_launch();
+}
+
+}  // namespace kx

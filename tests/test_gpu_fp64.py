@@ -1,0 +1,179 @@
+"""GPU parity of the FP64 path against the CPU oracle, through the C ABI.
+
+Tolerances (FP64 path): density matrix max-abs <= 1e-6, forces <= 1e-4 eV/A.
+Other quantities use bounds derived from FP64 rounding of the same
+arithmetic (1e-8 relative or tighter); the observed errors are ~1e-11.
+"""
+import numpy as np
+import pytest
+
+import paper_2303_00689_gb300 as kx
+import synth
+from oracle import dynamics as dyn, electronic as el
+from tests.gpu_helpers import create, oracle_system, max_abs, table
+
+pytestmark = pytest.mark.gpu
+
+D_TOL = 1e-6
+F_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2303_00689_gb300 import build
+    build.build()
+
+
+def _perturbed(D, seed, scale=1e-3):
+    rng = np.random.default_rng(seed)
+    Y = rng.normal(size=D.shape) * scale
+    return D + Y + Y.T
+
+
+def sysm_te(sysm, ev):
+    return ev["Te"]
+
+
+def _compare_eval(h, ev, sysm, Ktol=1e-8):
+    D = kx.sim_get_matrix(h, kx.SIM_MAT_D0)
+    Fk = kx.sim_get_matrix(h, kx.SIM_MAT_FOCK)
+    K = kx.sim_get_matrix(h, kx.SIM_MAT_KERNEL)
+    _, _, F, _ = kx.sim_get_state(h, sysm.N)
+    rec = kx.sim_last_result(h)
+    eps = kx.sim_get_vector(h, 0)
+    assert max_abs(Fk, ev["F"]) < 1e-9 * max(1.0, np.abs(ev["F"]).max())
+    assert max_abs(eps, ev["eps"]) < 1e-9 * max(1.0, np.abs(ev["eps"]).max())
+    assert max_abs(D, ev["D"]) < D_TOL
+    assert max_abs(F, ev["forces"]) < F_TOL
+    assert abs(rec["U"] - ev["U"]) < 1e-8 * max(1.0, abs(ev["U"]))
+    # mu is unique but ill-conditioned inside a wide gap: check eq. 8 at the GPU's mu instead
+    beta = 1.0 / (el.KB * sysm_te(sysm, ev))
+    assert abs(el.fermi(ev["eps"], rec["mu"], beta).sum() - sysm.nocc) < 1e-9
+    if "K" in ev:
+        assert max_abs(K, ev["K"]) < Ktol * max(1e-12, np.abs(ev["K"]).max())
+        assert rec["rank"] == ev["krylov"]["rank"]
+    assert np.array_equal(D, D.T)
+    return dict(D=max_abs(D, ev["D"]), F=max_abs(F, ev["forces"]))
+
+
+@pytest.fixture(scope="module")
+def c4h6():
+    mol = synth.c4h6(1)
+    sysm = oracle_system(mol)
+    cfg = dyn.Config(Te=1000.0, dt=0.5, m=4)
+    Dmin, _ = dyn.scf(sysm, mol.R, cfg)
+    return mol, sysm, cfg, Dmin
+
+
+def test_c4h6_evaluation_teacher_forced(c4h6):
+    mol, sysm, cfg, Dmin = c4h6
+    X = _perturbed(Dmin, 1)
+    ev = dyn.evaluate(sysm, mol.R, X, cfg)
+    h = create(mol, dict(Te=1000.0, dt=0.5, m_max=4, m_min=4), P0=X)
+    try:
+        _compare_eval(h, ev, sysm)
+        assert max_abs(kx.sim_get_matrix(h, kx.SIM_MAT_X), X) == 0.0
+    finally:
+        kx.sim_destroy(h)
+
+
+def test_c4h6_one_step_teacher_forced(c4h6):
+    mol, sysm, cfg, Dmin = c4h6
+    X = _perturbed(Dmin, 2)
+    V = synth.maxwell_boltzmann(mol.Z, 300.0, seed=1)
+    st = dyn.State(sysm, mol.R, V, cfg, X0=X)
+    st.step()
+    h = create(mol, dict(Te=1000.0, dt=0.5, m_max=4, m_min=4), V=V, P0=X)
+    try:
+        kx.sim_step(h, 1)
+        R, Vg, F, D = kx.sim_get_state(h, sysm.N)
+        assert max_abs(R, st.R) < 1e-12
+        assert max_abs(Vg, st.V) < 1e-10
+        assert max_abs(kx.sim_get_matrix(h, kx.SIM_MAT_X), st.X[0]) < 1e-10
+        _compare_eval(h, st.ev, sysm)
+    finally:
+        kx.sim_destroy(h)
+
+
+def test_c4h6_scf_and_20_step_trajectory(c4h6):
+    """Config 1: GPU SCF start and 20 FP64 steps against the oracle trajectory."""
+    mol, sysm, cfg, Dmin = c4h6
+    V = synth.maxwell_boltzmann(mol.Z, 300.0, seed=1)
+    h = create(mol, dict(Te=1000.0, dt=0.5, m_max=4, m_min=4), V=V)
+    try:
+        assert max_abs(kx.sim_get_matrix(h, kx.SIM_MAT_X), Dmin) < 1e-8
+        st = dyn.State(sysm, mol.R, V, cfg, X0=Dmin)
+        recs = kx.sim_step(h, 20)
+        etot = []
+        for _ in range(20):
+            st.step()
+            etot.append(st.total_energy())
+        R, Vg, F, D = kx.sim_get_state(h, sysm.N)
+        assert max_abs(R, st.R) < 1e-8
+        assert max_abs(F, st.ev["forces"]) < F_TOL
+        assert max_abs(D, st.ev["D"]) < D_TOL
+        assert max_abs([r["E_tot"] for r in recs], etot) < 1e-7
+    finally:
+        kx.sim_destroy(h)
+
+
+@pytest.mark.parametrize("kind", ["organic60", "carbon100"])
+def test_midsize_evaluation(kind):
+    """Several 64-wide tiles plus a ragged tail (n = 400 for carbon100)."""
+    if kind == "organic60":
+        rng = np.random.default_rng(np.random.SeedSequence([77, 1]))
+        mol = synth.organic_molecule(rng, 60)
+    else:
+        mol = synth.carbon_packing(seed=7, natoms=100)
+    sysm = oracle_system(mol)
+    cfg = dyn.Config(Te=3000.0, dt=0.5, m=4)
+    X = _perturbed(dyn.initial_guess(sysm), 3, scale=1e-3)
+    ev = dyn.evaluate(sysm, mol.R, X, cfg)
+    h = create(mol, dict(Te=3000.0, dt=0.5, m_max=4, m_min=4), P0=X)
+    try:
+        _compare_eval(h, ev, sysm, Ktol=1e-7)
+        Q = kx.sim_get_matrix(h, kx.SIM_MAT_Q)
+        eps = kx.sim_get_vector(h, 0)
+        Fk = kx.sim_get_matrix(h, kx.SIM_MAT_FOCK)
+        assert np.abs(Q.T @ Q - np.eye(sysm.n)).max() < 1e-9
+        assert np.abs(Fk @ Q - Q * eps).max() < 1e-9 * np.abs(Fk).max()
+    finally:
+        kx.sim_destroy(h)
+
+
+@pytest.mark.parametrize("case", ["C", "H2", "CH2"])
+def test_tiny_systems(case):
+    """Degenerate sizes: one atom (no pairs), n = 2 (no Householder step), n = 6."""
+    if case == "C":
+        mol = synth.Molecule(np.array([6], dtype=np.int32), np.zeros((1, 3)))
+    elif case == "H2":
+        mol = synth.Molecule(np.array([1, 1], dtype=np.int32), np.array([[0, 0, 0], [0, 0, 0.74]]))
+    else:
+        mol = synth.Molecule(np.array([6, 1, 1], dtype=np.int32),
+                             np.array([[0, 0, 0], [0, 0.9, 0.6], [0, -0.9, 0.6]]))
+    sysm = oracle_system(mol)
+    cfg = dyn.Config(Te=1000.0, dt=0.5, m=2)
+    X = _perturbed(dyn.initial_guess(sysm), 4, scale=1e-3)
+    ev = dyn.evaluate(sysm, mol.R, X, cfg)
+    h = create(mol, dict(Te=1000.0, dt=0.5, m_max=2, m_min=2), P0=X)
+    try:
+        _compare_eval(h, ev, sysm, Ktol=1e-7)
+    finally:
+        kx.sim_destroy(h)
+
+
+def test_invalid_inputs_are_rejected():
+    mol = synth.c4h6(1)
+    with pytest.raises(kx.SimError) as e:
+        create(synth.Molecule(mol.Z, mol.R, charge=1))
+    assert e.value.code == kx.SIM_EINVAL
+    bad = mol.Z.copy()
+    bad[0] = 9
+    with pytest.raises(kx.SimError) as e:
+        create(synth.Molecule(bad, mol.R))
+    assert e.value.code == kx.SIM_EINVAL
+    R = mol.R.copy()
+    R[1, 1] = np.nan
+    with pytest.raises(kx.SimError) as e:
+        create(synth.Molecule(mol.Z, R))
+    assert e.value.code == kx.SIM_EINVAL
