@@ -58,9 +58,10 @@ enum sim_precision {
   /* every step in FP64 (FP64 SIMT GEMMs for density and DMPT)               */
   SIM_PREC_FP64 = 0,
   /* FP64 eigensolve, mu and Krylov Gram/solve; density D0 = Q f Q^T and the
-   * DMPT contractions of eq. 36 on tcgen05 tensor cores with FP32
-   * accumulation, operands split into BF16 pieces (3 pieces for the
-   * density, 2 for DMPT) so that the products keep ~16-24 bits            */
+   * DMPT contractions of eq. 36 on tcgen05 tensor cores: operands cut into
+   * fixed-point BF16 slices (4 for the density, 3 for DMPT; 8 bits each
+   * relative to the row maximum), exact FP32 chunk sums, double-float
+   * accumulation across chunks, FP64 output                                 */
   SIM_PREC_MIXED = 1,
 };
 
@@ -95,11 +96,21 @@ typedef struct sim_config {
   double scf_mix;     /* linear mixing P <- mix P + (1 - mix) D[P] (paper: 0.1) */
   int device;         /* CUDA device ordinal                                   */
   void* stream;       /* cudaStream_t to launch on, or NULL for a private one  */
+  int scf_krylov;     /* 0: linear mixing; 1: low-rank Krylov SCF update
+                         P <- P - K (D[P] - P) with K of rank m_max (Results,
+                         "SCF Optimization": fixed rank, no preconditioner);
+                         a mixing step instead whenever the residual has
+                         grown tenfold over the best one                      */
+  int scf_accept;     /* 1: if the SCF does not reach scf_tol in scf_max
+                         iterations, start from the lowest-residual P seen
+                         (reported by sim_scf_info) instead of failing       */
 } sim_config;
 
 /* Fills a config with the defaults used by the paper-shaped workloads:
  * Te 1000 K, dt 0.5 fs, m = 4, fixed rank, FP64, scf_tol 1e-10,
- * scf_max 5000, mix 0.1, device 0, private stream. */
+ * scf_max 5000, mix 0.1, linear mixing, device 0, private stream.
+ * The SCF prints max|D[P] - P| per iteration to stderr when the
+ * environment variable KSAXL_SCF_TRACE is set. */
 void sim_config_default(sim_config* cfg);
 
 /* ---- per-step diagnostics ------------------------------------------------ */
@@ -136,6 +147,10 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms,
                const int* Z, const double* R, const double* V, int charge,
                const double* P0, sim_handle** out);
 
+/* SCF iterations used by sim_create and the final max|D[P] - P| (0, 0 when
+ * P0 was supplied). */
+int sim_scf_info(const sim_handle* h, int* iterations, double* residual);
+
 /* Number of basis functions n and occupied orbitals N_occ of a handle. */
 int sim_norb(const sim_handle* h);
 int sim_nocc(const sim_handle* h);
@@ -144,6 +159,14 @@ int sim_nocc(const sim_handle* h);
  * out: NULL or nsteps records (caller-owned) filled with the diagnostics of
  * each step.  Synchronous: returns after the last step finished. */
 int sim_step(sim_handle* h, int nsteps, sim_step_result* out);
+
+/* sim_step_host -- one MD step with the state exchanged through host memory:
+ * R_in/V_in (natoms x 3, or NULL to keep the device copy) are uploaded,
+ * the step of eqs. 27-30/35 runs, and R_out, V_out, F_out (natoms x 3) and
+ * the step record are downloaded (any output may be NULL).  Page-locked
+ * buffers make the copies asynchronous.  Synchronous on return. */
+int sim_step_host(sim_handle* h, const double* R_in, const double* V_in, double* R_out,
+                  double* V_out, double* F_out, sim_step_result* out);
 
 /* sim_step_async -- enqueue nsteps steps on the handle's stream without
  * waiting; diagnostics of the last step can be read with sim_last_result
@@ -192,6 +215,16 @@ long long sim_launch_count(void);
 void* sim_stream(sim_handle* h);
 
 void sim_destroy(sim_handle* h);
+
+/* sim_debug_tc_gemm -- test hook for the tensor-core contraction used by the
+ * mixed-precision path (no counterpart in the paper; it exposes one building
+ * block of eq. 19 / eq. 36 so tests can check it in isolation).
+ * C = sum over `terms` BF16-piece products A_i B_j^T of the FP64 inputs:
+ * terms = 1 (plain BF16), 3 (2 pieces) or 6 (3 pieces).  A, B, C are host
+ * n x n row-major arrays; sym != 0 computes only the upper tiles and mirrors
+ * (use only when A B^T is symmetric).  Allocates and frees its own device
+ * memory; synchronous. */
+int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sym, double* C);
 
 /* Thread-local message of the last error (never NULL). */
 const char* sim_last_error(void);

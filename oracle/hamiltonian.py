@@ -117,7 +117,7 @@ class PairCache:
     oracle's memory stays bounded; the values are the same either way.
     """
 
-    def __init__(self, sysm, R, limit=60000):
+    def __init__(self, sysm, R, limit=400000):
         self.sysm, self.R = sysm, np.array(R, dtype=np.float64)
         self.keep = len(sysm.pA) <= limit
         self._val, self._der = {}, {}

@@ -22,10 +22,10 @@ SIM_MAT_X, SIM_MAT_D0, SIM_MAT_FOCK, SIM_MAT_H, SIM_MAT_KERNEL, SIM_MAT_Q = rang
 SIM_NFIELDS = 23
 
 EXPORTED = (
-    "sim_config_default", "sim_create", "sim_norb", "sim_nocc", "sim_step", "sim_step_async",
+    "sim_config_default", "sim_create", "sim_scf_info", "sim_norb", "sim_nocc", "sim_step", "sim_step_async", "sim_step_host",
     "sim_last_result", "sim_get_state", "sim_set_state", "sim_get_matrix", "sim_get_vector",
     "sim_profile_enable", "sim_phase_count", "sim_phase_name", "sim_phase_times",
-    "sim_launch_count", "sim_stream", "sim_destroy", "sim_last_error",
+    "sim_launch_count", "sim_stream", "sim_destroy", "sim_last_error", "sim_debug_tc_gemm",
 )
 
 
@@ -39,7 +39,7 @@ class sim_config(C.Structure):
     _fields_ = [("Te", C.c_double), ("dt", C.c_double), ("m_max", C.c_int), ("m_min", C.c_int),
                 ("krylov_tol", C.c_double), ("precision", C.c_int), ("scf_tol", C.c_double),
                 ("scf_max", C.c_int), ("scf_mix", C.c_double), ("device", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("scf_krylov", C.c_int), ("scf_accept", C.c_int)]
 
 
 class sim_param_table(C.Structure):
@@ -70,9 +70,11 @@ def lib():
         L.sim_create.argtypes = [P(sim_config), P(sim_param_table), C.c_int, P(C.c_int), dp, dp, C.c_int,
                                  dp, P(C.c_void_p)]
         L.sim_norb.argtypes = [C.c_void_p]
+        L.sim_scf_info.argtypes = [C.c_void_p, P(C.c_int), dp]
         L.sim_nocc.argtypes = [C.c_void_p]
         L.sim_step.argtypes = [C.c_void_p, C.c_int, P(sim_step_result)]
         L.sim_step_async.argtypes = [C.c_void_p, C.c_int]
+        L.sim_step_host.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, P(sim_step_result)]
         L.sim_last_result.argtypes = [C.c_void_p, P(sim_step_result)]
         L.sim_get_state.argtypes = [C.c_void_p, dp, dp, dp, dp]
         L.sim_set_state.argtypes = [C.c_void_p, dp, dp, dp]
@@ -89,6 +91,7 @@ def lib():
         L.sim_stream.restype = C.c_void_p
         L.sim_destroy.argtypes = [C.c_void_p]
         L.sim_destroy.restype = None
+        L.sim_debug_tc_gemm.argtypes = [C.c_int, dp, dp, C.c_int, C.c_int, dp]
         L.sim_last_error.argtypes = []
         L.sim_last_error.restype = C.c_char_p
         _lib_handle = L
@@ -148,6 +151,13 @@ def sim_create(cfg, table, Z, R, V=None, charge=0, P0=None):
     return h
 
 
+def sim_scf_info(h):
+    it = C.c_int()
+    res = C.c_double()
+    _check(lib().sim_scf_info(h, C.byref(it), C.byref(res)))
+    return it.value, res.value
+
+
 def sim_norb(h):
     return lib().sim_norb(h)
 
@@ -166,6 +176,12 @@ def sim_step(h, nsteps, records=True):
 
 def sim_step_async(h, nsteps):
     _check(lib().sim_step_async(h, int(nsteps)))
+
+
+def sim_step_host(h, R_in, V_in, R_out, V_out, F_out, record=None):
+    """One step with host buffers (arrays must be C-contiguous float64, natoms x 3)."""
+    _check(lib().sim_step_host(h, _dptr(R_in), _dptr(V_in), _dptr(R_out), _dptr(V_out), _dptr(F_out),
+                               C.byref(record) if record is not None else None))
 
 
 def sim_last_result(h):
@@ -233,6 +249,15 @@ def sim_stream(h):
 def sim_destroy(h):
     if h:
         lib().sim_destroy(h)
+
+
+def sim_debug_tc_gemm(A, B, terms=1, sym=False):
+    A = _f64(A)
+    B = _f64(B)
+    n = A.shape[0]
+    out = np.empty((n, n))
+    _check(lib().sim_debug_tc_gemm(n, _dptr(A), _dptr(B), int(terms), 1 if sym else 0, _dptr(out)))
+    return out
 
 
 def sim_last_error():

@@ -77,6 +77,8 @@ struct sim_handle {
   TcWork tw;
   int xhead = 0;
   int last_rec = 0;   // index in rec[] of the most recent record
+  int scf_iters = 0;   // SCF iterations used by sim_create (0 when P0 was given)
+  double scf_residual = 0.0;
   // host mirror of the last results
   Scalars sc_h;
   // profiling
@@ -193,27 +195,45 @@ static MolDev mol(const sim_handle* h) { return MolDev{h->N, h->n, h->npair, h->
 static PairDev pairs(const sim_handle* h) { return PairDev{h->W, h->S, h->E, h->dW, h->dS, h->dE}; }
 static double* xslot(sim_handle* h, int k) { return h->X[(h->xhead + k) % 8]; }
 
-// D0 = Q diag(f) Q^T, exactly symmetric
+static bool mixed(const sim_handle* h) { return h->cfg.precision == SIM_PREC_MIXED; }
+
+// D0 = Q diag(f) Q^T = (Q f^1/2)(Q f^1/2)^T, exactly symmetric
 static void density(sim_handle* h) {
   cudaStream_t s = h->stream;
   int n = h->n;
   launch_scale_columns(s, n, h->Q, h->f, h->Qs);
-  if (h->cfg.precision == SIM_PREC_MIXED && tc_available()) {
-    tc_syrk_split(s, n, h->Qs, h->D, h->tw, 3);
+  if (mixed(h)) {
+    // four fixed-point BF16 slices, ten slice products (32 bits per row scale)
+    tc_split(s, h->tw, kSlotQs, h->Qs, 4, 0);
+    tc_gemm(s, h->tw, kSlotQs, kSlotQs, 10, 1.0, h->D, 1);
   } else {
     dgemm(s, 0, 1, n, n, n, 1.0, h->Qs, n, h->Qs, n, 0.0, h->D, n, 1);
   }
+}
+
+// BF16 pieces of Q and Q^T for the DMPT products (once per evaluation)
+static void dmpt_prepare(sim_handle* h) {
+  if (!mixed(h)) return;
+  tc_split(h->stream, h->tw, kSlotQ, h->Q, 3, 0);
+  tc_split(h->stream, h->tw, kSlotQt, h->Q, 3, 1);
 }
 
 // D1 = Q [Lambda o (Q^T F1 Q - dmu I)] Q^T (eq. 36)
 static void dmpt(sim_handle* h, const double* F1, double* D1) {
   cudaStream_t s = h->stream;
   int n = h->n;
-  if (h->cfg.precision == SIM_PREC_MIXED && tc_available()) {
-    tc_similarity(s, n, h->Q, F1, h->T2, h->tw, /*transpose_first=*/1);    // T2 = Q^T F1 Q
+  if (mixed(h)) {
+    // three fixed-point BF16 slices per operand, six slice products (24 bits per row scale)
+    tc_split(s, h->tw, kSlotT0, F1, 3, 0);
+    tc_gemm(s, h->tw, kSlotQt, kSlotT0, 6, 1.0, h->T1, 0);      // T1 = Q^T F1
+    tc_split(s, h->tw, kSlotT1, h->T1, 3, 0);
+    tc_gemm(s, h->tw, kSlotT1, kSlotQt, 6, 1.0, h->T2, 1);      // T2 = (Q^T F1) Q
     launch_dmu(s, n, h->T2, h->eps, h->f, h->beta, h->sc);
     launch_dmpt_y(s, n, h->T2, h->eps, h->f, h->beta, h->sc, h->Y);
-    tc_similarity(s, n, h->Q, h->Y, D1, h->tw, /*transpose_first=*/0);     // D1 = Q Y Q^T
+    tc_split(s, h->tw, kSlotT0, h->Y, 3, 0);
+    tc_gemm(s, h->tw, kSlotQ, kSlotT0, 6, 1.0, h->T1, 0);       // T1 = Q Y
+    tc_split(s, h->tw, kSlotT1, h->T1, 3, 0);
+    tc_gemm(s, h->tw, kSlotT1, kSlotQ, 6, 1.0, D1, 1);          // D1 = (Q Y) Q^T
     return;
   }
   dgemm(s, 0, 0, n, n, n, 1.0, F1, n, h->Q, n, 0.0, h->T1, n);         // T1 = F1 Q
@@ -236,6 +256,40 @@ static int eig(sim_handle* h) {
   eig_backtransform(h->stream, h->n, h->Q, h->ew);
   phase_end(h);
   return SIM_OK;
+}
+
+// Krylov kernel of W0 = D - P for the current eigenpairs (eqs. 31-34), result in h->K
+static void krylov_kernel(sim_handle* h, const double* P) {
+  cudaStream_t s = h->stream;
+  size_t nn = (size_t)h->n * h->n;
+  MolDev m = mol(h);
+  PairDev pd = pairs(h);
+  phase_begin(h, PH_KRY_GEMM);
+  dmpt_prepare(h);
+  phase_end(h);
+  phase_begin(h, PH_KRY_BLAS);
+  launch_krylov_start(s, nn, h->D, P, h->W0, h->sc, h->red);
+  phase_end(h);
+  for (int k = 0; k < h->mmax; ++k) {
+    phase_begin(h, PH_KRY_BLAS);
+    const double* src = (k == 0) ? h->W0 : h->Wk[k - 1];
+    launch_krylov_orth(s, nn, k, h->Vk, src, h->Vk[k], h->sc, h->red, h->coef);
+    phase_end(h);
+    phase_begin(h, PH_KRY_FOCK);
+    launch_pack_diag(s, m, h->Vk[k], h->Vd);
+    launch_build_fock(s, m, pd, h->tab, h->Vk[k], h->Vd, nullptr, h->F1);
+    phase_end(h);
+    phase_begin(h, PH_KRY_GEMM);
+    dmpt(h, h->F1, h->D1);
+    phase_end(h);
+    phase_begin(h, PH_KRY_BLAS);
+    launch_krylov_w(s, nn, k, h->D1, h->Vk[k], h->Wk[k], h->Wk, h->W0, h->sc, h->red, h->cfg.krylov_tol,
+                    h->cfg.m_min);
+    phase_end(h);
+  }
+  phase_begin(h, PH_KRY_BLAS);
+  launch_krylov_combine(s, nn, h->mmax, h->Vk, h->sc, h->K);
+  phase_end(h);
 }
 
 // Evaluate everything at (R, X(t)): pair blocks, F, D0, U, forces, Krylov kernel.
@@ -266,29 +320,8 @@ static int evaluate(sim_handle* h, bool krylov = true) {
   launch_forces(s, m, pd, h->tab, h->D, X, h->Dd, h->Pd, h->g, h->F);
   phase_end(h);
   if (!krylov) return SIM_OK;
-  // Krylov subspace approximation of K (D0 - X), eqs. 31-34
+  krylov_kernel(h, X);   // K (D0 - X), eqs. 31-34
   phase_begin(h, PH_KRY_BLAS);
-  launch_krylov_start(s, nn, h->D, X, h->W0, h->sc, h->red);
-  phase_end(h);
-  for (int k = 0; k < h->mmax; ++k) {
-    phase_begin(h, PH_KRY_BLAS);
-    const double* src = (k == 0) ? h->W0 : h->Wk[k - 1];
-    launch_krylov_orth(s, nn, k, h->Vk, src, h->Vk[k], h->sc, h->red, h->coef);
-    phase_end(h);
-    phase_begin(h, PH_KRY_FOCK);
-    launch_pack_diag(s, m, h->Vk[k], h->Vd);
-    launch_build_fock(s, m, pd, h->tab, h->Vk[k], h->Vd, nullptr, h->F1);
-    phase_end(h);
-    phase_begin(h, PH_KRY_GEMM);
-    dmpt(h, h->F1, h->D1);
-    phase_end(h);
-    phase_begin(h, PH_KRY_BLAS);
-    launch_krylov_w(s, nn, k, h->D1, h->Vk[k], h->Wk[k], h->Wk, h->W0, h->sc, h->red, h->cfg.krylov_tol,
-                    h->cfg.m_min);
-    phase_end(h);
-  }
-  phase_begin(h, PH_KRY_BLAS);
-  launch_krylov_combine(s, nn, h->mmax, h->Vk, h->sc, h->K);
   launch_check_finite(s, (size_t)3 * h->N, h->F, h->sc);
   launch_check_finite(s, nn, h->K, h->sc);
   phase_end(h);
@@ -336,10 +369,12 @@ static int one_step(sim_handle* h, sim_step_result* rec_dev) {
 }
 
 static int check_status(sim_handle* h) {
-  int st = 0;
+  int st = 0, tce = 0;
   CUDA_TRY(cudaMemcpyAsync(&st, &h->sc->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  if (mixed(h)) CUDA_TRY(cudaMemcpyAsync(&tce, tc_error_flag(h->tw), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   CUDA_TRY(cudaGetLastError());
+  if (tce) return fail(SIM_ETIMEOUT, "a bounded tensor-core pipeline wait expired");
   if (st & kStatusTimeout) return fail(SIM_ETIMEOUT, "a bounded device-side wait expired");
   if (st & kStatusNumeric) return fail(SIM_ENUMERIC, "NaN or Inf in forces or kernel result");
   return SIM_OK;
@@ -406,9 +441,10 @@ static void layout(sim_handle* h, Arena& a) {
   h->rec = a.take<sim_step_result>(kRecCap);
   void* ewb = a.take<char>(eig_work_bytes(h->n));
   if (a.base) eig_work_bind(h->ew, ewb, h->n);
-  size_t tcb = tc_work_bytes(h->n);
-  void* twb = a.take<char>(tcb);
-  if (a.base) tc_work_bind(h->tw, twb, h->n);
+  if (h->cfg.precision == SIM_PREC_MIXED) {
+    void* twb = a.take<char>(tc_work_bytes(h->n));
+    if (a.base) tc_work_bind(h->tw, twb, h->n);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -428,6 +464,7 @@ void sim_config_default(sim_config* c) {
   c->scf_tol = 1e-10;
   c->scf_max = 5000;
   c->scf_mix = 0.1;
+  c->scf_krylov = 0;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -435,9 +472,19 @@ void sim_config_default(sim_config* c) {
 const char* sim_last_error(void) { return t_err.c_str(); }
 long long sim_launch_count(void) { return g_launches.load(); }
 int sim_norb(const sim_handle* h) { return h ? h->n : -1; }
+int sim_scf_info(const sim_handle* h, int* iterations, double* residual) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (iterations) *iterations = h->scf_iters;
+  if (residual) *residual = h->scf_residual;
+  return SIM_OK;
+}
 int sim_nocc(const sim_handle* h) { return h ? h->nocc : -1; }
 void* sim_stream(sim_handle* h) { return h ? (void*)h->stream : nullptr; }
 
+// Ground state at t0 (Results, "SCF Optimization"): linear mixing
+// P <- mix P + (1 - mix) D[P], or, with scf_krylov != 0, the low-rank Krylov
+// (Newton-like) update P <- P - K (D[P] - P) built from the same DMPT
+// responses as the MD kernel.  Stops when max|D[P] - P| < scf_tol.
 static int scf(sim_handle* h, int* iters) {
   cudaStream_t s = h->stream;
   int n = h->n;
@@ -447,6 +494,7 @@ static int scf(sim_handle* h, int* iters) {
   double* P = xslot(h, 0);
   double* Dn = h->D;
   double* err_d = h->coef + 48;
+  const bool trace = getenv("KSAXL_SCF_TRACE") != nullptr;
   // diagonal guess: valence electrons spread over each atom's orbitals, trace N_occ
   std::vector<double> P0(nn, 0.0);
   double tr = 0.0;
@@ -458,6 +506,8 @@ static int scf(sim_handle* h, int* iters) {
   for (int i = 0; i < n; ++i) P0[(size_t)i * n + i] *= h->nocc / tr;
   CUDA_TRY(cudaMemcpyAsync(P, P0.data(), nn * sizeof(double), cudaMemcpyHostToDevice, s));
   double mix = h->cfg.scf_mix;
+  double best = 1e300;
+  double err = 0.0;
   for (int it = 0; it < h->cfg.scf_max; ++it) {
     launch_pack_diag(s, m, P, h->Pd);
     launch_build_fock(s, m, pd, h->tab, P, h->Pd, h->h, h->Fock);
@@ -466,21 +516,41 @@ static int scf(sim_handle* h, int* iters) {
     launch_fermi(s, n, h->eps, (double)h->nocc, h->beta, h->f, h->sc);
     density(h);
     launch_maxabs_diff(s, nn, Dn, P, err_d, h->red);
-    double err = 0.0;
     CUDA_TRY(cudaMemcpyAsync(&err, err_d, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     int st = 0;
     CUDA_TRY(cudaMemcpy(&st, &h->sc->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (trace) fprintf(stderr, "scf %4d  max|D-P| = %.3e\n", it, err);
     if (st & kStatusTimeout) return fail(SIM_ETIMEOUT, "eigensolver barrier timed out during SCF");
     if (!std::isfinite(err)) return fail(SIM_ENUMERIC, "NaN during SCF");
     if (err < h->cfg.scf_tol) {
       CUDA_TRY(cudaMemcpyAsync(P, Dn, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
       *iters = it;
+      h->scf_iters = it;
+      h->scf_residual = err;
       return SIM_OK;
     }
-    launch_axpby(s, nn, mix, P, 1.0 - mix, Dn, P);
+    if (err < best) {
+      best = err;
+      CUDA_TRY(cudaMemcpyAsync(xslot(h, 1), P, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));  // best P
+    }
+    if (h->cfg.scf_krylov && err < 10.0 * best) {
+      krylov_kernel(h, P);
+      launch_axpby(s, nn, 1.0, P, -1.0, h->K, P);      // P <- P - K (D - P)
+    } else {
+      launch_axpby(s, nn, mix, P, 1.0 - mix, Dn, P);   // linear mixing
+    }
   }
-  return fail(SIM_ENOCONV, "SCF did not converge within scf_max iterations");
+  h->scf_iters = h->cfg.scf_max;
+  h->scf_residual = best;
+  if (h->cfg.scf_accept) {
+    CUDA_TRY(cudaMemcpyAsync(P, xslot(h, 1), nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    *iters = h->cfg.scf_max;
+    return SIM_OK;
+  }
+  char msg[160];
+  snprintf(msg, sizeof msg, "SCF did not converge within %d iterations (max|D-P| = %.3e)", h->cfg.scf_max, err);
+  return fail(SIM_ENOCONV, msg);
 }
 
 int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, const int* Z,
@@ -492,6 +562,8 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
     return fail(SIM_EINVAL, "invalid configuration");
   if (cfg->precision != SIM_PREC_FP64 && cfg->precision != SIM_PREC_MIXED)
     return fail(SIM_EINVAL, "unknown precision mode");
+  if (cfg->precision == SIM_PREC_MIXED && !tc_available())
+    return fail(SIM_EINVAL, "mixed precision needs the tensor-map driver entry point (tcgen05/TMA path)");
   sim_handle* h = new sim_handle();
   h->cfg = *cfg;
   for (int e = 0; e < 4; ++e)
@@ -552,6 +624,10 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
   }
   Arena a{(char*)h->arena, 0, h->arena_bytes};
   layout(h, a);
+  if (mixed(h) && !tc_ready(h->tw)) {
+    sim_destroy(h);
+    return fail(SIM_EINTERNAL, "tensor map encoding failed for the BF16 operand pieces");
+  }
   cudaStream_t s = h->stream;
   std::vector<int> pa, pb;
   pa.reserve(h->npair);
@@ -637,6 +713,24 @@ int sim_step(sim_handle* h, int nsteps, sim_step_result* out) {
   }
   if (h->prof) collect_events(h);
   return SIM_OK;
+}
+
+int sim_step_host(sim_handle* h, const double* R_in, const double* V_in, double* R_out, double* V_out,
+                  double* F_out, sim_step_result* out) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  cudaStream_t s = h->stream;
+  size_t b3 = 3 * (size_t)h->N * sizeof(double);
+  if (R_in) CUDA_TRY(cudaMemcpyAsync(h->R, R_in, b3, cudaMemcpyHostToDevice, s));
+  if (V_in) CUDA_TRY(cudaMemcpyAsync(h->V, V_in, b3, cudaMemcpyHostToDevice, s));
+  int rc = one_step(h, h->rec);
+  if (rc) return rc;
+  h->last_rec = 0;
+  if (R_out) CUDA_TRY(cudaMemcpyAsync(R_out, h->R, b3, cudaMemcpyDeviceToHost, s));
+  if (V_out) CUDA_TRY(cudaMemcpyAsync(V_out, h->V, b3, cudaMemcpyDeviceToHost, s));
+  if (F_out) CUDA_TRY(cudaMemcpyAsync(F_out, h->F, b3, cudaMemcpyDeviceToHost, s));
+  if (out) CUDA_TRY(cudaMemcpyAsync(out, h->rec, sizeof(sim_step_result), cudaMemcpyDeviceToHost, s));
+  if (h->prof) collect_events(h);
+  return check_status(h);
 }
 
 int sim_last_result(sim_handle* h, sim_step_result* out) {
@@ -739,11 +833,51 @@ int sim_phase_times(sim_handle* h, double* ms, long long* launches, double* work
   return SIM_OK;
 }
 
+// Test hook: C = sum of BF16-piece products of A and B^T on the tensor cores.
+int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sym, double* C) {
+  if (n < 1 || !A || !B || !C || (terms != 1 && terms != 3 && terms != 6 && terms != 10))
+    return fail(SIM_EINVAL, "bad argument");
+  if (!tc_available()) return fail(SIM_EINVAL, "tensor-map entry point unavailable");
+  size_t nn = (size_t)n * n;
+  size_t bytes = 3 * nn * sizeof(double) + tc_work_bytes(n) + 4096;
+  char* arena = nullptr;
+  if (cudaMalloc(&arena, bytes) != cudaSuccess) return fail(SIM_ENOMEM, "allocation failed");
+  double* dA = (double*)arena;
+  double* dB = dA + nn;
+  double* dC = dB + nn;
+  void* tb = (void*)(((uintptr_t)(dC + nn) + 1023) & ~(uintptr_t)1023);
+  TcWork w;
+  tc_work_bind(w, tb, n);
+  int rc = SIM_OK;
+  cudaStream_t s = 0;
+  int pieces = (terms == 10) ? 4 : (terms == 6) ? 3 : (terms == 3) ? 2 : 1;
+  if (!tc_ready(w)) {
+    rc = fail(SIM_EINTERNAL, "tensor map encoding failed");
+  } else {
+    cudaMemcpy(dA, A, nn * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(dB, B, nn * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemset(dC, 0, nn * sizeof(double));
+    tc_split(s, w, kSlotT0, dA, pieces, 0);
+    tc_split(s, w, kSlotT1, dB, pieces, 0);
+    tc_gemm(s, w, kSlotT0, kSlotT1, terms, 1.0, dC, sym);
+    int err = 0;
+    cudaError_t ce = cudaDeviceSynchronize();
+    cudaMemcpy(&err, tc_error_flag(w), sizeof(int), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) rc = fail(SIM_EINTERNAL, std::string("CUDA error: ") + cudaGetErrorString(ce));
+    else if (err) rc = fail(SIM_ETIMEOUT, "tensor-core pipeline wait expired");
+    else cudaMemcpy(C, dC, nn * sizeof(double), cudaMemcpyDeviceToHost);
+  }
+  tc_work_release(w);
+  cudaFree(arena);
+  return rc;
+}
+
 void sim_destroy(sim_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& p : h->ev_pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->tw.base) tc_work_release(h->tw);
   if (h->arena) cudaFree(h->arena);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;

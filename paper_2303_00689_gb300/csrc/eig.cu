@@ -160,7 +160,6 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
 // Gershgorin interval, squared off-diagonals, pivmin; one block
 __global__ void gersh_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
                              double* __restrict__ e2, double* __restrict__ scal) {
-  __shared__ double red[32];
   double lo = 1e300, hi = -1e300, em = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double r = 0.0;
@@ -188,7 +187,6 @@ __global__ void gersh_kernel(int n, const double* __restrict__ d, const double* 
     hi += 4.0 * kEps * tn + 2.0 * pivmin;
     scal[0] = lo; scal[1] = hi; scal[2] = tn; scal[3] = pivmin;
   }
-  (void)red;
 }
 
 __device__ __forceinline__ int sturm_count(int n, const double* __restrict__ d,

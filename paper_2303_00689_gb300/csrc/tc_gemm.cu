@@ -1,11 +1,478 @@
-// Placeholder until the tcgen05 kernels land: reports the tensor-core path as
-// unavailable, and the mixed-precision mode refuses to run without it.
+// Tensor-core GEMMs for the mixed-precision path (sm_103a, tcgen05 + TMA).
+//
+// C (FP64 out) = alpha * sum_s A_{a(s)} B_{b(s)}^T over "segments" s, where
+// A_i (M x K) and B_j (N x K) are BF16 slices of FP64 operands, both stored
+// K-major (row-major with K contiguous, leading dimension ld).
+//
+// Slicing is fixed-point per row: with 2^e_r > max_k |X_rk|, slice a of row r
+// holds integers of magnitude <= 128 times 2^(e_r - 7 - 8a), so
+// X ~ X0 + X1 + ... keeps 8 bits per slice relative to the row maximum.  A
+// product of slices a and b of rows r and s is then an integer of magnitude
+// <= 2^14 times the single scale 2^(e_r + e_s - 14 - 8(a + b)); a sum of up
+// to 512 such products (one accumulation chunk) stays below 2^23 and is
+// exact in the FP32 tensor-core accumulator.  The product keeps the slice
+// pairs with a + b < slices (1, 3, 6 or 10 terms for 1-4 slices).
+//
+// One CTA computes a 128 x 128 tile with 18 warps:
+//   warp 0 / lane 0 : TMA producer (128B-swizzled boxes of 128 rows x 64 K)
+//   warp 1          : allocates / frees TMEM; lane 0 issues tcgen05.mma
+//                     (M = 128, N = 128, K = 16 slices)
+//   warps 2-17      : epilogue; warp w reads TMEM lane quarter w % 4 and
+//                     the 32-column group (w - 2) / 4
+// K is consumed in chunks of kChunk k-tiles that never straddle two
+// segments.  Each chunk accumulates (exactly, see above) in FP32 in one of
+// two TMEM buffers (2 x 128 columns); the epilogue warps fold every finished
+// chunk into double-float registers (FP32 hi + lo, TwoSum).  The final tile
+// is written in FP64.
+// A ring of kStages shared-memory stages is guarded by mbarriers (full: TMA
+// transaction bytes; empty: tcgen05.commit); the TMEM buffers by acc_full
+// (tcgen05.commit) and acc_empty (one arrival per epilogue warp).  Every wait is
+// bounded; on expiry the kernel raises an error flag, waits (bounded) for its
+// own TMA copies, frees its TMEM and returns.
+// With sym != 0 (M == N, result known symmetric) only tiles with
+// row-tile <= col-tile run and values are mirrored, so C is bitwise symmetric.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "kernels.h"
 #include "tc_gemm.h"
 
 namespace kx {
-size_t tc_work_bytes(int) { return 256; }
-void tc_work_bind(TcWork& w, void* base, int) { w.base = base; w.bytes = 256; }
-bool tc_available() { return false; }
-void tc_syrk_split(cudaStream_t, int, const double*, double*, TcWork&, int) {}
-void tc_similarity(cudaStream_t, int, const double*, const double*, double*, TcWork&, int) {}
+
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 5;
+constexpr int kChunk = 8;                    // k-tiles (512 K) per exact FP32 accumulation chunk
+constexpr int kEpiWarps = 16;                // 4 lane quarters x 4 column groups of 32
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kTileBytesA = kBM * kBK * 2;   // 16 KB
+constexpr int kTileBytesB = kBN * kBK * 2;   // 16 KB
+constexpr int kSmemBytes = kStages * (kTileBytesA + kTileBytesB) + 1024 + 256;
+constexpr long long kWaitLimit = 1LL << 22;
+
+struct SegTable {
+  int nseg;
+  int a[10];
+  int b[10];
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; returns false on timeout or when another thread flagged an error
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 1023) == 1023 && *(volatile int*)err) return false;
+  }
+  atomicOr(err, 1);
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row atoms of 1024 B
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // layout: 128B swizzle
+  return d;
+}
+// instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = 128
+__host__ __device__ constexpr uint32_t make_idesc() {
+  return (1u << 4)                      // D format FP32
+         | (1u << 7)                    // A format BF16
+         | (1u << 10)                   // B format BF16
+         | ((uint32_t)(kBN >> 3) << 17) // N / 8
+         | ((uint32_t)(kBM >> 4) << 24);// M / 16
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcMaps {
+  CUtensorMap a[kTcMaxSlices];
+  CUtensorMap b[kTcMaxSlices];
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// error-free FP32 addition folded into a (hi, lo) pair
+__device__ __forceinline__ void twosum_acc(float& hi, float& lo, float b) {
+  float s = hi + b;
+  float bb = s - hi;
+  float err = (hi - (s - bb)) + (b - bb);
+  hi = s;
+  lo += err;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ TcMaps maps, SegTable seg, int M, int N, int K, double alpha,
+                   double* __restrict__ C, int ldc, int sym, int* err) {
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (sym && bi > bj) return;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;
+  uint8_t* sB = base + kStages * kTileBytesA;
+  uint64_t* full = (uint64_t*)(sB + kStages * kTileBytesB);
+  uint64_t* empty = full + kStages;
+  uint64_t* acc_full = empty + kStages;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = bi * kBM, n0 = bj * kBN;
+  const int ktiles = (K + kBK - 1) / kBK;
+  const int total = seg.nseg * ktiles;
+  const int cps = (ktiles + kChunk - 1) / kChunk;   // chunks per segment
+  const int nchunks = seg.nseg * cps;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kEpiWarps);
+    }
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * kBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer
+      int issued = 0;
+      bool ok = true;
+      for (int it = 0; it < total && ok; ++it) {
+        int s = it % kStages;
+        uint32_t ph = (uint32_t)(it / kStages) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, err)) { ok = false; break; }
+        int sg = it / ktiles, kt = it % ktiles;
+        mbar_expect_tx(&full[s], kTileBytesA + kTileBytesB);
+        tma_load_2d(sA + s * kTileBytesA, &maps.a[seg.a[sg]], &full[s], kt * kBK, m0);
+        tma_load_2d(sB + s * kTileBytesB, &maps.b[seg.b[sg]], &full[s], kt * kBK, n0);
+        issued = it + 1;
+      }
+      if (!ok) {
+        // let our own copies land before the CTA can exit
+        for (int it = (issued > kStages ? issued - kStages : 0); it < issued; ++it) {
+          int s = it % kStages;
+          uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          for (long long w = 0; w < kWaitLimit && !mbar_try(&full[s], ph); ++w) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: chunk c accumulates into TMEM buffer c & 1
+      const uint32_t idesc = make_idesc();
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int b = c & 1;
+        if (!mbar_wait(&acc_empty[b], ((uint32_t)(c >> 1) & 1u) ^ 1u, err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t dst = tmem + (uint32_t)(b * kBN);
+        const int sg = c / cps, cc = c % cps;
+        const int it0 = sg * ktiles + cc * kChunk;
+        const int seg_end = (sg + 1) * ktiles;
+        const int it1 = (it0 + kChunk < seg_end) ? it0 + kChunk : seg_end;
+        for (int it = it0; it < it1; ++it) {
+          int s = it % kStages;
+          uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          if (!mbar_wait(&full[s], ph, err)) { ok = false; break; }
+          tc_fence_after();
+          uint32_t a_addr = smem_u32(sA + s * kTileBytesA);
+          uint32_t b_addr = smem_u32(sB + s * kTileBytesB);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) {
+            uint64_t da = smem_desc(a_addr + k * 32);
+            uint64_t db = smem_desc(b_addr + k * 32);
+            umma_bf16(dst, da, db, idesc, (it > it0 || k > 0) ? 1u : 0u);
+          }
+          umma_commit(&empty[s]);
+        }
+        if (ok) umma_commit(&acc_full[b]);
+      }
+    }
+  } else {
+    // epilogue warps: fold each chunk into double-float accumulators
+    const int quarter = warp & 3;              // TMEM lanes 32 * quarter ...
+    const int cg = (warp - 2) >> 2;            // columns 32 * cg ...
+    float hi[32], lo[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) { hi[j] = 0.0f; lo[j] = 0.0f; }
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1;
+      bool got = mbar_wait(&acc_full[b], (uint32_t)(c >> 1) & 1u, err);
+      got = __all_sync(0xffffffffu, got);
+      if (!got) { ok = false; break; }
+      tc_fence_after();
+      {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kBN + cg * 32), r);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) twosum_acc(hi[j], lo[j], __uint_as_float(r[j]));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+    }
+    if (ok && total > 0) {
+      const int row = m0 + quarter * 32 + lane;
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          int col = n0 + cg * 32 + j;
+          if (col >= N) break;
+          if (sym && row > col) continue;
+          double v = alpha * ((double)hi[j] + (double)lo[j]);
+          C[(size_t)row * ldc + col] = v;
+          if (sym && row != col) C[(size_t)col * ldc + row] = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kBN) : "memory");
+  }
+}
+
+// per-row scale exponent: e_r with max_k |X_rk| < 2^e_r (rows of X^T if transpose)
+__global__ void row_exponent_kernel(int n, const double* __restrict__ X, int transpose, int* __restrict__ ex) {
+  int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (r >= n) return;
+  double m = 0.0;
+  for (int k = lane; k < n; k += 32) m = fmax(m, fabs(transpose ? X[(size_t)k * n + r] : X[(size_t)r * n + k]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) {
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);   // m = f 2^e with 0.5 <= f < 1, so m < 2^e
+    ex[r] = e;
+  }
+}
+
+// FP64 -> fixed-point BF16 slices relative to the row exponent; ld-padded rows
+__global__ void split_bf16_kernel(int n, const double* __restrict__ X, int ld, int slices, int transpose,
+                                  const int* __restrict__ ex, __nv_bfloat16* const* __restrict__ P) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)n * ld;
+  if (t >= tot) return;
+  int i = (int)(t / ld), j = (int)(t % ld);
+  double x = 0.0;
+  if (j < n) x = transpose ? X[(size_t)j * n + i] : X[(size_t)i * n + j];
+  int e = ex[i];
+  for (int a = 0; a < slices; ++a) {
+    int sh = 7 + 8 * a - e;                      // slice unit is 2^-sh
+    double q = rint(ldexp(x, sh));               // integer, |q| <= 128
+    double v = ldexp(q, -sh);
+    P[a][t] = __double2bfloat16(v);              // exact: |q| <= 256
+    x -= v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+struct TcBuffers {
+  int n, ld;
+  __nv_bfloat16* piece[kTcPieceSlots][kTcMaxSlices];
+  __nv_bfloat16** dpieces;            // device copy of the slice pointers, per slot
+  CUtensorMap map[kTcPieceSlots][kTcMaxSlices];
+  int* ex;                            // per-row exponents, one array per slot
+  int* err;
+  bool maps_ok;
+};
+
+static int ld_for(int n) { return ((n + 63) / 64) * 64; }
+
+size_t tc_work_bytes(int n) {
+  size_t ld = (size_t)ld_for(n);
+  size_t one = ((size_t)n * ld * 2 + 1023) & ~(size_t)1023;
+  size_t exb = (((size_t)kTcPieceSlots * n * sizeof(int)) + 1023) & ~(size_t)1023;
+  return 2048 + exb + 1024 + (size_t)kTcPieceSlots * kTcMaxSlices * one + 256;
+}
+
+static bool make_map(CUtensorMap* m, void* ptr, int n, int ld) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+void tc_work_bind(TcWork& w, void* base, int n) {
+  // host-side bookkeeping lives in a heap object; the device arena holds the pieces
+  TcBuffers* tb = new TcBuffers();
+  tb->n = n;
+  tb->ld = ld_for(n);
+  size_t one = ((size_t)n * tb->ld * 2 + 1023) & ~(size_t)1023;
+  uint8_t* p = (uint8_t*)(((uintptr_t)base + 1023) & ~(uintptr_t)1023);
+  tb->err = (int*)p;
+  tb->dpieces = (__nv_bfloat16**)(p + 64);
+  p += 2048;
+  tb->ex = (int*)p;
+  p += (((size_t)kTcPieceSlots * n * sizeof(int)) + 1023) & ~(size_t)1023;
+  tb->maps_ok = true;
+  for (int s = 0; s < kTcPieceSlots; ++s)
+    for (int k = 0; k < kTcMaxSlices; ++k) {
+      tb->piece[s][k] = (__nv_bfloat16*)p;
+      p += one;
+      tb->maps_ok = tb->maps_ok && make_map(&tb->map[s][k], tb->piece[s][k], n, tb->ld);
+    }
+  w.base = tb;
+  w.bytes = tc_work_bytes(n);
+  cudaMemset(tb->err, 0, sizeof(int));
+  cudaMemcpy(tb->dpieces, tb->piece, sizeof(tb->piece), cudaMemcpyHostToDevice);
+}
+
+void tc_work_release(TcWork& w) {
+  delete (TcBuffers*)w.base;
+  w.base = nullptr;
+}
+
+bool tc_available() { return encode_fn() != nullptr; }
+
+bool tc_ready(const TcWork& w) { return w.base && ((TcBuffers*)w.base)->maps_ok; }
+
+int* tc_error_flag(const TcWork& w) { return w.base ? ((TcBuffers*)w.base)->err : nullptr; }
+
+void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int slices, int transpose) {
+  TcBuffers* tb = (TcBuffers*)w.base;
+  int n = tb->n;
+  int* ex = tb->ex + (size_t)slot * n;
+  row_exponent_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, X, transpose, ex);
+  count_launch();
+  size_t tot = (size_t)n * tb->ld;
+  split_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, X, tb->ld, slices, transpose, ex,
+                                                                   tb->dpieces + (size_t)slot * kTcMaxSlices);
+  count_launch();
+}
+
+void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, double alpha, double* C, int sym) {
+  TcBuffers* tb = (TcBuffers*)w.base;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    attr = true;
+  }
+  TcMaps maps;
+  for (int k = 0; k < kTcMaxSlices; ++k) {
+    maps.a[k] = tb->map[slotA][k];
+    maps.b[k] = tb->map[slotB][k];
+  }
+  // slice pairs (a, b) with a + b < slices, smallest terms first
+  int slices = (terms == 10) ? 4 : (terms == 6) ? 3 : (terms == 3) ? 2 : 1;
+  SegTable seg;
+  seg.nseg = 0;
+  for (int d = slices - 1; d >= 0; --d)
+    for (int a = 0; a <= d; ++a) {
+      seg.a[seg.nseg] = a;
+      seg.b[seg.nseg] = d - a;
+      ++seg.nseg;
+    }
+  int n = tb->n;
+  dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, tb->err);
+  count_launch();
+}
+
 }  // namespace kx

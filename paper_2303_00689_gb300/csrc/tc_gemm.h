@@ -4,17 +4,25 @@
 
 namespace kx {
 
+// slots of BF16 slice matrices (each holds up to kTcMaxSlices slices of one n x n operand)
+constexpr int kTcPieceSlots = 6;
+constexpr int kTcMaxSlices = 4;
+enum TcSlot { kSlotQs = 0, kSlotQ = 1, kSlotQt = 2, kSlotT0 = 3, kSlotT1 = 4, kSlotSpare = 5 };
+
 struct TcWork {
-  void* base = nullptr;
+  void* base = nullptr;   // host-side bookkeeping (tensor maps, piece pointers)
   size_t bytes = 0;
 };
 size_t tc_work_bytes(int n);
-void tc_work_bind(TcWork& w, void* base, int n);
-bool tc_available();
-// D = Qs Qs^T (symmetric), operands split into `pieces` BF16 parts
-void tc_syrk_split(cudaStream_t s, int n, const double* Qs, double* D, TcWork& w, int pieces);
-// transpose_first: C = Q^T M Q ; else C = Q M Q^T (M symmetric); C symmetric
-void tc_similarity(cudaStream_t s, int n, const double* Q, const double* M, double* C, TcWork& w,
-                   int transpose_first);
+void tc_work_bind(TcWork& w, void* device_base, int n);
+void tc_work_release(TcWork& w);
+bool tc_available();                  // driver entry point for tensor maps present
+bool tc_ready(const TcWork& w);       // tensor maps encoded for this handle
+int* tc_error_flag(const TcWork& w);  // device word set when a bounded wait expired
+// X (n x n FP64) -> `slices` fixed-point BF16 slices in slot (transpose != 0 slices X^T)
+void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int slices, int transpose);
+// C = alpha * sum over `terms` (1, 3, 6 or 10 for 1-4 slices) slice products A_a B_b^T
+void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, double alpha, double* C,
+             int sym);
 
 }  // namespace kx

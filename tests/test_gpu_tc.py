@@ -1,0 +1,73 @@
+"""tcgen05 BF16 GEMM (the contraction under eqs. 19 and 36 in the mixed path) vs numpy.
+
+The expected value is built independently in numpy: each FP64 row is cut
+into fixed-point slices of 8 bits relative to 2^e (e = frexp exponent of the
+row's max |x|), and the kept slice products are summed in FP64.  Each
+product of two slices is an integer times one power of two per (row, row,
+slice pair), so the GPU's FP32 chunk sums are exact and its result must
+equal the FP64 sum up to the double-float (hi + lo) rounding: <= 2^-40 of
+sum |a||b| per entry.
+"""
+import numpy as np
+import pytest
+
+import paper_2303_00689_gb300 as kx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2303_00689_gb300 import build
+    build.build()
+
+
+def slices(X, k):
+    """Fixed-point slices: slice a of row r is rint(x 2^(7 + 8a - e_r)) 2^-(7 + 8a - e_r)."""
+    _, e = np.frexp(np.max(np.abs(X), axis=1))
+    e = np.where(np.max(np.abs(X), axis=1) > 0, e, 0)[:, None]
+    out = []
+    r = X.copy()
+    for a in range(k):
+        sh = 7 + 8 * a - e
+        v = np.ldexp(np.rint(np.ldexp(r, sh)), -sh)
+        assert np.max(np.abs(np.ldexp(v, sh))) <= 128
+        out.append(v)
+        r = r - v
+    return out
+
+
+SLICES = {1: 1, 3: 2, 6: 3, 10: 4}
+
+
+def kept_pairs(k):
+    return [(a, d - a) for d in range(k) for a in range(d + 1)]
+
+
+@pytest.mark.parametrize("n", [64, 128, 200, 333, 700])
+@pytest.mark.parametrize("terms", [1, 3, 6, 10])
+def test_tc_gemm_is_exact_on_slices(n, terms):
+    rng = np.random.default_rng(n * 10 + terms)
+    A = rng.normal(size=(n, n)) * np.exp(rng.normal(size=(n, 1)))   # rows of different scale
+    B = rng.normal(size=(n, n))
+    C = kx.sim_debug_tc_gemm(A, B, terms=terms)
+    k = SLICES[terms]
+    pa, pb = slices(A, k), slices(B, k)
+    ref = sum(pa[i] @ pb[j].T for i, j in kept_pairs(k))
+    scale = np.abs(A) @ np.abs(B).T
+    assert np.max(np.abs(C - ref) / scale) < 2.0 ** -40
+    # and the sliced product approaches the FP64 product as slices are added
+    exact = A @ B.T
+    bound = {1: 2.0 ** -4, 3: 2.0 ** -12, 6: 2.0 ** -20, 10: 2.0 ** -28}[terms]
+    assert np.max(np.abs(C - exact) / scale) < bound
+
+
+@pytest.mark.parametrize("n", [100, 256, 300])
+def test_tc_gemm_symmetric_output(n):
+    rng = np.random.default_rng(n)
+    A = rng.normal(size=(n, n))
+    C = kx.sim_debug_tc_gemm(A, A, terms=10, sym=True)
+    assert np.array_equal(C, C.T)
+    exact = A @ A.T
+    scale = np.abs(A) @ np.abs(A).T
+    assert np.max(np.abs(C - exact) / scale) < 2.0 ** -26
