@@ -216,6 +216,28 @@ void* sim_stream(sim_handle* h);
 
 void sim_destroy(sim_handle* h);
 
+/* sim_tc_gemm_noalloc -- the tensor-core slice product of sim_debug_tc_gemm
+ * without any memory allocation.  The paper has no counterpart: it serves
+ * callers that cannot allocate device memory, such as a serving process that
+ * has divided all of the GPU's memory into fixed slots under a hard budget,
+ * or a latency-critical loop where cudaMalloc/cudaFree would synchronise the
+ * device.
+ *   A, B  DEVICE n x n row-major FP64 inputs; C: DEVICE n x n FP64 output
+ *   n     1..256 (larger n returns SIM_EINVAL)
+ *   terms 1, 3, 6 or 10 (1-4 fixed-point BF16 slices per operand)
+ *   sym   != 0: compute the upper tiles only and mirror (A B^T symmetric)
+ *   stream cudaStream_t (NULL = legacy default stream); the call returns
+ *          after synchronising it
+ * Scratch: one fixed device array of about 1 MB inside the library (held by
+ * every device that loads it, until exit), shared by all calls: calls that
+ * overlap on the GPU race and must be serialised by the caller.  The error
+ * flag in it is cleared on every call.  The first call on a device looks up
+ * the array's address (cudaGetSymbolAddress, device current) and should come
+ * before any stream capture on that device.  Returns SIM_ETIMEOUT if a
+ * bounded pipeline wait expired. */
+int sim_tc_gemm_noalloc(int n, const double* A, const double* B, int terms, int sym, double* C,
+                        void* stream);
+
 /* sim_debug_tc_gemm -- test hook for the tensor-core contraction used by the
  * mixed-precision path (no counterpart in the paper; it exposes one building
  * block of eq. 19 / eq. 36 so tests can check it in isolation).

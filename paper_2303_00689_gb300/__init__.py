@@ -26,6 +26,7 @@ EXPORTED = (
     "sim_last_result", "sim_get_state", "sim_set_state", "sim_get_matrix", "sim_get_vector",
     "sim_profile_enable", "sim_phase_count", "sim_phase_name", "sim_phase_times",
     "sim_launch_count", "sim_stream", "sim_destroy", "sim_last_error", "sim_debug_tc_gemm",
+    "sim_tc_gemm_noalloc",
 )
 
 
@@ -92,6 +93,8 @@ def lib():
         L.sim_destroy.argtypes = [C.c_void_p]
         L.sim_destroy.restype = None
         L.sim_debug_tc_gemm.argtypes = [C.c_int, dp, dp, C.c_int, C.c_int, dp]
+        L.sim_tc_gemm_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                          C.c_void_p]
         L.sim_last_error.argtypes = []
         L.sim_last_error.restype = C.c_char_p
         _lib_handle = L
@@ -258,6 +261,12 @@ def sim_debug_tc_gemm(A, B, terms=1, sym=False):
     out = np.empty((n, n))
     _check(lib().sim_debug_tc_gemm(n, _dptr(A), _dptr(B), int(terms), 1 if sym else 0, _dptr(out)))
     return out
+
+
+def sim_tc_gemm_noalloc(n, A_dev, B_dev, terms, sym, C_dev, stream=None):
+    """Device pointers (ints) in and out; returns the raw status code."""
+    return lib().sim_tc_gemm_noalloc(int(n), C.c_void_p(A_dev), C.c_void_p(B_dev), int(terms),
+                                     1 if sym else 0, C.c_void_p(C_dev), C.c_void_p(stream or 0))
 
 
 def sim_last_error():

@@ -346,6 +346,26 @@ __global__ void split_bf16_kernel(int n, const double* __restrict__ X, int ld, i
   }
 }
 
+// same slicing as split_bf16_kernel, slices at base + a * stride (no pointer table)
+__global__ void split_bf16_strided_kernel(int n, const double* __restrict__ X, int ld, int slices, int transpose,
+                                          const int* __restrict__ ex, __nv_bfloat16* __restrict__ base,
+                                          size_t stride) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)n * ld;
+  if (t >= tot) return;
+  int i = (int)(t / ld), j = (int)(t % ld);
+  double x = 0.0;
+  if (j < n) x = transpose ? X[(size_t)j * n + i] : X[(size_t)i * n + j];
+  int e = ex[i];
+  for (int a = 0; a < slices; ++a) {
+    int sh = 7 + 8 * a - e;
+    double q = rint(ldexp(x, sh));
+    double v = ldexp(q, -sh);
+    base[a * stride + t] = __double2bfloat16(v);
+    x -= v;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -472,6 +492,46 @@ void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, d
   int n = tb->n;
   dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
   tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, tb->err);
+  count_launch();
+}
+
+int tc_ld(int n) { return ld_for(n); }
+
+bool tc_encode_map(CUtensorMap* m, void* ptr, int n, int ld) { return make_map(m, ptr, n, ld); }
+
+void tc_split_strided(cudaStream_t s, int n, int ld, const double* X, int slices, int transpose, int* ex,
+                      __nv_bfloat16* base, size_t stride) {
+  row_exponent_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, X, transpose, ex);
+  count_launch();
+  size_t tot = (size_t)n * ld;
+  split_bf16_strided_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, X, ld, slices, transpose, ex, base,
+                                                                           stride);
+  count_launch();
+}
+
+void tc_gemm_on_maps(cudaStream_t s, int n, const CUtensorMap* mapsA, const CUtensorMap* mapsB, int terms,
+                     double alpha, double* C, int sym, int* err) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    attr = true;
+  }
+  TcMaps maps;
+  for (int k = 0; k < kTcMaxSlices; ++k) {
+    maps.a[k] = mapsA[k];
+    maps.b[k] = mapsB[k];
+  }
+  int slices = (terms == 10) ? 4 : (terms == 6) ? 3 : (terms == 3) ? 2 : 1;
+  SegTable seg;
+  seg.nseg = 0;
+  for (int d = slices - 1; d >= 0; --d)
+    for (int a = 0; a <= d; ++a) {
+      seg.a[seg.nseg] = a;
+      seg.b[seg.nseg] = d - a;
+      ++seg.nseg;
+    }
+  dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, err);
   count_launch();
 }
 

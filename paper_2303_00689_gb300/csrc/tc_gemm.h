@@ -1,5 +1,7 @@
 // Tensor-core (tcgen05) GEMMs for the mixed-precision path (internal header).
 #pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace kx {
@@ -24,5 +26,13 @@ void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int sl
 // C = alpha * sum over `terms` (1, 3, 6 or 10 for 1-4 slices) slice products A_a B_b^T
 void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, double alpha, double* C,
              int sym);
+
+// Building blocks on caller-provided buffers (used by the allocation-free entry point)
+int tc_ld(int n);                                                   // padded slice row length
+bool tc_encode_map(CUtensorMap* m, void* ptr, int n, int ld);       // BF16 slice tensor map
+void tc_split_strided(cudaStream_t s, int n, int ld, const double* X, int slices, int transpose, int* ex,
+                      __nv_bfloat16* base, size_t stride);
+void tc_gemm_on_maps(cudaStream_t s, int n, const CUtensorMap* mapsA, const CUtensorMap* mapsB, int terms,
+                     double alpha, double* C, int sym, int* err);
 
 }  // namespace kx
