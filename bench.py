@@ -290,6 +290,26 @@ def oracle_sample():
             "seconds_per_step": s}
 
 
+def profile_run(args):
+    """Short fixed run for ncu: the 840-atom workload from the diagonal guess
+    (no SCF), `warmup` + `steps` MD steps; prints launch counts to stderr."""
+    import paper_2303_00689_gb300 as kx
+    from paper_2303_00689_gb300 import build
+    build.build()
+    mol, V, table = _inputs()
+    X0 = 0.5 * np.eye(mol.norb)      # all-carbon: 4 valence electrons over 4 orbitals, per spin
+    prec = kx.SIM_PREC_FP64 if args.precision == "fp64" else kx.SIM_PREC_MIXED
+    c0 = kx.sim_launch_count()
+    h = _create(kx, mol, V, table, prec, P0=X0)
+    c1 = kx.sim_launch_count()
+    kx.sim_step(h, args.warmup, records=False)
+    c2 = kx.sim_launch_count()
+    kx.sim_step(h, args.steps, records=False)
+    c3 = kx.sim_launch_count()
+    kx.sim_destroy(h)
+    print(f"launches create={c1 - c0} warmup={c2 - c1} steps={c3 - c2}", file=sys.stderr, flush=True)
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -316,9 +336,14 @@ def main():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-timeout", type=float, default=600.0)
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--profile-run", action="store_true",
+                   help="short run for ncu (no SCF, no baselines); prints launch counts")
     args = p.parse_args()
     if args.oracle_sample:
         print(json.dumps(oracle_sample()), flush=True)
+        return
+    if args.profile_run:
+        profile_run(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -41,11 +41,11 @@ static const double kAlphaDamp = 0.0055;
 // phases timed with CUDA events
 // ---------------------------------------------------------------------------
 enum Phase {
-  PH_PAIRS = 0, PH_FOCK, PH_TRIDIAG, PH_TRIEIG, PH_BACKTR, PH_DENSITY, PH_FORCES,
+  PH_PAIRS = 0, PH_FOCK, PH_TRIDIAG, PH_BISECT, PH_TRIEIG, PH_BACKTR, PH_DENSITY, PH_FORCES,
   PH_KRY_FOCK, PH_KRY_GEMM, PH_KRY_BLAS, PH_UPDATE, PH_COUNT
 };
 static const char* kPhaseNames[PH_COUNT] = {
-    "pair_integrals", "fock_build", "eig_tridiag", "eig_tridiag_solve", "eig_backtransform",
+    "pair_integrals", "fock_build", "eig_tridiag", "eig_bisection", "eig_tridiag_vectors", "eig_backtransform",
     "density_gemm", "energy_forces", "krylov_fock", "krylov_dmpt_gemm", "krylov_blas", "integrate"};
 
 struct sim_handle {
@@ -249,11 +249,14 @@ static int eig(sim_handle* h) {
   int st = eig_tridiagonalize(h->stream, h->n, h->Fock, h->ew, &h->sc->status, h->sms);
   phase_end(h);
   if (st != 0) return fail(SIM_EINTERNAL, "tridiagonalisation launch failed (code " + std::to_string(st) + ")");
+  phase_begin(h, PH_BISECT);
+  eig_bisect(h->stream, h->n, h->eps, h->ew);
+  phase_end(h);
   phase_begin(h, PH_TRIEIG);
-  eig_tridiagonal_solve(h->stream, h->n, h->eps, h->Q, h->ew);
+  eig_vectors(h->stream, h->n, h->eps, h->Q, h->ew);
   phase_end(h);
   phase_begin(h, PH_BACKTR);
-  eig_backtransform(h->stream, h->n, h->Q, h->ew);
+  eig_backtransform(h->stream, h->n, h->Q, h->ew, mixed(h) ? &h->tw : nullptr);
   phase_end(h);
   return SIM_OK;
 }
@@ -817,8 +820,9 @@ int sim_phase_times(sim_handle* h, double* ms, long long* launches, double* work
   double w[PH_COUNT] = {
       np * (117.0 * 4.0) * 8.0,             // pair blocks + derivatives written (bytes)
       (np * 116.0 + 4.0 * n * n) * 8.0,     // h + F: pair blocks read, matrices written (bytes)
-      4.0 / 3.0 * n * n * n,                // tridiagonalisation flops
-      0.0,                                  // bisection + inverse iteration
+      4.0 / 3.0 * n * n * n,                // Householder tridiagonalisation, algorithmic flops
+      0.0,                                  // bisection
+      0.0,                                  // inverse iteration
       2.0 * n * n * n,                      // back-transformation flops
       n * n * n,                            // D0 = Q f Q^T (symmetric) flops
       np * (468.0) * 8.0,                   // force contraction bytes

@@ -10,19 +10,25 @@
 //     counter/generation pair with a bounded spin: on expiry the kernel sets
 //     kStatusTimeout and returns.
 //  2. Eigenvalues of the tridiagonal matrix by bisection on Sturm counts,
-//     one thread per eigenvalue (ascending order by construction).
-//  3. Eigenvectors by inverse iteration with a partially pivoted
+//     one thread per eigenvalue (ascending order by construction): a coarse
+//     FP32 phase, an FP64 bracket check, then FP64 bisection.
+//  3. Eigenvectors by inverse iteration (two steps) with a partially pivoted
 //     tridiagonal LU, one thread per cluster of close eigenvalues; members of
 //     a cluster are re-orthogonalised (modified Gram-Schmidt) in order.
-//  4. Back-transformation Q = H_0 ... H_{n-3} Z with blocks of 64 reflectors
-//     in compact WY form (I - V T V^T) applied by FP64 GEMMs.
+//  4. Back-transformation Q = H_0 ... H_{n-3} Z with blocks of reflectors in
+//     compact WY form (I - V T V^T): FP64 GEMMs (64 per block) on the FP64
+//     path; on the mixed path (128 per block) the two large products
+//     V^T Z and V (T W) run on the tensor cores with 4 fixed-point BF16
+//     slices, while the T factor and T W stay in FP64.
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_gemm.h"
 
 namespace kx {
 
 constexpr int kTriThreads = 512;
-constexpr int kBtBlock = 64;          // reflectors per back-transform block
+constexpr int kBtBlock = 64;          // reflectors per back-transform block (FP64 path)
+constexpr int kBtBlockTc = 128;       // reflectors per back-transform block (tensor-core path)
 constexpr double kEps = 2.220446049250313e-16;
 
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
@@ -189,28 +195,86 @@ __global__ void gersh_kernel(int n, const double* __restrict__ d, const double* 
   }
 }
 
+// Number of eigenvalues of T below x: sign changes of the leading principal
+// minors p_j = (d_j - x) p_{j-1} - e_{j-1}^2 p_{j-2} (Sturm sequence), kept in
+// range by exact power-of-two rescaling, so each step is two FMAs and no
+// division.  An exact zero minor counts as negative (the pivmin convention).
 __device__ __forceinline__ int sturm_count(int n, const double* __restrict__ d,
-                                           const double* __restrict__ e2, double x, double pivmin) {
-  double q = d[0] - x;
-  if (fabs(q) <= pivmin) q = -pivmin;
-  int c = (q < 0.0);
+                                           const double* __restrict__ e2, double x, double) {
+  // FP64 work per step is one multiply and one FMA; signs, zero tests and the
+  // rescaling test read the bit pattern with integer instructions.
+  double pm = 1.0;                    // p_{j-1}
+  double p = d[0] - x;                // p_0
+  long long b = __double_as_longlong(p);
+  int sp = (b < 0 || (b & 0x7FFFFFFFFFFFFFFFLL) == 0) ? 1 : 0;   // 1: negative (zero counts as negative)
+  int c = sp;
   for (int j = 1; j < n; ++j) {
-    q = d[j] - x - e2[j - 1] / q;
-    if (fabs(q) <= pivmin) q = -pivmin;
-    c += (q < 0.0);
+    double pn = fma(d[j] - x, p, -e2[j - 1] * pm);
+    pm = p;
+    p = pn;
+    b = __double_as_longlong(pn);
+    int zero = (b & 0x7FFFFFFFFFFFFFFFLL) == 0;
+    int sn = zero ? (sp ^ 1) : (int)((unsigned long long)b >> 63);
+    c += sn ^ sp;
+    sp = sn;
+    int ex = (int)((b >> 52) & 0x7FF);             // biased exponent of p_j
+    if (ex > 1023 + 400) {
+      p *= 0x1p-400; pm *= 0x1p-400;
+    } else if (ex < 1023 - 400 && (int)((__double_as_longlong(pm) >> 52) & 0x7FF) < 1023 - 400) {
+      p *= 0x1p400; pm *= 0x1p400;
+    }
   }
   return c;
 }
 
+// FP32 Sturm count (ratio form with a pivot floor) for the coarse phase
+__device__ __forceinline__ int sturm_count_f32(int n, const double* __restrict__ d,
+                                               const double* __restrict__ e2, float x, float pivmin) {
+  float q = (float)d[0] - x;
+  if (fabsf(q) <= pivmin) q = -pivmin;
+  int c = (q < 0.0f);
+  for (int j = 1; j < n; ++j) {
+    q = ((float)d[j] - x) - (float)e2[j - 1] / q;
+    if (fabsf(q) <= pivmin) q = -pivmin;
+    c += (q < 0.0f);
+  }
+  return c;
+}
+
+// Eigenvalue i of T: a coarse FP32 bisection down to ~2^-22 of the
+// Gershgorin width, a bracket check in FP64 (widened until
+// count(lo) <= i < count(hi)), then FP64 bisection to full accuracy.
 __global__ void bisect_kernel(int n, const double* __restrict__ d, const double* __restrict__ e2,
                               const double* __restrict__ scal, double* __restrict__ ev) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double lo = scal[0], hi = scal[1], pivmin = scal[3];
+  const double glo = scal[0], ghi = scal[1], pivmin = scal[3];
+  const double width = ghi - glo;
+  // coarse phase (FP32)
+  float lo32 = (float)glo, hi32 = (float)ghi;
+  const float piv32 = fmaxf((float)(1e-30 * fmax(1.0, width)), 1e-30f);
+  for (int it = 0; it < 22; ++it) {
+    float mid = 0.5f * (lo32 + hi32);
+    if (sturm_count_f32(n, d, e2, mid, piv32) > i) hi32 = mid; else lo32 = mid;
+  }
+  // bracket check in FP64, widening geometrically if the FP32 counts erred
+  double w = fmax((double)hi32 - (double)lo32, 1e-12 * width);
+  double lo = (double)lo32 - w, hi = (double)hi32 + w;
+  for (int k = 0; k < 60; ++k) {
+    bool ok_lo = (lo <= glo) || sturm_count(n, d, e2, lo, pivmin) <= i;
+    bool ok_hi = (hi >= ghi) || sturm_count(n, d, e2, hi, pivmin) > i;
+    if (ok_lo && ok_hi) break;
+    w *= 4.0;
+    if (!ok_lo) lo = fmax(glo, lo - w);
+    if (!ok_hi) hi = fmin(ghi, hi + w);
+  }
+  // 1e-12 of the spectral range is far below what the occupations and the DMPT
+  // weights resolve, and inverse iteration converges from such a shift in two steps
+  const double tol = fmax(2.0 * kEps * fmax(fabs(lo), fabs(hi)), 1e-12 * fmax(1.0, scal[2])) + pivmin;
   for (int it = 0; it < 200; ++it) {
     double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;
-    if (hi - lo <= 2.0 * kEps * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    if (hi - lo <= tol) break;
     if (sturm_count(n, d, e2, mid, pivmin) > i) hi = mid; else lo = mid;
   }
   ev[i] = 0.5 * (lo + hi);
@@ -284,8 +348,9 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
       }
     }
     if (fabs(LU(dd, n - 1)) < tiny) LU(dd, n - 1) = (LU(dd, n - 1) >= 0.0) ? tiny : -tiny;
+    for (int r = 0; r < n; ++r) LU(dd, r) = 1.0 / LU(dd, r);      // reciprocal pivots
     for (int r = 0; r < n; ++r) ZC(r, j) = start_value(r, j);
-    for (int it = 0; it < 3; ++it) {
+    for (int it = 0; it < 2; ++it) {
       // forward (L with pivots)
       for (int r = 0; r < n - 1; ++r) {
         double br = ZC(r, j), br1 = ZC(r + 1, j);
@@ -296,11 +361,11 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
           ZC(r + 1, j) = br - LU(dl, r) * br1;
         }
       }
-      // backward (U, three diagonals)
-      ZC(n - 1, j) = ZC(n - 1, j) / LU(dd, n - 1);
-      if (n > 1) ZC(n - 2, j) = (ZC(n - 2, j) - LU(du, n - 2) * ZC(n - 1, j)) / LU(dd, n - 2);
+      // backward (U, three diagonals; dd holds reciprocal pivots)
+      ZC(n - 1, j) = ZC(n - 1, j) * LU(dd, n - 1);
+      if (n > 1) ZC(n - 2, j) = (ZC(n - 2, j) - LU(du, n - 2) * ZC(n - 1, j)) * LU(dd, n - 2);
       for (int r = n - 3; r >= 0; --r)
-        ZC(r, j) = (ZC(r, j) - LU(du, r) * ZC(r + 1, j) - LU(du2, r) * ZC(r + 2, j)) / LU(dd, r);
+        ZC(r, j) = (ZC(r, j) - LU(du, r) * ZC(r + 1, j) - LU(du2, r) * ZC(r + 2, j)) * LU(dd, r);
       // scale, re-orthogonalise within the cluster, normalise
       double mx = 0.0;
       for (int r = 0; r < n; ++r) mx = fmax(mx, fabs(ZC(r, j)));
@@ -322,30 +387,40 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
 #undef ZC
 }
 
-// T factor of a block of kb reflectors (forward, columnwise): one block
+// T factor of a block of kb reflectors (forward, columnwise): one block,
+// T held in shared memory, each entry a dot product split over 4 partial sums
 __global__ void tfactor_kernel(int kb, const double* __restrict__ tau, const double* __restrict__ G,
                                int ldg, double* __restrict__ T, int ldt) {
-  __shared__ double tcol[kBtBlock];
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) T[(e / kb) * ldt + e % kb] = 0.0;
+  extern __shared__ double ts[];          // kb x kb
+  __shared__ double gcol[kBtBlockTc];
+  const int i = threadIdx.x;
+  for (int e = i; e < kb * kb; e += blockDim.x) ts[e] = 0.0;
   __syncthreads();
   for (int j = 0; j < kb; ++j) {
-    int i = threadIdx.x;
-    if (i < j) {
-      double acc = 0.0;
-      for (int l = i; l < j; ++l) acc += T[i * ldt + l] * G[l * ldg + j];
-      tcol[i] = -tau[j] * acc;
-    }
+    if (i < j) gcol[i] = G[i * ldg + j];
     __syncthreads();
-    if (i < j) T[i * ldt + j] = tcol[i];
-    if (i == j) T[j * ldt + j] = tau[j];
+    if (i < j) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int l = i;
+      for (; l + 3 < j; l += 4) {
+        a0 = fma(ts[i * kb + l], gcol[l], a0);
+        a1 = fma(ts[i * kb + l + 1], gcol[l + 1], a1);
+        a2 = fma(ts[i * kb + l + 2], gcol[l + 2], a2);
+        a3 = fma(ts[i * kb + l + 3], gcol[l + 3], a3);
+      }
+      for (; l < j; ++l) a0 = fma(ts[i * kb + l], gcol[l], a0);
+      ts[i * kb + j] = -tau[j] * ((a0 + a1) + (a2 + a3));
+    }
+    if (i == j) ts[j * kb + j] = tau[j];
     __syncthreads();
   }
+  for (int e = i; e < kb * kb; e += blockDim.x) T[(e / kb) * ldt + e % kb] = ts[e];
 }
 
 size_t eig_work_bytes(int n) {
   size_t nn = (size_t)n * n;
   size_t doubles = nn /*A*/ + nn /*Vst*/ + 4 * (size_t)n /*d e e2 tau*/ + 2 * (size_t)n /*pbuf*/ +
-                   5 * nn /*lu*/ + 2 * (size_t)kBtBlock * kBtBlock + 2 * (size_t)kBtBlock * n + 16;
+                   5 * nn /*lu*/ + 2 * (size_t)kBtBlockTc * kBtBlockTc + 2 * (size_t)kBtBlockTc * n + 16;
   return doubles * sizeof(double) + 64 + (size_t)n * sizeof(int) + 256;
 }
 
@@ -360,10 +435,10 @@ void eig_work_bind(EigWork& w, void* base, int n) {
   w.tau = p; p += n;
   w.pbuf = p; p += 2 * (size_t)n;
   w.lu = p; p += 5 * nn;
-  w.Tm = p; p += (size_t)kBtBlock * kBtBlock;
-  w.Gm = p; p += (size_t)kBtBlock * kBtBlock;
-  w.Wt = p; p += (size_t)kBtBlock * n;
-  w.Wt2 = p; p += (size_t)kBtBlock * n;
+  w.Tm = p; p += (size_t)kBtBlockTc * kBtBlockTc;
+  w.Gm = p; p += (size_t)kBtBlockTc * kBtBlockTc;
+  w.Wt = p; p += (size_t)kBtBlockTc * n;
+  w.Wt2 = p; p += (size_t)kBtBlockTc * n;
   w.scal = p; p += 16;
   w.bar = (unsigned*)p; p += 8;
   w.clus = (int*)p;
@@ -378,7 +453,7 @@ int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* 
   long long work = (long long)n * n;
   int blocks = (int)((work + (1 << 16) - 1) >> 16);
   if (blocks < 1) blocks = 1;
-  if (blocks > sm_count) blocks = sm_count;
+  if (blocks > sm_count) blocks = sm_count;           // one block per SM (two were slower)
   size_t smem = (3 * (size_t)n + 32) * sizeof(double);
   static size_t smem_set = 0;
   if (smem > 48 * 1024 && smem > smem_set) {
@@ -401,21 +476,93 @@ int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* 
   return 0;
 }
 
-void eig_tridiagonal_solve(cudaStream_t s, int n, double* eps, double* Q, EigWork& w) {
+void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w) {
   if (n <= 0) return;
   // 2. eigenvalues
   gersh_kernel<<<1, 1024, 0, s>>>(n, w.d, w.e, w.e2, w.scal);
   count_launch();
-  bisect_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, w.d, w.e2, w.scal, eps);
-  count_launch();
-  // 3. eigenvectors of the tridiagonal matrix
-  cluster_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, eps, w.scal, w.clus);
-  count_launch();
-  invit_kernel<<<(n + 63) / 64, 64, 0, s>>>(n, w.d, w.e, eps, w.scal, w.clus, w.lu, Q);
+  bisect_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e2, w.scal, eps);   // spread over all SMs
   count_launch();
 }
 
-void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w) {
+void eig_vectors(cudaStream_t s, int n, const double* eps, double* Q, EigWork& w) {
+  if (n <= 0) return;
+  // 3. eigenvectors of the tridiagonal matrix
+  cluster_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, eps, w.scal, w.clus);
+  count_launch();
+  invit_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e, eps, w.scal, w.clus, w.lu, Q);
+  count_launch();
+}
+
+// tensor-core back-transformation (mixed path), carried out on Z^T so that
+// every large operand is K-major: Z^T <- Z^T (I - V T V^T)^T block by block,
+//   U  = Z^T_sub V      (n x kb)      tensor cores, 4 slices
+//   U2 = U T^T          (n x kb)      FP64
+//   Z^T_sub -= U2 V^T                 tensor cores, 4 slices
+// with the Gram matrix V^T V of the block (for T) also on the tensor cores.
+__global__ void transpose_sq_kernel(int n, const double* __restrict__ A, double* __restrict__ At) {
+  __shared__ double tile[32][33];
+  int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int i = i0 + r, j = j0 + threadIdx.x;
+    tile[r][threadIdx.x] = (i < n && j < n) ? A[(size_t)i * n + j] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int j = j0 + r, i = i0 + threadIdx.x;
+    if (i < n && j < n) At[(size_t)j * n + i] = tile[threadIdx.x][r];
+  }
+}
+
+static void transpose_sq(cudaStream_t s, int n, const double* A, double* At) {
+  int t = (n + 31) / 32;
+  transpose_sq_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(n, A, At);
+  count_launch();
+}
+
+static void eig_backtransform_tc(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork& tw) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kBtBlockTc * kBtBlockTc * (int)sizeof(double));
+    attr = true;
+  }
+  const int nref = n - 2;
+  const int nblk = (nref + kBtBlockTc - 1) / kBtBlockTc;
+  const size_t stride = tc_slot_stride(tw);
+  int* err = tc_error_flag(tw);
+  double* Zt = w.A;                      // tridiagonalisation workspace is free now
+  transpose_sq(s, n, Q, Zt);
+  for (int b = nblk - 1; b >= 0; --b) {
+    int k0 = b * kBtBlockTc, k1 = (k0 + kBtBlockTc < nref) ? k0 + kBtBlockTc : nref;
+    int kb = k1 - k0, c0 = k0 + 1, m = n - c0;
+    const double* Vb = w.Vst + (size_t)k0 * n + c0;      // kb x m, ld n
+    double* Zs = Zt + c0;                                // n x m, ld n
+    int ldm = tc_ld(m), ldk = tc_ld(kb);
+    __nv_bfloat16* sV = tc_slot_base(tw, kSlotQ);
+    tc_split_rc(s, kb, m, Vb, n, 0, 4, tc_slot_exponents(tw, kSlotQ), sV, ldm, stride);
+    tc_gemm_rc(s, kb, kb, m, sV, ldm, stride, sV, ldm, stride, 10, 1.0, w.Gm, kBtBlockTc, 0, err);
+    tfactor_kernel<<<1, kBtBlockTc, kb * kb * sizeof(double), s>>>(kb, w.tau + k0, w.Gm, kBtBlockTc, w.Tm,
+                                                                    kBtBlockTc);
+    count_launch();
+    __nv_bfloat16* sZ = tc_slot_base(tw, kSlotT0);
+    tc_split_rc(s, n, m, Zs, n, 0, 4, tc_slot_exponents(tw, kSlotT0), sZ, ldm, stride);
+    tc_gemm_rc(s, n, kb, m, sZ, ldm, stride, sV, ldm, stride, 10, 1.0, w.Wt, kb, 0, err);      // U
+    dgemm(s, 0, 1, n, kb, kb, 1.0, w.Wt, kb, w.Tm, kBtBlockTc, 0.0, w.Wt2, kb);               // U2 = U T^T
+    __nv_bfloat16* sU = tc_slot_base(tw, kSlotT1);
+    tc_split_rc(s, n, kb, w.Wt2, kb, 0, 4, tc_slot_exponents(tw, kSlotT1), sU, ldk, stride);
+    __nv_bfloat16* sVt = tc_slot_base(tw, kSlotQt);
+    tc_split_rc(s, m, kb, Vb, n, 1, 4, tc_slot_exponents(tw, kSlotQt), sVt, ldk, stride);
+    tc_gemm_rc(s, n, m, kb, sU, ldk, stride, sVt, ldk, stride, 10, -1.0, Zs, n, 1, err);      // Zs -= U2 V^T
+  }
+  transpose_sq(s, n, Zt, Q);
+}
+
+void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork* tw) {
+  if (tw && n > 2) {
+    eig_backtransform_tc(s, n, Q, w, *tw);
+    return;
+  }
   // 4. back-transformation, last block of reflectors first
   int nref = n - 2;
   if (nref > 0) {
@@ -425,7 +572,7 @@ void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w) {
       int kb = k1 - k0, c0 = k0 + 1, m = n - c0;
       const double* Vb = w.Vst + (size_t)k0 * n + c0;
       dgemm(s, 0, 1, kb, kb, m, 1.0, Vb, n, Vb, n, 0.0, w.Gm, kBtBlock);
-      tfactor_kernel<<<1, kBtBlock, 0, s>>>(kb, w.tau + k0, w.Gm, kBtBlock, w.Tm, kBtBlock);
+      tfactor_kernel<<<1, kBtBlock, kb * kb * sizeof(double), s>>>(kb, w.tau + k0, w.Gm, kBtBlock, w.Tm, kBtBlock);
       count_launch();
       dgemm(s, 0, 0, kb, n, m, 1.0, Vb, n, Q + (size_t)c0 * n, n, 0.0, w.Wt, n);
       dgemm(s, 0, 0, kb, n, kb, 1.0, w.Tm, kBtBlock, w.Wt, n, 0.0, w.Wt2, n);
@@ -438,8 +585,9 @@ int symmetric_eig(cudaStream_t s, int n, const double* F, double* eps, double* Q
                   int* status, int sm_count) {
   int rc = eig_tridiagonalize(s, n, F, w, status, sm_count);
   if (rc) return rc;
-  eig_tridiagonal_solve(s, n, eps, Q, w);
-  eig_backtransform(s, n, Q, w);
+  eig_bisect(s, n, eps, w);
+  eig_vectors(s, n, eps, Q, w);
+  eig_backtransform(s, n, Q, w, nullptr);
   return 0;
 }
 

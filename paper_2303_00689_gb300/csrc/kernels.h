@@ -62,8 +62,11 @@ void eig_work_bind(EigWork& w, void* base, int n);
 // F (n x n symmetric, row-major) -> eps ascending, Q (eigenvectors as columns),
 // in three stages (tridiagonalise; tridiagonal eigenpairs into Q; back-transform Q)
 int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* status, int sm_count);
-void eig_tridiagonal_solve(cudaStream_t s, int n, double* eps, double* Q, EigWork& w);
-void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w);
+void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w);                       // eigenvalues
+void eig_vectors(cudaStream_t s, int n, const double* eps, double* Q, EigWork& w);     // tridiagonal vectors
+struct TcWork;
+// tw != nullptr: the large products run on the tensor cores (mixed path)
+void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork* tw);
 int symmetric_eig(cudaStream_t s, int n, const double* F, double* eps, double* Q, EigWork& w,
                   int* status, int sm_count);
 

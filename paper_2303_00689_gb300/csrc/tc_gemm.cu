@@ -4,8 +4,9 @@
 // A_i (M x K) and B_j (N x K) are BF16 slices of FP64 operands, both stored
 // K-major (row-major with K contiguous, leading dimension ld).
 //
-// Slicing is fixed-point per row: with 2^e_r > max_k |X_rk|, slice a of row r
-// holds integers of magnitude <= 128 times 2^(e_r - 7 - 8a), so
+// Slicing is fixed-point per row: with 2^e_r > max_k |X_rk|, the slices of
+// x are the balanced base-256 digits (in [-128, 128]) of the integer
+// round(x 2^(7 + 8(S-1) - e_r)), digit a scaled by 2^(e_r - 7 - 8a), so
 // X ~ X0 + X1 + ... keeps 8 bits per slice relative to the row maximum.  A
 // product of slices a and b of rows r and s is then an integer of magnitude
 // <= 2^14 times the single scale 2^(e_r + e_s - 14 - 8(a + b)); a sum of up
@@ -167,7 +168,7 @@ __device__ __forceinline__ void twosum_acc(float& hi, float& lo, float b) {
 
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ TcMaps maps, SegTable seg, int M, int N, int K, double alpha,
-                   double* __restrict__ C, int ldc, int sym, int* err) {
+                   double* __restrict__ C, int ldc, int sym, int beta, int* err) {
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (sym && bi > bj) return;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -299,6 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (col >= N) break;
           if (sym && row > col) continue;
           double v = alpha * ((double)hi[j] + (double)lo[j]);
+          if (beta) v += C[(size_t)row * ldc + col];
           C[(size_t)row * ldc + col] = v;
           if (sym && row != col) C[(size_t)col * ldc + row] = v;
         }
@@ -312,18 +314,56 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// per-row scale exponent: e_r with max_k |X_rk| < 2^e_r (rows of X^T if transpose)
+// per-row scale exponent: e_r with max_k |X_rk| < 2^e_r (rows of X^T if transpose).
+// |x| is compared as an integer (the bit patterns of non-negative doubles
+// order like their values), keeping the FP64 pipe free.
+__device__ __forceinline__ int exponent_of_max(unsigned long long bits) {
+  // frexp exponent of a finite double given by its |x| bit pattern (0 -> 0)
+  if (bits == 0) return 0;
+  int be = (int)(bits >> 52);
+  if (be == 0) {                       // subnormal
+    int lz = __clzll((long long)(bits & 0xFFFFFFFFFFFFFULL)) - 12;
+    return -1021 - lz;
+  }
+  return be - 1022;
+}
+
 __global__ void row_exponent_kernel(int n, const double* __restrict__ X, int transpose, int* __restrict__ ex) {
   int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (r >= n) return;
-  double m = 0.0;
-  for (int k = lane; k < n; k += 32) m = fmax(m, fabs(transpose ? X[(size_t)k * n + r] : X[(size_t)r * n + k]));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) {
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);   // m = f 2^e with 0.5 <= f < 1, so m < 2^e
-    ex[r] = e;
+  unsigned long long m = 0;
+  for (int k = lane; k < n; k += 32) {
+    double v = transpose ? X[(size_t)k * n + r] : X[(size_t)r * n + k];
+    unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+    m = (b > m) ? b : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (t > m) ? t : m;
+  }
+  if (lane == 0) ex[r] = exponent_of_max(m);
+}
+
+// Balanced base-256 digits of X = round(x 2^(7 + 8(S-1) - e)): slice a is digit
+// a (most significant first) times 2^(e - 7 - 8a).  Digits lie in [-128, 128],
+// so each slice value is exact in BF16.  FP64 work per element: one scaling
+// and one rounding conversion; the digits come from integer arithmetic.
+__device__ __forceinline__ void slice_value(double x, int e, int slices, __nv_bfloat16* out, size_t stride,
+                                            size_t t) {
+  const int top = 7 + 8 * (slices - 1);
+  long long X = __double2ll_rn(ldexp(x, top - e));
+  int dig[kTcMaxSlices];
+  for (int a = slices - 1; a > 0; --a) {
+    int r = (int)(X & 0xFF);
+    if (r >= 128) r -= 256;
+    dig[a] = r;
+    X = (X - r) >> 8;
+  }
+  dig[0] = (int)X;
+  for (int a = 0; a < slices; ++a) {
+    float v = ldexpf((float)dig[a], e - 7 - 8 * a);
+    out[a * stride + t] = __float2bfloat16_rn(v);
   }
 }
 
@@ -336,14 +376,17 @@ __global__ void split_bf16_kernel(int n, const double* __restrict__ X, int ld, i
   int i = (int)(t / ld), j = (int)(t % ld);
   double x = 0.0;
   if (j < n) x = transpose ? X[(size_t)j * n + i] : X[(size_t)i * n + j];
-  int e = ex[i];
-  for (int a = 0; a < slices; ++a) {
-    int sh = 7 + 8 * a - e;                      // slice unit is 2^-sh
-    double q = rint(ldexp(x, sh));               // integer, |q| <= 128
-    double v = ldexp(q, -sh);
-    P[a][t] = __double2bfloat16(v);              // exact: |q| <= 256
-    x -= v;
+  const int top = 7 + 8 * (slices - 1);
+  long long Xi = __double2ll_rn(ldexp(x, top - ex[i]));
+  int dig[kTcMaxSlices];
+  for (int a = slices - 1; a > 0; --a) {
+    int r = (int)(Xi & 0xFF);
+    if (r >= 128) r -= 256;
+    dig[a] = r;
+    Xi = (Xi - r) >> 8;
   }
+  dig[0] = (int)Xi;
+  for (int a = 0; a < slices; ++a) P[a][t] = __float2bfloat16_rn(ldexpf((float)dig[a], ex[i] - 7 - 8 * a));
 }
 
 // same slicing as split_bf16_kernel, slices at base + a * stride (no pointer table)
@@ -356,14 +399,38 @@ __global__ void split_bf16_strided_kernel(int n, const double* __restrict__ X, i
   int i = (int)(t / ld), j = (int)(t % ld);
   double x = 0.0;
   if (j < n) x = transpose ? X[(size_t)j * n + i] : X[(size_t)i * n + j];
-  int e = ex[i];
-  for (int a = 0; a < slices; ++a) {
-    int sh = 7 + 8 * a - e;
-    double q = rint(ldexp(x, sh));
-    double v = ldexp(q, -sh);
-    base[a * stride + t] = __double2bfloat16(v);
-    x -= v;
+  slice_value(x, ex[i], slices, base, stride, t);
+}
+
+// per-row exponent of op(X), op(X) = X (rows x cols, ldx) or X^T (X stored cols x rows)
+__global__ void row_exponent_general_kernel(int rows, int cols, const double* __restrict__ X, int ldx,
+                                            int transpose, int* __restrict__ ex) {
+  int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  unsigned long long m = 0;
+  for (int k = lane; k < cols; k += 32) {
+    double v = transpose ? X[(size_t)k * ldx + r] : X[(size_t)r * ldx + k];
+    unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+    m = (b > m) ? b : m;
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (t > m) ? t : m;
+  }
+  if (lane == 0) ex[r] = exponent_of_max(m);
+}
+
+__global__ void split_general_kernel(int rows, int cols, const double* __restrict__ X, int ldx, int transpose,
+                                     int slices, const int* __restrict__ ex, __nv_bfloat16* __restrict__ base,
+                                     int ld, size_t stride) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)rows * ld;
+  if (t >= tot) return;
+  int i = (int)(t / ld), j = (int)(t % ld);
+  double x = 0.0;
+  if (j < cols) x = transpose ? X[(size_t)j * ldx + i] : X[(size_t)i * ldx + j];
+  slice_value(x, ex[i], slices, base, stride, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -404,6 +471,19 @@ size_t tc_work_bytes(int n) {
   size_t one = ((size_t)n * ld * 2 + 1023) & ~(size_t)1023;
   size_t exb = (((size_t)kTcPieceSlots * n * sizeof(int)) + 1023) & ~(size_t)1023;
   return 2048 + exb + 1024 + (size_t)kTcPieceSlots * kTcMaxSlices * one + 256;
+}
+
+static bool make_map_rc(CUtensorMap* m, void* ptr, int rows, int cols, int ld) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 static bool make_map(CUtensorMap* m, void* ptr, int n, int ld) {
@@ -491,11 +571,63 @@ void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, d
     }
   int n = tb->n;
   dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
-  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, tb->err);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, 0, tb->err);
   count_launch();
 }
 
 int tc_ld(int n) { return ld_for(n); }
+
+__nv_bfloat16* tc_slot_base(const TcWork& w, int slot) { return ((TcBuffers*)w.base)->piece[slot][0]; }
+size_t tc_slot_stride(const TcWork& w) {
+  TcBuffers* tb = (TcBuffers*)w.base;
+  return (size_t)(tb->piece[0][1] - tb->piece[0][0]);
+}
+int* tc_slot_exponents(const TcWork& w, int slot) {
+  TcBuffers* tb = (TcBuffers*)w.base;
+  return tb->ex + (size_t)slot * tb->n;
+}
+
+// Slices of op(X) (rows x cols, K = cols) into `base` with row length ld and
+// slice stride `stride` elements; ex receives the row exponents.
+void tc_split_rc(cudaStream_t s, int rows, int cols, const double* X, int ldx, int transpose, int slices, int* ex,
+                 __nv_bfloat16* base, int ld, size_t stride) {
+  row_exponent_general_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(rows, cols, X, ldx, transpose, ex);
+  count_launch();
+  size_t tot = (size_t)rows * ld;
+  split_general_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(rows, cols, X, ldx, transpose, slices, ex,
+                                                                       base, ld, stride);
+  count_launch();
+}
+
+// C (M x N, ldc) = alpha * sum slice products A_a B_b^T (+ C if beta), A: M x K slices, B: N x K slices
+int tc_gemm_rc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, int lda, size_t astride,
+               const __nv_bfloat16* Bbase, int ldb, size_t bstride, int terms, double alpha, double* C, int ldc,
+               int beta, int* err) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    attr = true;
+  }
+  int slices = (terms == 10) ? 4 : (terms == 6) ? 3 : (terms == 3) ? 2 : 1;
+  TcMaps maps;
+  for (int a = 0; a < kTcMaxSlices; ++a) {
+    int sa = (a < slices) ? a : 0;
+    if (!make_map_rc(&maps.a[a], (void*)(Abase + sa * astride), M, K, lda)) return -1;
+    if (!make_map_rc(&maps.b[a], (void*)(Bbase + sa * bstride), N, K, ldb)) return -1;
+  }
+  SegTable seg;
+  seg.nseg = 0;
+  for (int d = slices - 1; d >= 0; --d)
+    for (int a = 0; a <= d; ++a) {
+      seg.a[seg.nseg] = a;
+      seg.b[seg.nseg] = d - a;
+      ++seg.nseg;
+    }
+  dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, M, N, K, alpha, C, ldc, 0, beta, err);
+  count_launch();
+  return 0;
+}
 
 bool tc_encode_map(CUtensorMap* m, void* ptr, int n, int ld) { return make_map(m, ptr, n, ld); }
 
@@ -531,7 +663,7 @@ void tc_gemm_on_maps(cudaStream_t s, int n, const CUtensorMap* mapsA, const CUte
       ++seg.nseg;
     }
   dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
-  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, err);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, 0, err);
   count_launch();
 }
 

@@ -35,4 +35,16 @@ void tc_split_strided(cudaStream_t s, int n, int ld, const double* X, int slices
 void tc_gemm_on_maps(cudaStream_t s, int n, const CUtensorMap* mapsA, const CUtensorMap* mapsB, int terms,
                      double alpha, double* C, int sym, int* err);
 
+// General shapes (back-transformation): slices of op(X) (rows x cols, K = cols, row
+// length ld, slice stride `stride` elements) and C (M x N, ldc) (+)= alpha sum A_a B_b^T
+void tc_split_rc(cudaStream_t s, int rows, int cols, const double* X, int ldx, int transpose, int slices, int* ex,
+                 __nv_bfloat16* base, int ld, size_t stride);
+int tc_gemm_rc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, int lda, size_t astride,
+               const __nv_bfloat16* Bbase, int ldb, size_t bstride, int terms, double alpha, double* C, int ldc,
+               int beta, int* err);
+// raw access to a slot's slice buffers (for the back-transformation)
+__nv_bfloat16* tc_slot_base(const TcWork& w, int slot);
+size_t tc_slot_stride(const TcWork& w);
+int* tc_slot_exponents(const TcWork& w, int slot);
+
 }  // namespace kx

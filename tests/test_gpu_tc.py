@@ -2,7 +2,8 @@
 
 The expected value is built independently in numpy: each FP64 row is cut
 into fixed-point slices of 8 bits relative to 2^e (e = frexp exponent of the
-row's max |x|), and the kept slice products are summed in FP64.  Each
+row's max |x|; balanced base-256 digits of the rounded scaled value), and
+the kept slice products are summed in FP64.  Each
 product of two slices is an integer times one power of two per (row, row,
 slice pair), so the GPU's FP32 chunk sums are exact and its result must
 equal the FP64 sum up to the double-float (hi + lo) rounding: <= 2^-40 of
@@ -23,17 +24,23 @@ def built():
 
 
 def slices(X, k):
-    """Fixed-point slices: slice a of row r is rint(x 2^(7 + 8a - e_r)) 2^-(7 + 8a - e_r)."""
-    _, e = np.frexp(np.max(np.abs(X), axis=1))
-    e = np.where(np.max(np.abs(X), axis=1) > 0, e, 0)[:, None]
+    """Fixed-point slices: the balanced base-256 digits of round(x 2^(7 + 8(k-1) - e_r)),
+    digit a scaled by 2^(e_r - 7 - 8a), with e_r the frexp exponent of the row's max |x|."""
+    amax = np.max(np.abs(X), axis=1)
+    _, e = np.frexp(amax)
+    e = np.where(amax > 0, e, 0)[:, None]
+    Xi = np.rint(np.ldexp(X, 7 + 8 * (k - 1) - e)).astype(np.int64)
+    digits = [None] * k
+    for a in range(k - 1, 0, -1):
+        r = Xi & 0xFF
+        r = np.where(r >= 128, r - 256, r)
+        digits[a] = r
+        Xi = (Xi - r) >> 8
+    digits[0] = Xi
     out = []
-    r = X.copy()
     for a in range(k):
-        sh = 7 + 8 * a - e
-        v = np.ldexp(np.rint(np.ldexp(r, sh)), -sh)
-        assert np.max(np.abs(np.ldexp(v, sh))) <= 128
-        out.append(v)
-        r = r - v
+        assert np.max(np.abs(digits[a])) <= 128
+        out.append(np.ldexp(digits[a].astype(np.float64), e - 7 - 8 * a))
     return out
 
 
