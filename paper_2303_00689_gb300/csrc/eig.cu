@@ -121,18 +121,38 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
     double* pb = pbuf + (size_t)(k & 1) * n;
     for (int i = k + 1 + gw; i < n; i += totw) {
       double* row = A + (size_t)i * n;
-      double acc = 0.0;
+      double acc = 0.0, acc2 = 0.0, acc3 = 0.0, acc4 = 0.0;   // four chains hide the FP64 latency
       if (prev) {
-        double vi = vp[i], wi = wp[i];
-        for (int j = k + 1 + lane; j < n; j += 32) {
-          double a = row[j] - (vi * wp[j] + wi * vp[j]);
+        const double vi = vp[i], wi = wp[i];
+        int j = k + 1 + lane;
+        for (; j + 96 < n; j += 128) {
+          double a = fma(-vi, wp[j], fma(-wi, vp[j], row[j]));
+          double b = fma(-vi, wp[j + 32], fma(-wi, vp[j + 32], row[j + 32]));
+          double c = fma(-vi, wp[j + 64], fma(-wi, vp[j + 64], row[j + 64]));
+          double e = fma(-vi, wp[j + 96], fma(-wi, vp[j + 96], row[j + 96]));
           row[j] = a;
-          acc += a * vc[j];
+          row[j + 32] = b;
+          row[j + 64] = c;
+          row[j + 96] = e;
+          acc = fma(a, vc[j], acc);
+          acc2 = fma(b, vc[j + 32], acc2);
+          acc3 = fma(c, vc[j + 64], acc3);
+          acc4 = fma(e, vc[j + 96], acc4);
+        }
+        for (; j < n; j += 32) {
+          double a = fma(-vi, wp[j], fma(-wi, vp[j], row[j]));
+          row[j] = a;
+          acc = fma(a, vc[j], acc);
         }
       } else {
-        for (int j = k + 1 + lane; j < n; j += 32) acc += row[j] * vc[j];
+        int j = k + 1 + lane;
+        for (; j + 32 < n; j += 64) {
+          acc = fma(row[j], vc[j], acc);
+          acc2 = fma(row[j + 32], vc[j + 32], acc2);
+        }
+        for (; j < n; j += 32) acc = fma(row[j], vc[j], acc);
       }
-      acc = warp_sum(acc);
+      acc = warp_sum((acc + acc2) + (acc3 + acc4));
       if (lane == 0) pb[i] = t * acc;
     }
     if (!grid_barrier(bar, gridDim.x, status)) return;
