@@ -83,6 +83,14 @@ typedef struct sim_param_table {
   double v[4][SIM_NFIELDS];
 } sim_param_table;
 
+/* Kernel approximation in the electronic equation of motion (eq. 25). */
+enum sim_kernel {
+  SIM_KERNEL_KRYLOV = 0,  /* low-rank Krylov subspace approximation, eqs. 31-35 */
+  SIM_KERNEL_XL = 1       /* original XL-BOMD scaled delta function K = -c I
+                             (Results, Langevin run of C240 2+); no response
+                             calculations, rank reported as 0              */
+};
+
 /* ---- configuration ------------------------------------------------------ */
 typedef struct sim_config {
   double Te;          /* electronic temperature, K (eq. 7); > 0                */
@@ -104,11 +112,16 @@ typedef struct sim_config {
   int scf_accept;     /* 1: if the SCF does not reach scf_tol in scf_max
                          iterations, start from the lowest-residual P seen
                          (reported by sim_scf_info) instead of failing       */
+  int kernel;         /* enum sim_kernel: the kernel K of Xddot = -w^2 K (D0 - X)
+                         (eq. 25) used by sim_step                           */
+  double xl_c;        /* SIM_KERNEL_XL only: K = -xl_c I (Results, C240 2+
+                         run: c = 1 originally, 0.9 tuned); any finite value */
 } sim_config;
 
 /* Fills a config with the defaults used by the paper-shaped workloads:
  * Te 1000 K, dt 0.5 fs, m = 4, fixed rank, FP64, scf_tol 1e-10,
- * scf_max 5000, mix 0.1, linear mixing, device 0, private stream.
+ * scf_max 5000, mix 0.1, linear mixing, device 0, private stream,
+ * Krylov kernel (xl_c = 1).
  * The SCF prints max|D[P] - P| per iteration to stderr when the
  * environment variable KSAXL_SCF_TRACE is set. */
 void sim_config_default(sim_config* cfg);

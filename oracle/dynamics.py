@@ -13,6 +13,11 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   X(t+dt) = 2X(t) - X(t-dt) - kappa sum V_i c_i + alpha sum_k c_k X(t-k dt);
   evaluate at (R(t+dt), X(t+dt)); Rdot(t+dt) = Rdot(t+dt/2) + dt/2 Rddot(t+dt).
 * constant of motion (eq. 26): E_tot = sum M Rdot^2 / 2 + U(R, X).
+* comparison mode (Results, Langevin run of C240 2+): the original XL-BOMD
+  kernel, a scaled delta function K = -c I, so K (D0 - X) = -c (D0 - X) and
+  no response calculation is made (Config.xl_c = c; None selects eq. 34).
+  Pin: with every two-electron integral zero the Jacobian of D0 - X is -I, so
+  the Krylov kernel at any rank equals the c = 1 kernel exactly.
 
 The damping constants (kappa, alpha, c_k for k_max = 6) are given in the
 paper's ref. 24 and not printed in the paper; the values below are that
@@ -36,8 +41,9 @@ CK = np.array([-14.0, 36.0, -27.0, -2.0, 12.0, -6.0, 1.0])
 
 class Config:
     def __init__(self, Te=1000.0, dt=0.5, m=4, m_min=None, tol=0.0,
-                 scf_tol=1e-10, scf_max=2000, mix=0.1):
+                 scf_tol=1e-10, scf_max=2000, mix=0.1, xl_c=None):
         self.Te, self.dt, self.m = Te, dt, m
+        self.xl_c = xl_c
         self.m_min = m if m_min is None else m_min
         self.tol, self.scf_tol, self.scf_max, self.mix = tol, scf_tol, scf_max, mix
 
@@ -83,7 +89,11 @@ def evaluate(sysm, R, X, cfg, krylov=True):
     forces = ham.forces(sysm, R, D, X, pairs)
     out = dict(F=F, h=h, G=G, D=D, eps=eps, Q=Q, f=f, mu=mu, S=S, U=U, Vnn=Vnn,
                forces=forces, Te=cfg.Te)
-    if krylov:
+    if krylov and cfg.xl_c is not None:
+        W0 = D - X
+        out.update(K=-cfg.xl_c * W0,
+                   krylov=dict(rank=0, c=np.zeros(0), fit=[], V=[], W=[]))
+    elif krylov:
         Lam = el.divided_differences(eps, f, mu, cfg.beta)
 
         def response(V):

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libksaxl.so")
 
 SIM_OK, SIM_PENDING, SIM_EINVAL, SIM_ENOMEM, SIM_ENOCONV, SIM_ENUMERIC, SIM_ETIMEOUT, SIM_EINTERNAL = range(8)
 SIM_PREC_FP64, SIM_PREC_MIXED = 0, 1
+SIM_KERNEL_KRYLOV, SIM_KERNEL_XL = 0, 1
 SIM_MAT_X, SIM_MAT_D0, SIM_MAT_FOCK, SIM_MAT_H, SIM_MAT_KERNEL, SIM_MAT_Q = range(6)
 SIM_NFIELDS = 23
 
@@ -40,7 +41,8 @@ class sim_config(C.Structure):
     _fields_ = [("Te", C.c_double), ("dt", C.c_double), ("m_max", C.c_int), ("m_min", C.c_int),
                 ("krylov_tol", C.c_double), ("precision", C.c_int), ("scf_tol", C.c_double),
                 ("scf_max", C.c_int), ("scf_mix", C.c_double), ("device", C.c_int),
-                ("stream", C.c_void_p), ("scf_krylov", C.c_int), ("scf_accept", C.c_int)]
+                ("stream", C.c_void_p), ("scf_krylov", C.c_int), ("scf_accept", C.c_int),
+                ("kernel", C.c_int), ("xl_c", C.c_double)]
 
 
 class sim_param_table(C.Structure):

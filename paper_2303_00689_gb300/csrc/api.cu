@@ -218,30 +218,33 @@ static void dmpt_prepare(sim_handle* h) {
   tc_split(h->stream, h->tw, kSlotQt, h->Q, 3, 1);
 }
 
-// D1 = Q [Lambda o (Q^T F1 Q - dmu I)] Q^T (eq. 36)
+// D1 = Q [Lambda o (Q^T F1 Q - dmu I)] Q^T (eq. 36).  Every launch reads the
+// device flag sc->active and returns at once when the Krylov fit has already
+// converged, so unused Krylov vectors cost no work and no host round trip.
 static void dmpt(sim_handle* h, const double* F1, double* D1) {
   cudaStream_t s = h->stream;
   int n = h->n;
+  const int* g = &h->sc->active;
   if (mixed(h)) {
     // three fixed-point BF16 slices per operand, six slice products (24 bits per row scale)
-    tc_split(s, h->tw, kSlotT0, F1, 3, 0);
-    tc_gemm(s, h->tw, kSlotQt, kSlotT0, 6, 1.0, h->T1, 0);      // T1 = Q^T F1
-    tc_split(s, h->tw, kSlotT1, h->T1, 3, 0);
-    tc_gemm(s, h->tw, kSlotT1, kSlotQt, 6, 1.0, h->T2, 1);      // T2 = (Q^T F1) Q
+    tc_split(s, h->tw, kSlotT0, F1, 3, 0, g);
+    tc_gemm(s, h->tw, kSlotQt, kSlotT0, 6, 1.0, h->T1, 0, g);      // T1 = Q^T F1
+    tc_split(s, h->tw, kSlotT1, h->T1, 3, 0, g);
+    tc_gemm(s, h->tw, kSlotT1, kSlotQt, 6, 1.0, h->T2, 1, g);      // T2 = (Q^T F1) Q
     launch_dmu(s, n, h->T2, h->eps, h->f, h->beta, h->sc);
     launch_dmpt_y(s, n, h->T2, h->eps, h->f, h->beta, h->sc, h->Y);
-    tc_split(s, h->tw, kSlotT0, h->Y, 3, 0);
-    tc_gemm(s, h->tw, kSlotQ, kSlotT0, 6, 1.0, h->T1, 0);       // T1 = Q Y
-    tc_split(s, h->tw, kSlotT1, h->T1, 3, 0);
-    tc_gemm(s, h->tw, kSlotT1, kSlotQ, 6, 1.0, D1, 1);          // D1 = (Q Y) Q^T
+    tc_split(s, h->tw, kSlotT0, h->Y, 3, 0, g);
+    tc_gemm(s, h->tw, kSlotQ, kSlotT0, 6, 1.0, h->T1, 0, g);       // T1 = Q Y
+    tc_split(s, h->tw, kSlotT1, h->T1, 3, 0, g);
+    tc_gemm(s, h->tw, kSlotT1, kSlotQ, 6, 1.0, D1, 1, g);          // D1 = (Q Y) Q^T
     return;
   }
-  dgemm(s, 0, 0, n, n, n, 1.0, F1, n, h->Q, n, 0.0, h->T1, n);         // T1 = F1 Q
-  dgemm(s, 1, 0, n, n, n, 1.0, h->Q, n, h->T1, n, 0.0, h->T2, n, 1);   // T2 = Q^T T1
+  dgemm(s, 0, 0, n, n, n, 1.0, F1, n, h->Q, n, 0.0, h->T1, n, 0, g);         // T1 = F1 Q
+  dgemm(s, 1, 0, n, n, n, 1.0, h->Q, n, h->T1, n, 0.0, h->T2, n, 1, g);      // T2 = Q^T T1
   launch_dmu(s, n, h->T2, h->eps, h->f, h->beta, h->sc);
   launch_dmpt_y(s, n, h->T2, h->eps, h->f, h->beta, h->sc, h->Y);
-  dgemm(s, 0, 0, n, n, n, 1.0, h->Q, n, h->Y, n, 0.0, h->T1, n);       // T1 = Q Y
-  dgemm(s, 0, 1, n, n, n, 1.0, h->T1, n, h->Q, n, 0.0, D1, n, 1);      // D1 = T1 Q^T
+  dgemm(s, 0, 0, n, n, n, 1.0, h->Q, n, h->Y, n, 0.0, h->T1, n, 0, g);       // T1 = Q Y
+  dgemm(s, 0, 1, n, n, n, 1.0, h->T1, n, h->Q, n, 0.0, D1, n, 1, g);         // D1 = T1 Q^T
 }
 
 static int eig(sim_handle* h) {
@@ -279,8 +282,8 @@ static void krylov_kernel(sim_handle* h, const double* P) {
     launch_krylov_orth(s, nn, k, h->Vk, src, h->Vk[k], h->sc, h->red, h->coef);
     phase_end(h);
     phase_begin(h, PH_KRY_FOCK);
-    launch_pack_diag(s, m, h->Vk[k], h->Vd);
-    launch_build_fock(s, m, pd, h->tab, h->Vk[k], h->Vd, nullptr, h->F1);
+    launch_pack_diag(s, m, h->Vk[k], h->Vd, &h->sc->active);
+    launch_build_fock(s, m, pd, h->tab, h->Vk[k], h->Vd, nullptr, h->F1, &h->sc->active);
     phase_end(h);
     phase_begin(h, PH_KRY_GEMM);
     dmpt(h, h->F1, h->D1);
@@ -323,7 +326,13 @@ static int evaluate(sim_handle* h, bool krylov = true) {
   launch_forces(s, m, pd, h->tab, h->D, X, h->Dd, h->Pd, h->g, h->F);
   phase_end(h);
   if (!krylov) return SIM_OK;
-  krylov_kernel(h, X);   // K (D0 - X), eqs. 31-34
+  if (h->cfg.kernel == SIM_KERNEL_XL) {
+    phase_begin(h, PH_KRY_BLAS);
+    launch_scaled_residual(s, nn, h->D, X, h->cfg.xl_c, h->W0, h->K, h->sc, h->red);   // -c (D0 - X)
+    phase_end(h);
+  } else {
+    krylov_kernel(h, X);   // K (D0 - X), eqs. 31-34
+  }
   phase_begin(h, PH_KRY_BLAS);
   launch_check_finite(s, (size_t)3 * h->N, h->F, h->sc);
   launch_check_finite(s, nn, h->K, h->sc);
@@ -468,6 +477,8 @@ void sim_config_default(sim_config* c) {
   c->scf_max = 5000;
   c->scf_mix = 0.1;
   c->scf_krylov = 0;
+  c->kernel = SIM_KERNEL_KRYLOV;
+  c->xl_c = 1.0;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -561,7 +572,8 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
   if (!cfg || !table || !Z || !R || !out || natoms < 1) return fail(SIM_EINVAL, "null argument or natoms < 1");
   *out = nullptr;
   if (!(cfg->Te > 0.0) || !(cfg->dt > 0.0) || cfg->m_max < 1 || cfg->m_max > 16 || cfg->m_min < 1 ||
-      cfg->m_min > cfg->m_max || cfg->scf_max < 1 || !(cfg->scf_mix >= 0.0 && cfg->scf_mix < 1.0))
+      cfg->m_min > cfg->m_max || cfg->scf_max < 1 || !(cfg->scf_mix >= 0.0 && cfg->scf_mix < 1.0) ||
+      (cfg->kernel != SIM_KERNEL_KRYLOV && cfg->kernel != SIM_KERNEL_XL) || !std::isfinite(cfg->xl_c))
     return fail(SIM_EINVAL, "invalid configuration");
   if (cfg->precision != SIM_PREC_FP64 && cfg->precision != SIM_PREC_MIXED)
     return fail(SIM_EINVAL, "unknown precision mode");

@@ -162,7 +162,9 @@ struct DotArgs {
   const double* b[kMaxDots];
 };
 
-__global__ void dots_partial_kernel(size_t len, int cnt, DotArgs args, double* __restrict__ partial) {
+__global__ void dots_partial_kernel(size_t len, int cnt, DotArgs args, double* __restrict__ partial,
+                                    const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ double red[32];
   for (int k = 0; k < cnt; ++k) {
     const double* a = args.a[k];
@@ -176,7 +178,8 @@ __global__ void dots_partial_kernel(size_t len, int cnt, DotArgs args, double* _
 }
 
 __global__ void dots_final_kernel(int cnt, int nparts, const double* __restrict__ partial,
-                                  double* __restrict__ out) {
+                                  double* __restrict__ out, const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ double red[32];
   for (int k = 0; k < cnt; ++k) {
     double loc = 0.0;
@@ -186,13 +189,14 @@ __global__ void dots_final_kernel(int cnt, int nparts, const double* __restrict_
   }
 }
 
+// gate (nullable): both kernels return at once when *gate == 0
 static void dots(cudaStream_t s, size_t len, int cnt, const double* const* A, const double* const* B,
-                 double* out, double* partial) {
+                 double* out, double* partial, const int* gate = nullptr) {
   DotArgs args;
   for (int k = 0; k < cnt; ++k) { args.a[k] = A[k]; args.b[k] = B[k]; }
-  dots_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(len, cnt, args, partial);
+  dots_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(len, cnt, args, partial, gate);
   count_launch();
-  dots_final_kernel<<<1, kRedThreads, 0, s>>>(cnt, kRedBlocks, partial, out);
+  dots_final_kernel<<<1, kRedThreads, 0, s>>>(cnt, kRedBlocks, partial, out, gate);
   count_launch();
 }
 
@@ -304,14 +308,14 @@ void launch_krylov_orth(cudaStream_t s, size_t len, int k, double* const* Vs, co
       const double* a[16];
       const double* b[16];
       for (int i = 0; i < k; ++i) { a[i] = Vs[i]; b[i] = cur; }
-      dots(s, len, k, a, b, coef, partial);
+      dots(s, len, k, a, b, coef, partial, &sc->active);
     }
     sub_combo_kernel<<<nb, 256, 0, s>>>(len, k, V, coef, cur, v, sc);
     count_launch();
     cur = v;
   }
   const double* a2[2] = {v, src};
-  dots(s, len, 2, a2, a2, coef + 16, partial);
+  dots(s, len, 2, a2, a2, coef + 16, partial, &sc->active);
   normalize_kernel<<<nb, 256, 0, s>>>(len, v, coef + 16, sc);
   count_launch();
 }
@@ -408,7 +412,7 @@ void launch_krylov_w(cudaStream_t s, size_t len, int k, const double* D1, const 
   a[k + 1] = Wk;
   b[k + 1] = W0;
   double* dv = partial + kRedBlocks * kMaxDots + 32;
-  dots(s, len, k + 2, a, b, dv, partial);
+  dots(s, len, k + 2, a, b, dv, partial, &sc->active);
   gram_solve_kernel<<<1, 1, 0, s>>>(k, dv, sc, tol, m_min);
   count_launch();
 }
@@ -426,6 +430,37 @@ void launch_krylov_combine(cudaStream_t s, size_t len, int mmax, double* const* 
   PtrList V;
   for (int i = 0; i < mmax; ++i) V.p[i] = Vs[i];
   combine_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, mmax, V, sc, K);
+  count_launch();
+}
+
+// Original XL-BOMD kernel K = -c I (Results, C240 2+ Langevin run):
+// W0 = D0 - X and K (D0 - X) = -c W0; no Krylov vectors, rank 0.
+__global__ void scaled_residual_kernel(size_t len, const double* __restrict__ D, const double* __restrict__ X,
+                                       double c, double* __restrict__ W0, double* __restrict__ K) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= len) return;
+  double w = D[t] - X[t];
+  W0[t] = w;
+  K[t] = -c * w;
+}
+
+__global__ void scaled_residual_final(const double* n2, Scalars* sc) {
+  sc->w0n2 = n2[0];
+  sc->res2 = n2[0];
+  sc->rank = 0;
+  sc->fit = 0.0;
+  sc->active = 0;
+  for (int i = 0; i < 16; ++i) sc->c[i] = 0.0;
+}
+
+void launch_scaled_residual(cudaStream_t s, size_t len, const double* D, const double* X, double c, double* W0,
+                            double* K, Scalars* sc, double* partial) {
+  scaled_residual_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, D, X, c, W0, K);
+  count_launch();
+  const double* a[1] = {W0};
+  double* tmp = partial + kRedBlocks * kMaxDots;
+  dots(s, len, 1, a, a, tmp, partial);
+  scaled_residual_final<<<1, 1, 0, s>>>(tmp, sc);
   count_launch();
 }
 

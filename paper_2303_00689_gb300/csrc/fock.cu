@@ -45,7 +45,8 @@ __device__ __forceinline__ double onec(const Elem& e, int a, int b, int c, int d
 }
 
 __global__ void pack_diag_kernel(int N, int n, const int* __restrict__ off, const double* __restrict__ M,
-                                 double* __restrict__ out) {
+                                 double* __restrict__ out, const int* gate) {
+  if (gate && *gate == 0) return;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * 10) return;
   int A = t / 10, p = t % 10;
@@ -123,7 +124,8 @@ __global__ void h_offdiag_kernel(MolDev m, PairDev pd, ElemTable tab, double* __
 
 __global__ void fock_diag_kernel(MolDev m, PairDev pd, ElemTable tab, const double* __restrict__ P,
                                  const double* __restrict__ Pd, const double* __restrict__ h,
-                                 double* __restrict__ out) {
+                                 double* __restrict__ out, const int* gate) {
+  if (gate && *gate == 0) return;
   int A = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (A >= m.N) return;
   double acc[10];
@@ -146,7 +148,8 @@ __global__ void fock_diag_kernel(MolDev m, PairDev pd, ElemTable tab, const doub
 }
 
 __global__ void fock_offdiag_kernel(MolDev m, PairDev pd, ElemTable tab, const double* __restrict__ P,
-                                    const double* __restrict__ h, double* __restrict__ out) {
+                                    const double* __restrict__ h, double* __restrict__ out, const int* gate) {
+  if (gate && *gate == 0) return;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= m.npair) return;
   int A = m.pA[t], B = m.pB[t];
@@ -169,7 +172,8 @@ __global__ void fock_offdiag_kernel(MolDev m, PairDev pd, ElemTable tab, const d
 }
 
 // copy the strict upper triangle onto the lower one (32 x 32 tiles)
-__global__ void mirror_upper_kernel(int n, double* __restrict__ a) {
+__global__ void mirror_upper_kernel(int n, double* __restrict__ a, const int* gate) {
+  if (gate && *gate == 0) return;
   __shared__ double tile[32][33];
   int bi = blockIdx.y, bj = blockIdx.x;
   if (bi > bj) return;
@@ -269,14 +273,14 @@ __global__ void force_atom_kernel(MolDev m, const double* __restrict__ g, double
 
 static inline int blocks_for(long long work, int per) { return (int)((work + per - 1) / per); }
 
-void launch_pack_diag(cudaStream_t s, const MolDev& m, const double* M, double* out) {
-  pack_diag_kernel<<<blocks_for((long long)m.N * 10, 256), 256, 0, s>>>(m.N, m.n, m.off, M, out);
+void launch_pack_diag(cudaStream_t s, const MolDev& m, const double* M, double* out, const int* gate) {
+  pack_diag_kernel<<<blocks_for((long long)m.N * 10, 256), 256, 0, s>>>(m.N, m.n, m.off, M, out, gate);
   count_launch();
 }
 
-static void mirror(cudaStream_t s, int n, double* a) {
+static void mirror(cudaStream_t s, int n, double* a, const int* gate) {
   int t = (n + 31) / 32;
-  mirror_upper_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(n, a);
+  mirror_upper_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(n, a, gate);
   count_launch();
 }
 
@@ -291,14 +295,14 @@ void launch_build_h(cudaStream_t s, const MolDev& m, const PairDev& pd, const El
 }
 
 void launch_build_fock(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,
-                       const double* P, const double* Pd, const double* h, double* out) {
-  fock_diag_kernel<<<blocks_for((long long)m.N * 32, 128), 128, 0, s>>>(m, pd, tab, P, Pd, h, out);
+                       const double* P, const double* Pd, const double* h, double* out, const int* gate) {
+  fock_diag_kernel<<<blocks_for((long long)m.N * 32, 128), 128, 0, s>>>(m, pd, tab, P, Pd, h, out, gate);
   count_launch();
   if (m.npair > 0) {
-    fock_offdiag_kernel<<<blocks_for(m.npair, 128), 128, 0, s>>>(m, pd, tab, P, h, out);
+    fock_offdiag_kernel<<<blocks_for(m.npair, 128), 128, 0, s>>>(m, pd, tab, P, h, out, gate);
     count_launch();
   }
-  mirror(s, m.n, out);
+  mirror(s, m.n, out, gate);
 }
 
 void launch_forces(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,

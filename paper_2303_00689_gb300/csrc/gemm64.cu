@@ -15,7 +15,8 @@ constexpr int GBM = 64, GBN = 64, GBK = 16;
 __global__ void __launch_bounds__(256) dgemm_kernel(int ta, int tb, int M, int N, int K, double alpha,
                                                     const double* __restrict__ A, int lda,
                                                     const double* __restrict__ B, int ldb, double beta,
-                                                    double* __restrict__ C, int ldc, int sym) {
+                                                    double* __restrict__ C, int ldc, int sym, const int* gate) {
+  if (gate && *gate == 0) return;
   int bi = blockIdx.y, bj = blockIdx.x;
   if (sym && bi > bj) return;
   __shared__ double As[GBK][GBM + 1];
@@ -77,10 +78,10 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int ta, int tb, int M, int N
 }
 
 void dgemm(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha, const double* A, int lda,
-           const double* B, int ldb, double beta, double* C, int ldc, int sym) {
+           const double* B, int ldb, double beta, double* C, int ldc, int sym, const int* gate) {
   if (M <= 0 || N <= 0) return;
   dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
-  dgemm_kernel<<<grid, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+  dgemm_kernel<<<grid, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym, gate);
   count_launch();
 }
 

@@ -26,13 +26,15 @@ struct PairDev {         // pair blocks (SoA, stride npair)
 };
 
 // out[N][10]: diagonal 4x4 block of M per atom, packed by orbital product
-void launch_pack_diag(cudaStream_t s, const MolDev& m, const double* M, double* out);
+// gate (nullable device int): kernels return at once when *gate == 0 (adaptive Krylov rank)
+void launch_pack_diag(cudaStream_t s, const MolDev& m, const double* M, double* out, const int* gate = nullptr);
 // core Hamiltonian h (dense, symmetric)
 void launch_build_h(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,
                     double* h);
 // out = (h ? h : 0) + G(P) (eq. 3 with NDDO integrals); Pd = packed diagonal blocks of P
 void launch_build_fock(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,
-                       const double* P, const double* Pd, const double* h, double* out);
+                       const double* P, const double* Pd, const double* h, double* out,
+                       const int* gate = nullptr);
 // per-pair gradient contributions g[3][npair] (eq. 37) and per-atom forces
 void launch_forces(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,
                    const double* D, const double* P, const double* Dd, const double* Pd,
@@ -43,7 +45,8 @@ void launch_forces(cudaStream_t s, const MolDev& m, const PairDev& pd, const Ele
 // sym != 0: C is symmetric; only tiles on or above the diagonal are computed
 // and each value is written to (i, j) and (j, i) (bitwise symmetric result).
 void dgemm(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha, const double* A,
-           int lda, const double* B, int ldb, double beta, double* C, int ldc, int sym = 0);
+           int lda, const double* B, int ldb, double beta, double* C, int ldc, int sym = 0,
+           const int* gate = nullptr);
 
 // ---- eig.cu -----------------------------------------------------------------
 struct EigWork {
@@ -103,6 +106,9 @@ void launch_krylov_w(cudaStream_t s, size_t len, int k, const double* D1, const 
                      int m_min);
 void launch_krylov_combine(cudaStream_t s, size_t len, int mmax, double* const* Vs, Scalars* sc,
                            double* K);
+// original XL-BOMD kernel: W0 = D - X, K = -c W0, rank 0 (sc->active = 0)
+void launch_scaled_residual(cudaStream_t s, size_t len, const double* D, const double* X, double c, double* W0,
+                            double* K, Scalars* sc, double* partial);
 void launch_x_update(cudaStream_t s, size_t len, double* const* Xh /*7 ptrs, k = 0..6*/,
                      const double* K, double kappa, double alpha, double* Xnew);
 // nuclei

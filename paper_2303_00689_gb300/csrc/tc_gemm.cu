@@ -168,7 +168,8 @@ __device__ __forceinline__ void twosum_acc(float& hi, float& lo, float b) {
 
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ TcMaps maps, SegTable seg, int M, int N, int K, double alpha,
-                   double* __restrict__ C, int ldc, int sym, int beta, int* err) {
+                   double* __restrict__ C, int ldc, int sym, int beta, int* err, const int* gate) {
+  if (gate && *gate == 0) return;      // whole CTA, before any barrier or TMEM use
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (sym && bi > bj) return;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -328,7 +329,9 @@ __device__ __forceinline__ int exponent_of_max(unsigned long long bits) {
   return be - 1022;
 }
 
-__global__ void row_exponent_kernel(int n, const double* __restrict__ X, int transpose, int* __restrict__ ex) {
+__global__ void row_exponent_kernel(int n, const double* __restrict__ X, int transpose, int* __restrict__ ex,
+                                    const int* gate) {
+  if (gate && *gate == 0) return;
   int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (r >= n) return;
@@ -369,7 +372,9 @@ __device__ __forceinline__ void slice_value(double x, int e, int slices, __nv_bf
 
 // FP64 -> fixed-point BF16 slices relative to the row exponent; ld-padded rows
 __global__ void split_bf16_kernel(int n, const double* __restrict__ X, int ld, int slices, int transpose,
-                                  const int* __restrict__ ex, __nv_bfloat16* const* __restrict__ P) {
+                                  const int* __restrict__ ex, __nv_bfloat16* const* __restrict__ P,
+                                  const int* gate) {
+  if (gate && *gate == 0) return;
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t tot = (size_t)n * ld;
   if (t >= tot) return;
@@ -535,19 +540,21 @@ bool tc_ready(const TcWork& w) { return w.base && ((TcBuffers*)w.base)->maps_ok;
 
 int* tc_error_flag(const TcWork& w) { return w.base ? ((TcBuffers*)w.base)->err : nullptr; }
 
-void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int slices, int transpose) {
+void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int slices, int transpose,
+              const int* gate) {
   TcBuffers* tb = (TcBuffers*)w.base;
   int n = tb->n;
   int* ex = tb->ex + (size_t)slot * n;
-  row_exponent_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, X, transpose, ex);
+  row_exponent_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, X, transpose, ex, gate);
   count_launch();
   size_t tot = (size_t)n * tb->ld;
   split_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, X, tb->ld, slices, transpose, ex,
-                                                                   tb->dpieces + (size_t)slot * kTcMaxSlices);
+                                                                   tb->dpieces + (size_t)slot * kTcMaxSlices, gate);
   count_launch();
 }
 
-void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, double alpha, double* C, int sym) {
+void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, double alpha, double* C, int sym,
+             const int* gate) {
   TcBuffers* tb = (TcBuffers*)w.base;
   static bool attr = false;
   if (!attr) {
@@ -571,7 +578,7 @@ void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, d
     }
   int n = tb->n;
   dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
-  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, 0, tb->err);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, 0, tb->err, gate);
   count_launch();
 }
 
@@ -624,7 +631,7 @@ int tc_gemm_rc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, 
       ++seg.nseg;
     }
   dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
-  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, M, N, K, alpha, C, ldc, 0, beta, err);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, M, N, K, alpha, C, ldc, 0, beta, err, nullptr);
   count_launch();
   return 0;
 }
@@ -633,7 +640,7 @@ bool tc_encode_map(CUtensorMap* m, void* ptr, int n, int ld) { return make_map(m
 
 void tc_split_strided(cudaStream_t s, int n, int ld, const double* X, int slices, int transpose, int* ex,
                       __nv_bfloat16* base, size_t stride) {
-  row_exponent_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, X, transpose, ex);
+  row_exponent_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, X, transpose, ex, nullptr);
   count_launch();
   size_t tot = (size_t)n * ld;
   split_bf16_strided_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, X, ld, slices, transpose, ex, base,
@@ -663,7 +670,7 @@ void tc_gemm_on_maps(cudaStream_t s, int n, const CUtensorMap* mapsA, const CUte
       ++seg.nseg;
     }
   dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
-  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, 0, err);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, 0, err, nullptr);
   count_launch();
 }
 

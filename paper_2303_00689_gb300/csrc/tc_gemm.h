@@ -22,10 +22,12 @@ bool tc_available();                  // driver entry point for tensor maps pres
 bool tc_ready(const TcWork& w);       // tensor maps encoded for this handle
 int* tc_error_flag(const TcWork& w);  // device word set when a bounded wait expired
 // X (n x n FP64) -> `slices` fixed-point BF16 slices in slot (transpose != 0 slices X^T)
-void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int slices, int transpose);
+// gate (nullable device int): the kernels return at once when *gate == 0
+void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int slices, int transpose,
+              const int* gate = nullptr);
 // C = alpha * sum over `terms` (1, 3, 6 or 10 for 1-4 slices) slice products A_a B_b^T
 void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, double alpha, double* C,
-             int sym);
+             int sym, const int* gate = nullptr);
 
 // Building blocks on caller-provided buffers (used by the allocation-free entry point)
 int tc_ld(int n);                                                   // padded slice row length

@@ -34,6 +34,30 @@ def test_damped_recursion_is_stable_for_minus_identity_kernel():
     assert np.abs(np.roots([1.0, -(2.0 - dyn.KAPPA), 1.0])).max() == pytest.approx(1.0, abs=1e-12)
 
 
+def test_xl_kernel_equals_krylov_kernel_without_two_electron_terms():
+    """G = 0 makes the residual Jacobian -I (eq. 31), so K = -I exactly: the
+    Krylov kernel at rank 1 and 3 and the XL-BOMD kernel -c I with c = 1 agree,
+    and c scales the XL kernel linearly."""
+    mol = synth.c4h6(1)
+    tab0 = synth.synthetic_table(1, two_electron=False)
+    sysm = ham.System(mol.Z, tab0)
+    rng = np.random.default_rng(3)
+    X = dyn.initial_guess(sysm)
+    A = rng.standard_normal(X.shape) * 1e-2
+    X = X + 0.5 * (A + A.T)
+    kx = dyn.evaluate(sysm, mol.R, X, dyn.Config(Te=1000.0, xl_c=1.0))["K"]
+    for m in (1, 3):
+        kk = dyn.evaluate(sysm, mol.R, X, dyn.Config(Te=1000.0, m=m))["K"]
+        assert np.abs(kk - kx).max() < 1e-10 * np.abs(kx).max()
+    k9 = dyn.evaluate(sysm, mol.R, X, dyn.Config(Te=1000.0, xl_c=0.9))["K"]
+    assert np.abs(k9 - 0.9 * kx).max() < 1e-15 * np.abs(kx).max() + 1e-300
+    # with the two-electron terms on, the exact kernel is no longer -I
+    sysm1 = ham.System(mol.Z, TAB)
+    kk = dyn.evaluate(sysm1, mol.R, X, dyn.Config(Te=1000.0, m=4))["K"]
+    kx1 = dyn.evaluate(sysm1, mol.R, X, dyn.Config(Te=1000.0, xl_c=1.0))["K"]
+    assert np.abs(kk - kx1).max() > 1e-3 * np.abs(kx1).max()
+
+
 @pytest.mark.slow
 def test_energy_conservation_and_dt_squared_scaling():
     """E_tot (eq. 26) fluctuates ~dt^2 and does not drift (Results, Gramicidin S NVE)."""
