@@ -79,6 +79,40 @@ def scf(sysm, R, cfg, P0=None):
     raise RuntimeError(f"SCF did not converge (max|D-P| = {err:.3e})")
 
 
+def scf_krylov(sysm, R, cfg, m, P0=None, tol=None, max_iter=None):
+    """Low-rank Krylov SCF (Results, "SCF Optimization": fixed rank, no
+    preconditioner).  The SCF residual D[P] - P has the same Jacobian as the
+    XL-BOMD residual (eq. 31), so the rank-m kernel of eqs. 31-34 gives the
+    Newton-like update P <- P - K (D[P] - P).  Reading: whenever the residual
+    has grown tenfold over the best one seen, a linear-mixing step is taken
+    instead.  Returns (P, iterations, residual history)."""
+    tol = cfg.scf_tol if tol is None else tol
+    max_iter = cfg.scf_max if max_iter is None else max_iter
+    P = initial_guess(sysm) if P0 is None else P0.copy()
+    pairs = ham.PairCache(sysm, R)
+    h, _ = ham.core_hamiltonian(sysm, R, pairs)
+    best, hist = np.inf, []
+    for it in range(max_iter):
+        F = h + ham.two_electron(sysm, R, P, pairs)
+        D, eps, Q, f, mu = el.density(F, sysm.nocc, cfg.Te)
+        err = np.abs(D - P).max()
+        hist.append(err)
+        if err < tol:
+            return D, it, hist
+        best = min(best, err)
+        if err < 10.0 * best:
+            Lam = el.divided_differences(eps, f, mu, cfg.beta)
+
+            def response(V):
+                return el.dmpt(ham.two_electron(sysm, R, V, pairs), Q, Lam)[0]
+
+            K, _ = el.krylov_kernel(D - P, response, m, m, 0.0)
+            P = P - K
+        else:
+            P = cfg.mix * P + (1.0 - cfg.mix) * D
+    raise RuntimeError(f"Krylov SCF did not converge (max|D-P| = {err:.3e})")
+
+
 def evaluate(sysm, R, X, cfg, krylov=True):
     """Shadow energy, forces, D0 and Krylov kernel at (R, X)."""
     pairs = ham.PairCache(sysm, R)

@@ -75,7 +75,9 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
   __shared__ double s_par[4];  // beta, tau, scale, d_k
   const int tid = threadIdx.x, lane = tid & 31;
   const int wpb = blockDim.x >> 5;
-  const int gw = blockIdx.x * wpb + (tid >> 5);
+  // row r of the trailing matrix goes to block r % G, warp (r / G) % wpb: every
+  // block keeps an equal share of rows as the trailing matrix shrinks
+  const int gw = blockIdx.x + gridDim.x * (tid >> 5);
   const int totw = gridDim.x * wpb;
   bool prev = false;
 

@@ -14,6 +14,6 @@ produces as plain inputs:
 from .params import synthetic_table, FIELDS, ELEMENTS, table_to_array  # noqa: F401
 from .geometry import (  # noqa: F401
     c4h6, carbon_packing, carbon_fragments, organic_molecule, molecule_batch,
-    serving_requests, Molecule,
+    serving_requests, fullerene_c60, Molecule,
 )
 from .velocities import maxwell_boltzmann, MASS  # noqa: F401

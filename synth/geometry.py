@@ -8,6 +8,7 @@ sampling with distance constraints only.
 * ``organic_molecule``      -- C/N/O heavy-atom tree filled with H (batch workload)
 * ``molecule_batch(seed)``  -- 128 molecules with 12..200 atoms
 * ``carbon_fragments(seed)``-- 400 C as chains plus graphene-like sheet fragments
+* ``fullerene_c60(...)``    -- truncated-icosahedron C60 cages (closed, no dangling bonds)
 * ``serving_requests``      -- Poisson arrival times, sizes and step counts
 """
 from dataclasses import dataclass
@@ -180,6 +181,45 @@ def carbon_fragments(seed=5, natoms=400, spacing=6.0):
     R = np.vstack(allpos)[:natoms]
     Z = np.full(len(R), 6, dtype=np.int32)
     return Molecule(Z, R - R.mean(axis=0))
+
+
+def _c60_unit():
+    """Vertices of the truncated icosahedron with edge length 1, centred at 0.
+
+    With edge length 2 the vertices are the even (cyclic) permutations of
+    (0, +-1, +-3p), (+-1, +-(2 + p), +-2p) and (+-p, +-2, +-(2p + 1)), p the
+    golden ratio."""
+    p = (1.0 + 5.0 ** 0.5) / 2.0
+    base = [(0.0, 1.0, 3 * p), (1.0, 2.0 + p, 2 * p), (p, 2.0, 2 * p + 1.0)]
+    pts = set()
+    for a, b, c in base:
+        for sa in (-1, 1):
+            for sb in (-1, 1):
+                for sc in (-1, 1):
+                    v = (sa * a, sb * b, sc * c)
+                    for k in range(3):                       # cyclic permutations
+                        pts.add(tuple(round(x, 12) + 0.0 for x in (v[k], v[(k + 1) % 3], v[(k + 2) % 3])))
+    P = np.array(sorted(pts)) / 2.0
+    assert P.shape == (60, 3)
+    return P
+
+
+def fullerene_c60(seed=5, copies=1, bond=1.42, spacing=12.0, charge=0):
+    """``copies`` C60 cages (C-C ``bond`` Angstrom), each randomly rotated and
+    jittered by 0.02 A, on a line ``spacing`` Angstrom apart."""
+    rng = _rng(606, seed)
+    unit = _c60_unit() * bond
+    out = []
+    for c in range(copies):
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        w, x, y, z = q
+        Rm = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                       [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                       [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+        out.append(unit @ Rm.T + rng.normal(size=unit.shape) * 0.02 + np.array([c * spacing, 0.0, 0.0]))
+    R = np.concatenate(out)
+    return Molecule(np.full(len(R), 6, dtype=np.int32), R, charge=charge)
 
 
 def serving_requests(seed=4, count=64, rate_per_s=1.0, nmin=20, nmax=600, smin=10, smax=100):
