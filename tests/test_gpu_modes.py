@@ -110,3 +110,21 @@ def test_adaptive_rank_equals_fixed_rank_bitwise(fragments, precision):
             kx.sim_destroy(hf)
     finally:
         kx.sim_destroy(ha)
+
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_krylov_scf_matches_oracle(m):
+    """sim_create with scf_krylov: the low-rank Krylov SCF reaches the oracle's
+    ground state (same fixed point; the iteration counts agree within one)."""
+    mol = synth.c4h6(1)
+    sysm = oracle_system(mol)
+    cfg = dyn.Config(Te=1000.0, scf_tol=1e-10)
+    D_ref, it_ref, _ = dyn.scf_krylov(sysm, mol.R, cfg, m=m)
+    h = create(mol, dict(Te=1000.0, m_max=m, m_min=m, scf_tol=1e-10, scf_krylov=1))
+    try:
+        it, res = kx.sim_scf_info(h)
+        assert res < 1e-10
+        assert abs(it - it_ref) <= 1
+        assert max_abs(kx.sim_get_matrix(h, kx.SIM_MAT_X), D_ref) < 1e-9
+    finally:
+        kx.sim_destroy(h)

@@ -83,3 +83,17 @@ def test_energy_conservation_and_dt_squared_scaling():
     for s, d in zip(stds, drifts):
         assert abs(d) * sysm.N * 0.060 < s
     assert stds[0] < 2e-3
+
+
+def test_krylov_scf_reaches_the_linear_mixing_fixed_point():
+    """The low-rank Krylov SCF (Results, "SCF Optimization") and linear mixing
+    are different iterations with the same fixed point D[P] = P; the Krylov
+    one needs far fewer iterations on a gapped molecule."""
+    mol = synth.c4h6(1)
+    sysm = ham.System(mol.Z, TAB)
+    cfg = dyn.Config(Te=1000.0, scf_tol=1e-10)
+    D_lin, it_lin = dyn.scf(sysm, mol.R, cfg)
+    D_kry, it_kry, hist = dyn.scf_krylov(sysm, mol.R, cfg, m=3)
+    assert np.abs(D_kry - D_lin).max() < 1e-9
+    assert it_kry < it_lin / 2
+    assert hist[-1] < 1e-10
