@@ -187,6 +187,102 @@ int sim_step_host(sim_handle* h, const double* R_in, const double* V_in, double*
 int sim_step_async(sim_handle* h, int nsteps);
 int sim_last_result(sim_handle* h, sim_step_result* out);
 
+/* sim_records -- copy the records of the last `count` steps (oldest first)
+ * into `out`; count <= 4096 and <= the steps run since the last sim_step,
+ * sim_batch_step, sim_set_state or sim_create (whose initial evaluation is
+ * record 0).  Synchronises the handle's stream. */
+int sim_records(sim_handle* h, sim_step_result* out, int count);
+
+/* sim_wait -- synchronise the handle's stream and return the first error a
+ * kernel reported since the last check (SIM_ETIMEOUT for an expired bounded
+ * wait, SIM_ENUMERIC for NaN/Inf), else SIM_OK. */
+int sim_wait(sim_handle* h);
+
+/* sim_enable_graphs -- enable != 0 captures one MD step into CUDA graphs
+ * (one per phase of the 8-slot X(t - k dt) ring, eq. 29) and from then on
+ * replays them in every step call; 0 releases them.  A replayed step is the
+ * same kernel sequence on the same buffers, so results are bitwise those of
+ * direct launches.  Steps taken while phase profiling is on launch directly.
+ * The configuration and the molecule are fixed by the capture. */
+int sim_enable_graphs(sim_handle* h, int enable);
+
+/* sim_batch_step -- advance `count` independent handles by nsteps steps
+ * each (molecule batches: one trajectory per molecule).  The steps are
+ * issued round-robin, each handle on its own stream, so the device runs the
+ * small, latency-bound steps of different molecules concurrently (with
+ * graphs enabled each step is one graph launch).  Synchronous; returns the
+ * first error.  Records of the steps are read with sim_records. */
+int sim_batch_step(sim_handle* const* handles, int count, int nsteps);
+
+/* Bytes of device memory sim_create allocates for this molecule/config. */
+size_t sim_estimate_bytes(const sim_config* cfg, int natoms, const int* Z);
+
+/* ---- serving: continuous batching of many trajectories ------------------
+ * A server owns a device, a memory budget and two host threads: an admission
+ * thread that creates trajectories (SCF included) in submission order while
+ * their estimated memory fits the budget and fewer than max_active are live,
+ * and a stepping thread that keeps one step in flight per live trajectory
+ * (each on its own stream, through CUDA graphs when use_graphs != 0) and
+ * retires a trajectory when its steps are done.  Every trajectory computes
+ * exactly what sim_create + sim_step compute for it alone: no data is shared
+ * between trajectories, so results do not depend on the rest of the mix. */
+typedef struct sim_server sim_server;
+
+typedef struct sim_server_config {
+  int device;               /* CUDA device ordinal                                 */
+  int max_active;           /* live trajectories at most (<= 0: 64)                */
+  size_t hbm_budget_bytes;  /* device bytes for trajectories (0: 90% of free)      */
+  int use_graphs;           /* step through CUDA graphs                            */
+} sim_server_config;
+
+typedef struct sim_request {
+  sim_config cfg;           /* copied; cfg.device/stream are set by the server     */
+  sim_param_table table;    /* copied                                              */
+  int natoms;
+  const int* Z;             /* natoms; copied at submission                        */
+  const double* R;          /* natoms x 3, Angstrom; copied                        */
+  const double* V;          /* natoms x 3 or NULL; copied                          */
+  int charge;
+  int nsteps;               /* MD steps to run (>= 0, <= 4096)                     */
+  double* R_out;            /* caller buffers written at completion (or NULL):     */
+  double* V_out;            /*   natoms x 3 final positions, velocities, forces;   */
+  double* F_out;            /*   they must stay valid until sim_poll reports done  */
+  sim_step_result* records; /* nsteps records or NULL                              */
+} sim_request;
+
+typedef struct sim_traj_result {
+  int status;               /* SIM_OK or the error of sim_create / a step          */
+  int steps_done;
+  double queue_ms;          /* submission -> admitted (creation started)           */
+  double create_ms;         /* sim_create incl. SCF                                */
+  double run_ms;            /* first step launched -> last step finished           */
+  char error[160];          /* message when status != SIM_OK                       */
+} sim_traj_result;
+
+typedef struct sim_server_stats {
+  long long submitted, completed, failed, queued, active, max_active_seen;
+  long long atom_steps;     /* sum over finished steps of the molecule's atoms     */
+  double step_p50_ms;       /* per-trajectory step latency: time between the       */
+  double step_p99_ms;       /*   completions of consecutive steps of one trajectory*/
+  double elapsed_s;         /* since sim_server_create                             */
+  size_t hbm_in_use, hbm_budget;
+} sim_server_stats;
+
+int sim_server_create(const sim_server_config* cfg, sim_server** out);
+/* Copies the request; *ticket identifies it.  Thread-safe.  SIM_EINVAL for a
+ * request that can never be admitted (bad sizes, larger than the budget). */
+int sim_submit(sim_server* s, const sim_request* req, unsigned long long* ticket);
+/* SIM_PENDING while the trajectory is queued or running; otherwise fills
+ * *out, forgets the ticket and returns SIM_OK (out->status holds the
+ * trajectory's own result).  SIM_EINVAL for an unknown ticket.  Thread-safe. */
+int sim_poll(sim_server* s, unsigned long long ticket, sim_traj_result* out);
+int sim_server_stats_get(sim_server* s, sim_server_stats* out);
+/* Wait until no trajectory is queued or live (SIM_ETIMEOUT after timeout_s). */
+int sim_server_drain(sim_server* s, double timeout_s);
+/* Stops both threads after the live trajectories finish their current step;
+ * unfinished ones are dropped. */
+void sim_server_destroy(sim_server* s);
+
 /* sim_get_state -- copy the current state out (any pointer may be NULL).
  *   R, V, F: natoms x 3 (F = forces, eV/Angstrom, eq. 37 with the eq. 9 sign)
  *   D0:      n x n per-spin D0[X(t)] of the last evaluation (eq. 19) */

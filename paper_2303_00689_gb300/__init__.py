@@ -27,7 +27,9 @@ EXPORTED = (
     "sim_last_result", "sim_get_state", "sim_set_state", "sim_get_matrix", "sim_get_vector",
     "sim_profile_enable", "sim_phase_count", "sim_phase_name", "sim_phase_times",
     "sim_launch_count", "sim_stream", "sim_destroy", "sim_last_error", "sim_debug_tc_gemm",
-    "sim_tc_gemm_noalloc",
+    "sim_tc_gemm_noalloc", "sim_records", "sim_wait", "sim_enable_graphs", "sim_batch_step",
+    "sim_estimate_bytes", "sim_server_create", "sim_submit", "sim_poll", "sim_server_stats_get",
+    "sim_server_drain", "sim_server_destroy",
 )
 
 
@@ -53,6 +55,31 @@ class sim_step_result(C.Structure):
     _fields_ = [("E_kin", C.c_double), ("U", C.c_double), ("E_tot", C.c_double), ("mu", C.c_double),
                 ("gap", C.c_double), ("res_norm", C.c_double), ("fit_err", C.c_double),
                 ("rank", C.c_int), ("pad", C.c_int)]
+
+
+class sim_server_config(C.Structure):
+    _fields_ = [("device", C.c_int), ("max_active", C.c_int), ("hbm_budget_bytes", C.c_size_t),
+                ("use_graphs", C.c_int)]
+
+
+class sim_request(C.Structure):
+    _fields_ = [("cfg", sim_config), ("table", sim_param_table), ("natoms", C.c_int),
+                ("Z", C.POINTER(C.c_int)), ("R", C.POINTER(C.c_double)), ("V", C.POINTER(C.c_double)),
+                ("charge", C.c_int), ("nsteps", C.c_int), ("R_out", C.POINTER(C.c_double)),
+                ("V_out", C.POINTER(C.c_double)), ("F_out", C.POINTER(C.c_double)),
+                ("records", C.POINTER(sim_step_result))]
+
+
+class sim_traj_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("steps_done", C.c_int), ("queue_ms", C.c_double),
+                ("create_ms", C.c_double), ("run_ms", C.c_double), ("error", C.c_char * 160)]
+
+
+class sim_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
+                ("queued", C.c_longlong), ("active", C.c_longlong), ("max_active_seen", C.c_longlong),
+                ("atom_steps", C.c_longlong), ("step_p50_ms", C.c_double), ("step_p99_ms", C.c_double),
+                ("elapsed_s", C.c_double), ("hbm_in_use", C.c_size_t), ("hbm_budget", C.c_size_t)]
 
 
 _lib_handle = None
@@ -97,6 +124,19 @@ def lib():
         L.sim_debug_tc_gemm.argtypes = [C.c_int, dp, dp, C.c_int, C.c_int, dp]
         L.sim_tc_gemm_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                           C.c_void_p]
+        L.sim_records.argtypes = [C.c_void_p, P(sim_step_result), C.c_int]
+        L.sim_wait.argtypes = [C.c_void_p]
+        L.sim_enable_graphs.argtypes = [C.c_void_p, C.c_int]
+        L.sim_batch_step.argtypes = [P(C.c_void_p), C.c_int, C.c_int]
+        L.sim_estimate_bytes.argtypes = [P(sim_config), C.c_int, P(C.c_int)]
+        L.sim_estimate_bytes.restype = C.c_size_t
+        L.sim_server_create.argtypes = [P(sim_server_config), P(C.c_void_p)]
+        L.sim_submit.argtypes = [C.c_void_p, P(sim_request), P(C.c_ulonglong)]
+        L.sim_poll.argtypes = [C.c_void_p, C.c_ulonglong, P(sim_traj_result)]
+        L.sim_server_stats_get.argtypes = [C.c_void_p, P(sim_server_stats)]
+        L.sim_server_drain.argtypes = [C.c_void_p, C.c_double]
+        L.sim_server_destroy.argtypes = [C.c_void_p]
+        L.sim_server_destroy.restype = None
         L.sim_last_error.argtypes = []
         L.sim_last_error.restype = C.c_char_p
         _lib_handle = L
@@ -269,6 +309,90 @@ def sim_tc_gemm_noalloc(n, A_dev, B_dev, terms, sym, C_dev, stream=None):
     """Device pointers (ints) in and out; returns the raw status code."""
     return lib().sim_tc_gemm_noalloc(int(n), C.c_void_p(A_dev), C.c_void_p(B_dev), int(terms),
                                      1 if sym else 0, C.c_void_p(C_dev), C.c_void_p(stream or 0))
+
+
+def sim_records(h, count):
+    out = (sim_step_result * max(1, count))()
+    _check(lib().sim_records(h, out, int(count)))
+    return [{f: getattr(r, f) for f, _ in sim_step_result._fields_} for r in out[:count]]
+
+
+def sim_wait(h):
+    _check(lib().sim_wait(h))
+
+
+def sim_enable_graphs(h, enable=True):
+    _check(lib().sim_enable_graphs(h, 1 if enable else 0))
+
+
+def sim_batch_step(handles, nsteps):
+    arr = (C.c_void_p * max(1, len(handles)))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    _check(lib().sim_batch_step(arr, len(handles), int(nsteps)))
+
+
+def sim_estimate_bytes(cfg, Z):
+    Z = np.ascontiguousarray(Z, dtype=np.int32)
+    return lib().sim_estimate_bytes(C.byref(cfg), len(Z), Z.ctypes.data_as(C.POINTER(C.c_int)))
+
+
+class Server:
+    """sim_server_* wrapper: submit(...) -> ticket, poll(ticket) -> dict or None."""
+
+    def __init__(self, device=0, max_active=64, hbm_budget_bytes=0, use_graphs=True):
+        self._h = C.c_void_p()
+        cfg = sim_server_config(device, max_active, hbm_budget_bytes, 1 if use_graphs else 0)
+        _check(lib().sim_server_create(C.byref(cfg), C.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, cfg, table, Z, R, V=None, charge=0, nsteps=0, records=True):
+        Z = np.ascontiguousarray(Z, dtype=np.int32)
+        N = len(Z)
+        R = _f64(R, (N, 3))
+        V = _f64(V, (N, 3))
+        outs = dict(R=np.empty((N, 3)), V=np.empty((N, 3)), F=np.empty((N, 3)),
+                    rec=(sim_step_result * max(1, nsteps))() if records else None)
+        req = sim_request(cfg=cfg, table=table, natoms=N, Z=Z.ctypes.data_as(C.POINTER(C.c_int)),
+                          R=_dptr(R), V=_dptr(V), charge=int(charge), nsteps=int(nsteps),
+                          R_out=_dptr(outs["R"]), V_out=_dptr(outs["V"]), F_out=_dptr(outs["F"]),
+                          records=outs["rec"])
+        t = C.c_ulonglong()
+        _check(lib().sim_submit(self._h, C.byref(req), C.byref(t)))
+        outs["nsteps"] = nsteps
+        self._keep[t.value] = outs
+        return t.value
+
+    def poll(self, ticket):
+        res = sim_traj_result()
+        rc = lib().sim_poll(self._h, C.c_ulonglong(ticket), C.byref(res))
+        if rc == SIM_PENDING:
+            return None
+        _check(rc)
+        outs = self._keep.pop(ticket)
+        recs = None
+        if outs["rec"] is not None:
+            recs = [{f: getattr(r, f) for f, _ in sim_step_result._fields_} for r in outs["rec"][:res.steps_done]]
+        return dict(status=res.status, steps_done=res.steps_done, queue_ms=res.queue_ms,
+                    create_ms=res.create_ms, run_ms=res.run_ms, error=res.error.decode(),
+                    R=outs["R"], V=outs["V"], F=outs["F"], records=recs)
+
+    def stats(self):
+        st = sim_server_stats()
+        _check(lib().sim_server_stats_get(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in sim_server_stats._fields_}
+
+    def drain(self, timeout_s=600.0):
+        _check(lib().sim_server_drain(self._h, float(timeout_s)))
+
+    def close(self):
+        if self._h:
+            lib().sim_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def sim_last_error():

@@ -73,10 +73,11 @@ struct sim_handle {
   double *red = nullptr, *coef = nullptr;
   Scalars* sc = nullptr;
   sim_step_result* rec = nullptr;   // device per-step records (ring of kRecCap)
+  int* rec_idx = nullptr;           // device: index of the next record in rec[]
+  long long rec_count = 0;          // host: records written since the last reset
   EigWork ew;
   TcWork tw;
   int xhead = 0;
-  int last_rec = 0;   // index in rec[] of the most recent record
   int scf_iters = 0;   // SCF iterations used by sim_create (0 when P0 was given)
   double scf_residual = 0.0;
   // host mirror of the last results
@@ -89,6 +90,10 @@ struct sim_handle {
   long long ph_n[PH_COUNT] = {};
   int cur_phase = -1;
   cudaEvent_t cur_start = nullptr;
+  // CUDA graphs of one step, one per phase of the 8-slot X ring
+  bool graphs = false;
+  cudaGraphExec_t gexec[8] = {};
+  long long gnodes[8] = {};
 };
 static const int kRecCap = 4096;
 
@@ -340,7 +345,10 @@ static int evaluate(sim_handle* h, bool krylov = true) {
   return SIM_OK;
 }
 
-__global__ void record_kernel(const Scalars* sc, double Te, sim_step_result* out) {
+__global__ void record_kernel(const Scalars* sc, double Te, sim_step_result* base, int* idx, int cap) {
+  const int i = *idx;
+  *idx = i + 1;
+  sim_step_result* out = base + (i % cap);
   sim_step_result r;
   r.E_kin = sc->e_kin;
   r.U = sc->e_elec - 2.0 * Te * sc->entropy + sc->vnn;
@@ -354,7 +362,18 @@ __global__ void record_kernel(const Scalars* sc, double Te, sim_step_result* out
   *out = r;
 }
 
-static int one_step(sim_handle* h, sim_step_result* rec_dev) {
+static void record(sim_handle* h) {
+  record_kernel<<<1, 1, 0, h->stream>>>(h->sc, h->cfg.Te, h->rec, h->rec_idx, kRecCap);
+  count_launch();
+  h->rec_count += 1;
+}
+
+static void reset_records(sim_handle* h) {
+  cudaMemsetAsync(h->rec_idx, 0, sizeof(int), h->stream);
+  h->rec_count = 0;
+}
+
+static int one_step(sim_handle* h) {
   cudaStream_t s = h->stream;
   size_t nn = (size_t)h->n * h->n;
   double dt = h->cfg.dt;
@@ -372,12 +391,67 @@ static int one_step(sim_handle* h, sim_step_result* rec_dev) {
   phase_begin(h, PH_UPDATE);
   launch_half_kick(s, h->N, h->V, h->F, h->mass, dt);     // eq. 30
   launch_kinetic(s, h->N, h->V, h->mass, h->sc);
-  if (rec_dev) {
-    record_kernel<<<1, 1, 0, s>>>(h->sc, h->cfg.Te, rec_dev);
-    count_launch();
-  }
+  record(h);
   phase_end(h);
   return SIM_OK;
+}
+
+// Capture one step per ring phase into CUDA graphs (kernels and copies only:
+// the step has no host synchronisation and no allocation).
+static int capture_graphs(sim_handle* h) {
+  const bool prof = h->prof;
+  h->prof = false;
+  const int head = h->xhead;
+  const long long rc0 = h->rec_count;
+  int rc = SIM_OK;
+  for (int p = 0; p < 8 && rc == SIM_OK; ++p) {
+    h->xhead = p;
+    long long c0 = g_launches.load();
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = fail(SIM_EINTERNAL, "cudaStreamBeginCapture failed");
+      break;
+    }
+    int st = one_step(h);
+    cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
+    if (st != SIM_OK || ee != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      rc = fail(SIM_EINTERNAL, std::string("graph capture of a step failed: ") + cudaGetErrorString(ee));
+      break;
+    }
+    cudaError_t ie = cudaGraphInstantiate(&h->gexec[p], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      h->gexec[p] = nullptr;
+      rc = fail(SIM_EINTERNAL, std::string("graph instantiation failed: ") + cudaGetErrorString(ie));
+      break;
+    }
+    long long nodes = g_launches.load() - c0;
+    g_launches.fetch_sub(nodes);   // captured, not launched
+    h->gnodes[p] = nodes;
+  }
+  h->xhead = head;
+  h->rec_count = rc0;
+  h->prof = prof;
+  if (rc != SIM_OK)
+    for (int p = 0; p < 8; ++p)
+      if (h->gexec[p]) { cudaGraphExecDestroy(h->gexec[p]); h->gexec[p] = nullptr; }
+  return rc;
+}
+
+// one step: graph replay when enabled, else direct launches
+static int launch_step(sim_handle* h) {
+  if (h->graphs && !h->prof) {
+    const int p = h->xhead;
+    CUDA_TRY(cudaGraphLaunch(h->gexec[p], h->stream));
+    g_launches.fetch_add(h->gnodes[p]);
+    h->xhead = (p + 7) % 8;
+    h->rec_count += 1;
+    return SIM_OK;
+  }
+  return one_step(h);
 }
 
 static int check_status(sim_handle* h) {
@@ -451,6 +525,7 @@ static void layout(sim_handle* h, Arena& a) {
   h->coef = a.take<double>(64);
   h->sc = a.take<Scalars>(1);
   h->rec = a.take<sim_step_result>(kRecCap);
+  h->rec_idx = a.take<int>(4);
   void* ewb = a.take<char>(eig_work_bytes(h->n));
   if (a.base) eig_work_bind(h->ew, ewb, h->n);
   if (h->cfg.precision == SIM_PREC_MIXED) {
@@ -683,8 +758,8 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
     rc = evaluate(h);
     if (rc) break;
     launch_kinetic(s, h->N, h->V, h->mass, h->sc);
-    record_kernel<<<1, 1, 0, s>>>(h->sc, h->cfg.Te, h->rec);
-    count_launch();
+    reset_records(h);
+    record(h);
     rc = check_status(h);
   } while (0);
   if (rc != SIM_OK) {
@@ -700,10 +775,9 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
 int sim_step_async(sim_handle* h, int nsteps) {
   if (!h || nsteps < 0) return fail(SIM_EINVAL, "bad handle or nsteps");
   for (int i = 0; i < nsteps; ++i) {
-    int rc = one_step(h, h->rec);
+    int rc = launch_step(h);
     if (rc) return rc;
   }
-  h->last_rec = 0;
   return SIM_OK;
 }
 
@@ -713,11 +787,11 @@ int sim_step(sim_handle* h, int nsteps, sim_step_result* out) {
   while (done < nsteps) {
     int chunk = nsteps - done;
     if (chunk > kRecCap) chunk = kRecCap;
+    reset_records(h);
     for (int i = 0; i < chunk; ++i) {
-      int rc = one_step(h, h->rec + i);
+      int rc = launch_step(h);
       if (rc) return rc;
     }
-    h->last_rec = chunk - 1;
     if (out) {
       CUDA_TRY(cudaMemcpyAsync(out + done, h->rec, chunk * sizeof(sim_step_result), cudaMemcpyDeviceToHost,
                                h->stream));
@@ -737,9 +811,9 @@ int sim_step_host(sim_handle* h, const double* R_in, const double* V_in, double*
   size_t b3 = 3 * (size_t)h->N * sizeof(double);
   if (R_in) CUDA_TRY(cudaMemcpyAsync(h->R, R_in, b3, cudaMemcpyHostToDevice, s));
   if (V_in) CUDA_TRY(cudaMemcpyAsync(h->V, V_in, b3, cudaMemcpyHostToDevice, s));
-  int rc = one_step(h, h->rec);
+  reset_records(h);
+  int rc = launch_step(h);
   if (rc) return rc;
-  h->last_rec = 0;
   if (R_out) CUDA_TRY(cudaMemcpyAsync(R_out, h->R, b3, cudaMemcpyDeviceToHost, s));
   if (V_out) CUDA_TRY(cudaMemcpyAsync(V_out, h->V, b3, cudaMemcpyDeviceToHost, s));
   if (F_out) CUDA_TRY(cudaMemcpyAsync(F_out, h->F, b3, cudaMemcpyDeviceToHost, s));
@@ -750,9 +824,77 @@ int sim_step_host(sim_handle* h, const double* R_in, const double* V_in, double*
 
 int sim_last_result(sim_handle* h, sim_step_result* out) {
   if (!h || !out) return fail(SIM_EINVAL, "null argument");
+  long long i = h->rec_count > 0 ? (h->rec_count - 1) % kRecCap : 0;
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  CUDA_TRY(cudaMemcpy(out, h->rec + h->last_rec, sizeof(sim_step_result), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(out, h->rec + i, sizeof(sim_step_result), cudaMemcpyDeviceToHost));
   return SIM_OK;
+}
+
+int sim_records(sim_handle* h, sim_step_result* out, int count) {
+  if (!h || !out || count < 0) return fail(SIM_EINVAL, "bad arguments");
+  if (count > kRecCap || count > h->rec_count) return fail(SIM_EINVAL, "fewer records available than requested");
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < count; ++i) {
+    long long idx = (h->rec_count - count + i) % kRecCap;
+    CUDA_TRY(cudaMemcpy(out + i, h->rec + idx, sizeof(sim_step_result), cudaMemcpyDeviceToHost));
+  }
+  return SIM_OK;
+}
+
+int sim_wait(sim_handle* h) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  return check_status(h);
+}
+
+size_t sim_estimate_bytes(const sim_config* cfg, int natoms, const int* Z) {
+  if (!cfg || !Z || natoms < 1 || cfg->m_max < 1 || cfg->m_max > 16) return 0;
+  sim_handle tmp;
+  tmp.cfg = *cfg;
+  tmp.N = natoms;
+  int n = 0;
+  for (int A = 0; A < natoms; ++A) n += (Z[A] == 1) ? 1 : 4;
+  tmp.n = n;
+  tmp.npair = natoms * (natoms - 1) / 2;
+  tmp.mmax = cfg->m_max;
+  Arena sizing{nullptr, 0, 0};
+  layout(&tmp, sizing);
+  return sizing.off + 256;
+}
+
+int sim_enable_graphs(sim_handle* h, int enable) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (enable && !h->graphs) {
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    int rc = capture_graphs(h);
+    if (rc) return rc;
+    h->graphs = true;
+  } else if (!enable && h->graphs) {
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int p = 0; p < 8; ++p)
+      if (h->gexec[p]) { cudaGraphExecDestroy(h->gexec[p]); h->gexec[p] = nullptr; }
+    h->graphs = false;
+  }
+  return SIM_OK;
+}
+
+int sim_batch_step(sim_handle* const* hs, int count, int nsteps) {
+  if (!hs || count < 0 || nsteps < 0) return fail(SIM_EINVAL, "bad batch arguments");
+  for (int i = 0; i < count; ++i)
+    if (!hs[i]) return fail(SIM_EINVAL, "null handle in batch");
+  // interleave the handles step by step: each runs on its own stream, so the
+  // device overlaps the (mostly latency-bound) steps of small systems
+  for (int k = 0; k < nsteps; ++k)
+    for (int i = 0; i < count; ++i) {
+      if (k == 0) reset_records(hs[i]);
+      int rc = launch_step(hs[i]);
+      if (rc) return rc;
+    }
+  int first = SIM_OK;
+  for (int i = 0; i < count; ++i) {
+    int rc = check_status(hs[i]);
+    if (rc && first == SIM_OK) first = rc;
+  }
+  return first;
 }
 
 int sim_get_state(sim_handle* h, double* R, double* V, double* F, double* D0) {
@@ -780,9 +922,8 @@ int sim_set_state(sim_handle* h, const double* R, const double* V, const double*
   int rc = evaluate(h);
   if (rc) return rc;
   launch_kinetic(s, h->N, h->V, h->mass, h->sc);
-  record_kernel<<<1, 1, 0, s>>>(h->sc, h->cfg.Te, h->rec);
-  count_launch();
-  h->last_rec = 0;
+  reset_records(h);
+  record(h);
   return check_status(h);
 }
 
@@ -891,6 +1032,8 @@ int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sy
 void sim_destroy(sim_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int p = 0; p < 8; ++p)
+    if (h->gexec[p]) cudaGraphExecDestroy(h->gexec[p]);
   for (auto& p : h->ev_pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   if (h->tw.base) tc_work_release(h->tw);

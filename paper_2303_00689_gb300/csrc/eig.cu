@@ -20,6 +20,8 @@
 //     path; on the mixed path (128 per block) the two large products
 //     V^T Z and V (T W) run on the tensor cores with 4 fixed-point BF16
 //     slices, while the T factor and T W stay in FP64.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tc_gemm.h"
@@ -477,12 +479,18 @@ int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* 
   if (blocks < 1) blocks = 1;
   if (blocks > sm_count) blocks = sm_count;           // one block per SM (two were slower)
   size_t smem = (3 * (size_t)n + 32) * sizeof(double);
-  static size_t smem_set = 0;
-  if (smem > 48 * 1024 && smem > smem_set) {
-    if (cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return -1;
-    smem_set = smem;
+  if (smem > 48 * 1024) {
+    static std::mutex mu;          // raise the opt-in size monotonically (thread-safe)
+    static size_t smem_set = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (smem > smem_set) {
+      if (cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+      }
+      smem_set = smem;
+    }
   }
   {
     int nn = n;
@@ -543,12 +551,11 @@ static void transpose_sq(cudaStream_t s, int n, const double* A, double* At) {
 }
 
 static void eig_backtransform_tc(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork& tw) {
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
     cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kBtBlockTc * kBtBlockTc * (int)sizeof(double));
-    attr = true;
-  }
+  });
   const int nref = n - 2;
   const int nblk = (nref + kBtBlockTc - 1) / kBtBlockTc;
   const size_t stride = tc_slot_stride(tw);

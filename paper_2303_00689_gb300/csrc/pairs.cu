@@ -23,6 +23,8 @@
 //   E[pair]                        core-core energy
 //   dW[(k*100 + p*10 + q) * npair + pair], dS[(k*16 + ..)], dE[k*npair + pair]
 // Products: 0 ss, 1 sx, 2 sy, 3 sz, 4 xx, 5 yy, 6 zz, 7 xy, 8 xz, 9 yz.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -344,9 +346,7 @@ Poly ppow(const Poly& a, int k) {
 }
 }  // namespace
 
-bool upload_overlap_tables() {
-  static bool done = false;
-  if (done) return true;
+static bool upload_overlap_tables_once() {
   double tab[2][2][3][3][5][5] = {};
   const Poly vol = mono(0, 0, 0, 0, 1, -1);          // xi^2 - eta^2
   const Poly rA = mono(0, 1, 1, 0, 0, 0);            // xi + eta
@@ -378,8 +378,14 @@ bool upload_overlap_tables() {
   const double phi[3] = {2.0 * M_PI, 2.0 * M_PI, M_PI};
   if (cudaMemcpyToSymbol(c_ovl_poly, tab, sizeof(tab)) != cudaSuccess) return false;
   if (cudaMemcpyToSymbol(c_ovl_phi, phi, sizeof(phi)) != cudaSuccess) return false;
-  done = true;
   return true;
+}
+
+bool upload_overlap_tables() {
+  static std::once_flag once;
+  static bool ok = false;
+  std::call_once(once, [] { ok = upload_overlap_tables_once(); });
+  return ok;
 }
 
 void launch_pair_values(cudaStream_t s, int npair, const int* pA, const int* pB, const int* elem,

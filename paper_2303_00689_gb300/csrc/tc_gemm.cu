@@ -36,6 +36,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tc_gemm.h"
@@ -447,15 +449,14 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 static EncodeTiledFn encode_fn() {
   static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = (EncodeTiledFn)p;
-  }
+  });
   return fn;
 }
 
@@ -540,6 +541,13 @@ bool tc_ready(const TcWork& w) { return w.base && ((TcBuffers*)w.base)->maps_ok;
 
 int* tc_error_flag(const TcWork& w) { return w.base ? ((TcBuffers*)w.base)->err : nullptr; }
 
+static void set_smem_attribute() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  });
+}
+
 void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int slices, int transpose,
               const int* gate) {
   TcBuffers* tb = (TcBuffers*)w.base;
@@ -556,11 +564,7 @@ void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int sl
 void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, double alpha, double* C, int sym,
              const int* gate) {
   TcBuffers* tb = (TcBuffers*)w.base;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    attr = true;
-  }
+  set_smem_attribute();
   TcMaps maps;
   for (int k = 0; k < kTcMaxSlices; ++k) {
     maps.a[k] = tb->map[slotA][k];
@@ -610,11 +614,7 @@ void tc_split_rc(cudaStream_t s, int rows, int cols, const double* X, int ldx, i
 int tc_gemm_rc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, int lda, size_t astride,
                const __nv_bfloat16* Bbase, int ldb, size_t bstride, int terms, double alpha, double* C, int ldc,
                int beta, int* err) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    attr = true;
-  }
+  set_smem_attribute();
   int slices = (terms == 10) ? 4 : (terms == 6) ? 3 : (terms == 3) ? 2 : 1;
   TcMaps maps;
   for (int a = 0; a < kTcMaxSlices; ++a) {
@@ -650,11 +650,7 @@ void tc_split_strided(cudaStream_t s, int n, int ld, const double* X, int slices
 
 void tc_gemm_on_maps(cudaStream_t s, int n, const CUtensorMap* mapsA, const CUtensorMap* mapsB, int terms,
                      double alpha, double* C, int sym, int* err) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    attr = true;
-  }
+  set_smem_attribute();
   TcMaps maps;
   for (int k = 0; k < kTcMaxSlices; ++k) {
     maps.a[k] = mapsA[k];
