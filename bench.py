@@ -386,7 +386,7 @@ def run_serve(args):
     cfg = kx.sim_config_default(Te=1000.0, dt=0.5, m_max=4, m_min=4, precision=kx.SIM_PREC_MIXED,
                                 scf_tol=1e-7, scf_max=40, scf_krylov=1, scf_accept=1)
     count = args.serve_requests
-    reqs = synth.serving_requests(seed=4, count=count, rate_per_s=1.0)
+    reqs = synth.serving_requests(seed=4, count=count, rate_per_s=1.0, nmax=args.serve_nmax)
     work = sum(m.natoms * st for _, m, st in reqs)
 
     def replay(rate_scale):
@@ -401,7 +401,16 @@ def run_serve(args):
                         time.sleep(wait)
                 V = synth.maxwell_boltzmann(m.Z, 300.0, seed=int(ta * 1e3) % 100000)
                 tickets.append(srv.submit(cfg, table, m.Z, m.R, V=V, charge=m.charge, nsteps=st, records=False))
-            srv.drain(3600.0)
+            while True:                      # progress to stderr while draining
+                st = srv.stats()
+                print(f"serve t={time.perf_counter() - t0:7.1f}s done={st['completed']}+{st['failed']} "
+                      f"live={st['active']} queued={st['queued']} atom_steps={st['atom_steps']}",
+                      file=sys.stderr, flush=True)
+                if st["completed"] + st["failed"] == len(reqs):
+                    break
+                if time.perf_counter() - t0 > args.serve_timeout:
+                    raise RuntimeError("serving run exceeded --serve-timeout")
+                time.sleep(2.0)
             wall = time.perf_counter() - t0
             res = [srv.poll(t) for t in tickets]
             st = srv.stats()
@@ -420,7 +429,7 @@ def run_serve(args):
            "value": served["atom_steps_per_s"], "unit": "atom-steps/s", "n_gpus": 1, "steps": count,
            "warmup": 0, "ms_per_step": served["step_p50_ms"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64+bf16-slices", "data": "synthetic",
-           "config": {"workload": f"{count} requests, 20-600 atoms, 10-100 steps (seed 4)", "Te_K": 1000.0,
+           "config": {"workload": f"{count} requests, 20-{args.serve_nmax} atoms, 10-100 steps (seed 4)", "Te_K": 1000.0,
                       "krylov_rank": 4, "precision": "mixed", "offered_load": "0.8 x closed-loop capacity"},
            "latency_ms": {"p50": served["step_p50_ms"], "p99": served["step_p99_ms"]},
            "queue_ms": {"p50": served["queue_p50_ms"], "p99": served["queue_p99_ms"]},
@@ -458,6 +467,8 @@ def main():
                    help="md840: the headline single-system step; batch: 128-molecule batch; serve: "
                         "Poisson-arrival serving")
     p.add_argument("--serve-requests", type=int, default=48)
+    p.add_argument("--serve-nmax", type=int, default=600)
+    p.add_argument("--serve-timeout", type=float, default=900.0)
     p.add_argument("--profile-run", action="store_true",
                    help="short run for ncu (no SCF, no baselines); prints launch counts")
     args = p.parse_args()

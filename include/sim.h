@@ -218,8 +218,8 @@ int sim_batch_step(sim_handle* const* handles, int count, int nsteps);
 size_t sim_estimate_bytes(const sim_config* cfg, int natoms, const int* Z);
 
 /* ---- serving: continuous batching of many trajectories ------------------
- * A server owns a device, a memory budget and two host threads: an admission
- * thread that creates trajectories (SCF included) in submission order while
+ * A server owns a device, a memory budget and host threads: admission
+ * threads that create trajectories (SCF included) in submission order while
  * their estimated memory fits the budget and fewer than max_active are live,
  * and a stepping thread that keeps one step in flight per live trajectory
  * (each on its own stream, through CUDA graphs when use_graphs != 0) and
@@ -233,6 +233,7 @@ typedef struct sim_server_config {
   int max_active;           /* live trajectories at most (<= 0: 64)                */
   size_t hbm_budget_bytes;  /* device bytes for trajectories (0: 90% of free)      */
   int use_graphs;           /* step through CUDA graphs                            */
+  int admission_threads;    /* concurrent sim_create calls (<= 0: 4)               */
 } sim_server_config;
 
 typedef struct sim_request {
@@ -279,8 +280,8 @@ int sim_poll(sim_server* s, unsigned long long ticket, sim_traj_result* out);
 int sim_server_stats_get(sim_server* s, sim_server_stats* out);
 /* Wait until no trajectory is queued or live (SIM_ETIMEOUT after timeout_s). */
 int sim_server_drain(sim_server* s, double timeout_s);
-/* Stops both threads after the live trajectories finish their current step;
- * unfinished ones are dropped. */
+/* Stops the threads after the live trajectories finish their current step
+ * and the creations under way end; unfinished trajectories are dropped. */
 void sim_server_destroy(sim_server* s);
 
 /* sim_get_state -- copy the current state out (any pointer may be NULL).

@@ -59,7 +59,7 @@ class sim_step_result(C.Structure):
 
 class sim_server_config(C.Structure):
     _fields_ = [("device", C.c_int), ("max_active", C.c_int), ("hbm_budget_bytes", C.c_size_t),
-                ("use_graphs", C.c_int)]
+                ("use_graphs", C.c_int), ("admission_threads", C.c_int)]
 
 
 class sim_request(C.Structure):
@@ -338,9 +338,9 @@ def sim_estimate_bytes(cfg, Z):
 class Server:
     """sim_server_* wrapper: submit(...) -> ticket, poll(ticket) -> dict or None."""
 
-    def __init__(self, device=0, max_active=64, hbm_budget_bytes=0, use_graphs=True):
+    def __init__(self, device=0, max_active=64, hbm_budget_bytes=0, use_graphs=True, admission_threads=4):
         self._h = C.c_void_p()
-        cfg = sim_server_config(device, max_active, hbm_budget_bytes, 1 if use_graphs else 0)
+        cfg = sim_server_config(device, max_active, hbm_budget_bytes, 1 if use_graphs else 0, admission_threads)
         _check(lib().sim_server_create(C.byref(cfg), C.byref(self._h)))
         self._keep = {}
 

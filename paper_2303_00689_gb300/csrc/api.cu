@@ -706,11 +706,18 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
   Arena sizing{nullptr, 0, 0};
   layout(h, sizing);
   h->arena_bytes = sizing.off + 256;
-  if (cudaMalloc(&h->arena, h->arena_bytes) != cudaSuccess) {
+  // stream-ordered allocation: creating or destroying a handle does not
+  // synchronise the device (other handles keep running)
+  if (cudaMallocAsync(&h->arena, h->arena_bytes, h->stream) != cudaSuccess) {
     cudaGetLastError();
     size_t need = h->arena_bytes;
     sim_destroy(h);
     return fail(SIM_ENOMEM, "device allocation of " + std::to_string(need) + " bytes failed");
+  }
+  // the arena is used from other streams below (synchronous copies): wait for it
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    sim_destroy(h);
+    return fail(SIM_EINTERNAL, "stream synchronisation after allocation failed");
   }
   Arena a{(char*)h->arena, 0, h->arena_bytes};
   layout(h, a);
@@ -1037,7 +1044,10 @@ void sim_destroy(sim_handle* h) {
   for (auto& p : h->ev_pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   if (h->tw.base) tc_work_release(h->tw);
-  if (h->arena) cudaFree(h->arena);
+  if (h->arena) {
+    cudaFreeAsync(h->arena, h->stream);
+    cudaStreamSynchronize(h->stream);
+  }
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }

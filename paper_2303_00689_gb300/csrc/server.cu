@@ -1,9 +1,10 @@
 // Trajectory server: continuous batching of many independent MD trajectories
 // on one device under a memory budget (declared in include/sim.h).
 //
-// Two host threads.  The admission thread takes submitted requests in order,
-// reserves their estimated device bytes against the budget and runs
-// sim_create (SCF included) for each, then hands the handle over.  The
+// Host threads: admission threads take submitted requests in order, reserve
+// their estimated device bytes against the budget and run sim_create (SCF
+// included; several at once, each on its own stream), then hand the handle
+// over to the stepping thread.  The
 // stepping thread keeps up to two steps in flight per live trajectory, each
 // trajectory on its own stream, and polls CUDA events to relaunch the next
 // step as soon as one finishes; a trajectory whose steps are done is copied
@@ -73,7 +74,8 @@ struct sim_server {
   std::vector<float> lat_ms;
   bool stop = false;
   Clock::time_point t0;
-  std::thread admit_thr, step_thr;
+  std::vector<std::thread> admit_thr;
+  std::thread step_thr;
 };
 
 namespace {
@@ -243,8 +245,9 @@ int sim_server_create(const sim_server_config* cfg, sim_server** out) {
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { delete s; return SIM_EINTERNAL; }
     s->cfg.hbm_budget_bytes = (size_t)(0.9 * (double)fr);
   }
+  if (s->cfg.admission_threads <= 0) s->cfg.admission_threads = 4;
   s->t0 = Clock::now();
-  s->admit_thr = std::thread(admission_loop, s);
+  for (int i = 0; i < s->cfg.admission_threads; ++i) s->admit_thr.emplace_back(admission_loop, s);
   s->step_thr = std::thread(stepping_loop, s);
   *out = s;
   return SIM_OK;
@@ -340,7 +343,8 @@ void sim_server_destroy(sim_server* s) {
   }
   s->cv_admit.notify_all();
   s->cv_step.notify_all();
-  if (s->admit_thr.joinable()) s->admit_thr.join();
+  for (auto& t : s->admit_thr)
+    if (t.joinable()) t.join();
   if (s->step_thr.joinable()) s->step_thr.join();
   for (Job* j : s->ready) {
     for (int k = 0; k < kInFlight; ++k)
