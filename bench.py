@@ -409,7 +409,10 @@ def run_serve(args):
                 if st["completed"] + st["failed"] == len(reqs):
                     break
                 if time.perf_counter() - t0 > args.serve_timeout:
-                    raise RuntimeError("serving run exceeded --serve-timeout")
+                    # leave without joining the server's threads
+                    print(json.dumps({"error": "serving run exceeded --serve-timeout", "stats": st}),
+                          file=sys.stderr, flush=True)
+                    os._exit(3)
                 time.sleep(2.0)
             wall = time.perf_counter() - t0
             res = [srv.poll(t) for t in tickets]

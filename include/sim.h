@@ -210,8 +210,10 @@ int sim_enable_graphs(sim_handle* h, int enable);
  * each (molecule batches: one trajectory per molecule).  The steps are
  * issued round-robin, each handle on its own stream, so the device runs the
  * small, latency-bound steps of different molecules concurrently (with
- * graphs enabled each step is one graph launch).  Synchronous; returns the
- * first error.  Records of the steps are read with sim_records. */
+ * graphs enabled each step is one graph launch).  Handles are taken in
+ * groups whose persistent eigensolver grids fit on the device at the same
+ * time; groups run one after the other.  Synchronous; returns the first
+ * error.  Records of the steps are read with sim_records. */
 int sim_batch_step(sim_handle* const* handles, int count, int nsteps);
 
 /* Bytes of device memory sim_create allocates for this molecule/config. */
@@ -220,7 +222,9 @@ size_t sim_estimate_bytes(const sim_config* cfg, int natoms, const int* Z);
 /* ---- serving: continuous batching of many trajectories ------------------
  * A server owns a device, a memory budget and host threads: admission
  * threads that create trajectories (SCF included) in submission order while
- * their estimated memory fits the budget and fewer than max_active are live,
+ * their estimated memory fits the budget, fewer than max_active are live and
+ * the persistent eigensolver grids of all live trajectories fit on the
+ * device at once (their grid barriers need every block resident),
  * and a stepping thread that keeps one step in flight per live trajectory
  * (each on its own stream, through CUDA graphs when use_graphs != 0) and
  * retires a trajectory when its steps are done.  Every trajectory computes

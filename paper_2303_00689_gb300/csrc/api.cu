@@ -888,18 +888,32 @@ int sim_batch_step(sim_handle* const* hs, int count, int nsteps) {
   if (!hs || count < 0 || nsteps < 0) return fail(SIM_EINVAL, "bad batch arguments");
   for (int i = 0; i < count; ++i)
     if (!hs[i]) return fail(SIM_EINVAL, "null handle in batch");
-  // interleave the handles step by step: each runs on its own stream, so the
-  // device overlaps the (mostly latency-bound) steps of small systems
-  for (int k = 0; k < nsteps; ++k)
-    for (int i = 0; i < count; ++i) {
-      if (k == 0) reset_records(hs[i]);
-      int rc = launch_step(hs[i]);
-      if (rc) return rc;
-    }
   int first = SIM_OK;
-  for (int i = 0; i < count; ++i) {
-    int rc = check_status(hs[i]);
-    if (rc && first == SIM_OK) first = rc;
+  // groups of consecutive handles whose persistent eigensolver grids fit on
+  // the device at the same time (their grid barriers need every block resident)
+  for (int g0 = 0; g0 < count;) {
+    const long long cap = 1000LL * hs[g0]->sms;
+    long long load = 0;
+    int g1 = g0;
+    while (g1 < count) {
+      long long w = eig_tridiag_weight(hs[g1]->n, hs[g1]->sms);
+      if (g1 > g0 && load + w > cap) break;
+      load += w;
+      ++g1;
+    }
+    // interleave the group's handles step by step: each runs on its own stream,
+    // so the device overlaps the (mostly latency-bound) steps of small systems
+    for (int k = 0; k < nsteps; ++k)
+      for (int i = g0; i < g1; ++i) {
+        if (k == 0) reset_records(hs[i]);
+        int rc = launch_step(hs[i]);
+        if (rc) return rc;
+      }
+    for (int i = g0; i < g1; ++i) {
+      int rc = check_status(hs[i]);
+      if (rc && first == SIM_OK) first = rc;
+    }
+    g0 = g1;
   }
   return first;
 }

@@ -33,6 +33,20 @@ constexpr int kBtBlock = 64;          // reflectors per back-transform block (FP
 constexpr int kBtBlockTc = 128;       // reflectors per back-transform block (tensor-core path)
 constexpr double kEps = 2.220446049250313e-16;
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of the persistent tridiagonalisation.  The wait is bounded
+// in wall time (kBarrierNs) and by an iteration cap; a block that gives up, or
+// that finds another block's timeout flag set, records kStatusTimeout and the
+// kernel returns.  Correct operation needs every block resident at once
+// (cooperative launch; callers that run several such grids concurrently keep
+// their total within what the device holds at one time, eig_tridiag_weight).
+constexpr unsigned long long kBarrierNs = 2000000000ull;   // 2 s
+
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
   __shared__ int s_ok;
   __syncthreads();
@@ -46,9 +60,13 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
+      const unsigned long long t0 = global_ns();
       long long it = 0;
       while (*vgen == g) {
-        if (++it > (1LL << 25)) {
+        ++it;
+        if ((it & 63) == 0 &&
+            (global_ns() - t0 > kBarrierNs || it > (1LL << 27) ||
+             ((*(volatile int*)status) & kStatusTimeout))) {
           atomicOr(status, (int)kStatusTimeout);
           break;
         }
@@ -468,41 +486,65 @@ void eig_work_bind(EigWork& w, void* base, int n) {
   w.clus = (int*)p;
 }
 
+static int tridiag_blocks(int n, int sm_count) {
+  long long work = (long long)n * n;
+  int blocks = (int)((work + (1 << 16) - 1) >> 16);
+  if (blocks < 1) blocks = 1;
+  if (blocks > sm_count) blocks = sm_count;           // one block per SM (two were slower)
+  return blocks;
+}
+
+static size_t tridiag_smem(int n) { return (3 * (size_t)n + 32) * sizeof(double); }
+
+// raise the kernel's opt-in dynamic shared memory monotonically (thread-safe)
+static bool tridiag_smem_attribute(size_t smem) {
+  if (smem <= 48 * 1024) return true;
+  static std::mutex mu;
+  static size_t smem_set = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (smem > smem_set) {
+    if (cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    smem_set = smem;
+  }
+  return true;
+}
+
+int eig_tridiag_weight(int n, int sm_count) {
+  if (n <= 0) return 0;
+  size_t smem = tridiag_smem(n);
+  int per_sm = 0;
+  if (!tridiag_smem_attribute(smem) ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, kTriThreads, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  long long b = tridiag_blocks(n, sm_count);
+  return (int)((1000LL * b + per_sm - 1) / per_sm);
+}
+
 int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* status, int sm_count) {
   if (n <= 0) return 0;
   cudaMemcpyAsync(w.A, F, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s);
   cudaMemsetAsync(w.e, 0, (size_t)n * sizeof(double), s);
   // 1. tridiagonalisation
-  long long work = (long long)n * n;
-  int blocks = (int)((work + (1 << 16) - 1) >> 16);
-  if (blocks < 1) blocks = 1;
-  if (blocks > sm_count) blocks = sm_count;           // one block per SM (two were slower)
-  size_t smem = (3 * (size_t)n + 32) * sizeof(double);
-  if (smem > 48 * 1024) {
-    static std::mutex mu;          // raise the opt-in size monotonically (thread-safe)
-    static size_t smem_set = 0;
-    std::lock_guard<std::mutex> lk(mu);
-    if (smem > smem_set) {
-      if (cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess) {
-        cudaGetLastError();
-        return -1;
-      }
-      smem_set = smem;
-    }
-  }
-  {
-    int nn = n;
-    double *A = w.A, *V = w.Vst, *d = w.d, *e = w.e, *t = w.tau, *pb = w.pbuf;
-    unsigned* bar = w.bar;
-    int* st = status;
-    void* args[] = {&nn, &A, &V, &d, &e, &t, &pb, &bar, &st};
-    if (cudaLaunchCooperativeKernel((void*)tridiag_kernel, dim3(blocks), dim3(kTriThreads), args, smem, s) !=
-        cudaSuccess)
-      return -2;
-    count_launch();
-  }
+  int blocks = tridiag_blocks(n, sm_count);
+  size_t smem = tridiag_smem(n);
+  if (!tridiag_smem_attribute(smem)) return -1;
+  int nn = n;
+  double *A = w.A, *V = w.Vst, *d = w.d, *e = w.e, *t = w.tau, *pb = w.pbuf;
+  unsigned* bar = w.bar;
+  int* st = status;
+  void* args[] = {&nn, &A, &V, &d, &e, &t, &pb, &bar, &st};
+  if (cudaLaunchCooperativeKernel((void*)tridiag_kernel, dim3(blocks), dim3(kTriThreads), args, smem, s) !=
+      cudaSuccess)
+    return -2;
+  count_launch();
   return 0;
 }
 

@@ -65,6 +65,10 @@ void eig_work_bind(EigWork& w, void* base, int n);
 // F (n x n symmetric, row-major) -> eps ascending, Q (eigenvectors as columns),
 // in three stages (tridiagonalise; tridiagonal eigenpairs into Q; back-transform Q)
 int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* status, int sm_count);
+// Share of the device, in thousandths of an SM, that the cooperative
+// tridiagonalisation grid of size n occupies while resident (blocks divided by
+// blocks per SM).  Grids that run concurrently must sum to <= 1000 x SMs.
+int eig_tridiag_weight(int n, int sm_count);
 void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w);                       // eigenvalues
 void eig_vectors(cudaStream_t s, int n, const double* eps, double* Q, EigWork& w);     // tridiagonal vectors
 struct TcWork;

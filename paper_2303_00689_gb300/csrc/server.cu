@@ -4,7 +4,9 @@
 // Host threads: admission threads take submitted requests in order, reserve
 // their estimated device bytes against the budget and run sim_create (SCF
 // included; several at once, each on its own stream), then hand the handle
-// over to the stepping thread.  The
+// over to the stepping thread; admission also keeps the eigensolver's
+// cooperative grids of all live trajectories within what the device holds at
+// once.  The
 // stepping thread keeps up to two steps in flight per live trajectory, each
 // trajectory on its own stream, and polls CUDA events to relaunch the next
 // step as soon as one finishes; a trajectory whose steps are done is copied
@@ -25,6 +27,7 @@
 #include <vector>
 
 #include "../../include/sim.h"
+#include "kernels.h"
 
 namespace {
 
@@ -45,6 +48,7 @@ struct Job {
   std::vector<double> R, V;
   bool has_V = false;
   size_t bytes = 0;
+  long long weight = 0;            // co-residency share of its cooperative grid (thousandths of an SM)
   Clock::time_point t_submit, t_admit, t_first, t_last;
   sim_handle* h = nullptr;
   int launched = 0, done = 0;
@@ -69,6 +73,8 @@ struct sim_server {
   std::unordered_map<unsigned long long, Job*> finished;   // waiting for sim_poll
   unsigned long long next_ticket = 1;
   size_t in_use = 0;
+  long long coop_in_use = 0, coop_cap = 0;
+  int sms = 0;
   long long live = 0;
   long long submitted = 0, completed = 0, failed = 0, max_active_seen = 0, atom_steps = 0;
   std::vector<float> lat_ms;
@@ -89,6 +95,7 @@ void retire(sim_server* s, Job* j) {
   }
   std::lock_guard<std::mutex> lk(s->mu);
   s->in_use -= j->bytes;
+  s->coop_in_use -= j->weight;
   s->live -= 1;
   if (j->res.status == SIM_OK) s->completed += 1; else s->failed += 1;
   s->pending.erase(j->ticket);
@@ -104,13 +111,18 @@ void admission_loop(sim_server* s) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_admit.wait(lk, [&] {
+        // the persistent eigensolver grids of all live trajectories must fit
+        // on the device at once, or their grid barriers could wait on blocks
+        // that cannot become resident
         return s->stop || (!s->queue.empty() && s->live < s->cfg.max_active &&
-                           s->in_use + s->queue.front()->bytes <= s->cfg.hbm_budget_bytes);
+                           s->in_use + s->queue.front()->bytes <= s->cfg.hbm_budget_bytes &&
+                           (s->live == 0 || s->coop_in_use + s->queue.front()->weight <= s->coop_cap));
       });
       if (s->stop) return;
       j = s->queue.front();
       s->queue.pop_front();
       s->in_use += j->bytes;
+      s->coop_in_use += j->weight;
       s->live += 1;
       s->max_active_seen = std::max(s->max_active_seen, s->live);
     }
@@ -246,6 +258,8 @@ int sim_server_create(const sim_server_config* cfg, sim_server** out) {
     s->cfg.hbm_budget_bytes = (size_t)(0.9 * (double)fr);
   }
   if (s->cfg.admission_threads <= 0) s->cfg.admission_threads = 4;
+  cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->cfg.device);
+  s->coop_cap = 1000LL * s->sms;
   s->t0 = Clock::now();
   for (int i = 0; i < s->cfg.admission_threads; ++i) s->admit_thr.emplace_back(admission_loop, s);
   s->step_thr = std::thread(stepping_loop, s);
@@ -270,6 +284,14 @@ int sim_submit(sim_server* s, const sim_request* req, unsigned long long* ticket
   j->req.R = nullptr;
   j->req.V = nullptr;
   j->bytes = bytes;
+  {
+    int n = 0, prev = 0;
+    for (int A = 0; A < req->natoms; ++A) n += (req->Z[A] == 1) ? 1 : 4;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->cfg.device);
+    j->weight = kx::eig_tridiag_weight(n, s->sms);
+    cudaSetDevice(prev);
+  }
   j->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);
