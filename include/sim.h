@@ -271,6 +271,8 @@ typedef struct sim_server_stats {
   double step_p99_ms;       /*   completions of consecutive steps of one trajectory*/
   double elapsed_s;         /* since sim_server_create                             */
   size_t hbm_in_use, hbm_budget;
+  char threads[512];        /* diagnostics: what each server thread is doing and  */
+                            /*   ticket:done/launched/nsteps of live trajectories */
 } sim_server_stats;
 
 int sim_server_create(const sim_server_config* cfg, sim_server** out);

@@ -79,7 +79,8 @@ class sim_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
                 ("queued", C.c_longlong), ("active", C.c_longlong), ("max_active_seen", C.c_longlong),
                 ("atom_steps", C.c_longlong), ("step_p50_ms", C.c_double), ("step_p99_ms", C.c_double),
-                ("elapsed_s", C.c_double), ("hbm_in_use", C.c_size_t), ("hbm_budget", C.c_size_t)]
+                ("elapsed_s", C.c_double), ("hbm_in_use", C.c_size_t), ("hbm_budget", C.c_size_t),
+                ("threads", C.c_char * 512)]
 
 
 _lib_handle = None
@@ -378,7 +379,9 @@ class Server:
     def stats(self):
         st = sim_server_stats()
         _check(lib().sim_server_stats_get(self._h, C.byref(st)))
-        return {f: getattr(st, f) for f, _ in sim_server_stats._fields_}
+        out = {f: getattr(st, f) for f, _ in sim_server_stats._fields_}
+        out["threads"] = st.threads.decode(errors="replace")
+        return out
 
     def drain(self, timeout_s=600.0):
         _check(lib().sim_server_drain(self._h, float(timeout_s)))

@@ -327,7 +327,9 @@ __global__ void cluster_kernel(int n, const double* __restrict__ ev, const doubl
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double ctol = 1e-7 * fmax(1.0, scal[2]);
-  clus[i] = (i == 0 || ev[i] - ev[i - 1] > ctol) ? 1 : 0;
+  // a NaN gap starts a new cluster: non-finite input must not merge the whole
+  // spectrum into one cluster (one thread would then orthogonalise n vectors)
+  clus[i] = (i == 0 || !(ev[i] - ev[i - 1] <= ctol)) ? 1 : 0;
 }
 
 __device__ __forceinline__ double start_value(int row, int col) {

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -38,7 +39,7 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 }
 
 constexpr int kInFlight = 2;     // steps queued per trajectory
-constexpr int kCheckEvery = 32;  // device status check interval (steps)
+constexpr int kCheckEvery = 8;   // device status check interval (steps)
 constexpr int kMaxRecords = 4096;
 
 struct Job {
@@ -82,9 +83,27 @@ struct sim_server {
   Clock::time_point t0;
   std::vector<std::thread> admit_thr;
   std::thread step_thr;
+  // diagnostics: what each thread is doing (slot 0: stepping, 1..: admission)
+  static constexpr int kSlots = 17;
+  std::atomic<int> act[kSlots];
+  std::atomic<unsigned long long> act_ticket[kSlots];
+  std::mutex live_mu;
+  std::string live_desc;        // stepping thread's view of its live trajectories
+  sim_server() {
+    for (int i = 0; i < kSlots; ++i) { act[i] = 0; act_ticket[i] = 0; }
+  }
 };
 
 namespace {
+
+enum Act { A_IDLE = 0, A_CREATE, A_GRAPHS, A_EVENTS, A_QUERY, A_LAUNCH, A_WAIT, A_FINISH, A_RETIRE };
+const char* kActNames[] = {"idle", "create", "graphs", "events", "query", "launch", "wait", "finish", "retire"};
+
+void mark(sim_server* s, int slot, int what, unsigned long long ticket) {
+  if (slot < 0 || slot >= sim_server::kSlots) return;
+  s->act[slot].store(what);
+  s->act_ticket[slot].store(ticket);
+}
 
 void retire(sim_server* s, Job* j) {
   if (j->h) {
@@ -104,9 +123,10 @@ void retire(sim_server* s, Job* j) {
   s->cv_done.notify_all();
 }
 
-void admission_loop(sim_server* s) {
+void admission_loop(sim_server* s, int slot) {
   cudaSetDevice(s->cfg.device);
   for (;;) {
+    mark(s, slot, A_IDLE, 0);
     Job* j = nullptr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
@@ -131,14 +151,18 @@ void admission_loop(sim_server* s) {
     sim_config c = j->req.cfg;
     c.device = s->cfg.device;
     c.stream = nullptr;
+    mark(s, slot, A_CREATE, j->ticket);
     int rc = sim_create(&c, &j->req.table, j->req.natoms, j->Z.data(), j->R.data(),
                         j->has_V ? j->V.data() : nullptr, j->req.charge, nullptr, &j->h);
+    mark(s, slot, A_GRAPHS, j->ticket);
     if (rc == SIM_OK && s->cfg.use_graphs) rc = sim_enable_graphs(j->h, 1);
+    mark(s, slot, A_EVENTS, j->ticket);
     for (int k = 0; rc == SIM_OK && k < kInFlight; ++k)
       if (cudaEventCreateWithFlags(&j->ev[k], cudaEventDisableTiming) != cudaSuccess) rc = SIM_EINTERNAL;
     j->res.create_ms = ms_between(j->t_admit, Clock::now());
     if (rc != SIM_OK) {
       set_error(j, rc, sim_last_error());
+      mark(s, slot, A_RETIRE, j->ticket);
       retire(s, j);
       continue;
     }
@@ -190,6 +214,7 @@ void stepping_loop(sim_server* s) {
       int rc = SIM_OK;
       // collect finished steps in order
       while (rc == SIM_OK && j->done < j->launched) {
+        mark(s, 0, A_QUERY, j->ticket);
         cudaError_t q = cudaEventQuery(j->ev[j->done % kInFlight]);
         if (q == cudaErrorNotReady) break;
         if (q != cudaSuccess) { rc = SIM_EINTERNAL; break; }
@@ -199,7 +224,10 @@ void stepping_loop(sim_server* s) {
         j->done += 1;
         steps_now += j->req.natoms;
         progressed = true;
-        if (j->done % kCheckEvery == 0) rc = sim_wait(j->h);
+        if (j->done % kCheckEvery == 0) {
+          mark(s, 0, A_WAIT, j->ticket);
+          rc = sim_wait(j->h);
+        }
       }
       // keep the pipeline full
       while (rc == SIM_OK && j->launched < nsteps && j->launched - j->done < kInFlight) {
@@ -207,6 +235,7 @@ void stepping_loop(sim_server* s) {
           j->t_first = Clock::now();
           j->t_last = j->t_first;
         }
+        mark(s, 0, A_LAUNCH, j->ticket);
         rc = launch_one(j);
         progressed = true;
       }
@@ -214,8 +243,10 @@ void stepping_loop(sim_server* s) {
         if (rc != SIM_OK) {
           set_error(j, rc, sim_last_error());
           j->res.steps_done = j->done;
+          mark(s, 0, A_RETIRE, j->ticket);
           retire(s, j);
         } else {
+          mark(s, 0, A_FINISH, j->ticket);
           finish(s, j);
         }
         active[i] = active.back();
@@ -229,6 +260,17 @@ void stepping_loop(sim_server* s) {
       s->atom_steps += steps_now;
       if (s->lat_ms.size() < (size_t)4000000) s->lat_ms.insert(s->lat_ms.end(), lat.begin(), lat.end());
       lat.clear();
+    }
+    mark(s, 0, A_IDLE, 0);
+    {
+      std::string d;
+      char buf[64];
+      for (Job* j : active) {
+        std::snprintf(buf, sizeof buf, " #%llu:%d/%d/%d", j->ticket, j->done, j->launched, j->req.nsteps);
+        d += buf;
+      }
+      std::lock_guard<std::mutex> lk(s->live_mu);
+      s->live_desc = d;
     }
     if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
@@ -261,7 +303,8 @@ int sim_server_create(const sim_server_config* cfg, sim_server** out) {
   cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->cfg.device);
   s->coop_cap = 1000LL * s->sms;
   s->t0 = Clock::now();
-  for (int i = 0; i < s->cfg.admission_threads; ++i) s->admit_thr.emplace_back(admission_loop, s);
+  if (s->cfg.admission_threads > sim_server::kSlots - 1) s->cfg.admission_threads = sim_server::kSlots - 1;
+  for (int i = 0; i < s->cfg.admission_threads; ++i) s->admit_thr.emplace_back(admission_loop, s, i + 1);
   s->step_thr = std::thread(stepping_loop, s);
   *out = s;
   return SIM_OK;
@@ -338,6 +381,20 @@ int sim_server_stats_get(sim_server* s, sim_server_stats* out) {
     lat = s->lat_ms;
   }
   out->elapsed_s = ms_between(s->t0, Clock::now()) / 1e3;
+  {
+    std::string d = "step:";
+    char buf[48];
+    for (int i = 0; i <= s->cfg.admission_threads && i < sim_server::kSlots; ++i) {
+      if (i == 1) d += " admit:";
+      std::snprintf(buf, sizeof buf, " %s#%llu", kActNames[s->act[i].load()], s->act_ticket[i].load());
+      d += buf;
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->live_mu);
+      d += " live:" + s->live_desc;
+    }
+    std::snprintf(out->threads, sizeof(out->threads), "%s", d.c_str());
+  }
   out->step_p50_ms = out->step_p99_ms = 0.0;
   if (!lat.empty()) {
     size_t i50 = lat.size() / 2, i99 = std::min(lat.size() - 1, (size_t)(0.99 * (double)lat.size()));

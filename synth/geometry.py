@@ -222,13 +222,20 @@ def fullerene_c60(seed=5, copies=1, bond=1.42, spacing=12.0, charge=0):
     return Molecule(np.full(len(R), 6, dtype=np.int32), R, charge=charge)
 
 
-def serving_requests(seed=4, count=64, rate_per_s=1.0, nmin=20, nmax=600, smin=10, smax=100):
-    """Poisson arrivals of MD requests: (arrival_s, Molecule, nsteps) tuples."""
+def serving_requests(seed=4, count=64, rate_per_s=1.0, nmin=20, nmax=600, smin=10, smax=100, kind="organic"):
+    """Poisson arrivals of MD requests: (arrival_s, Molecule, nsteps) tuples.
+
+    kind "organic": C/N/O/H trees of nmin..nmax atoms.  kind "fullerene":
+    1..nmax/60 C60 cages (60..600 atoms) at a 1.60 A bond length."""
     rng = _rng(404, seed)
     t = 0.0
     out = []
     for _ in range(count):
         t += rng.exponential(1.0 / rate_per_s)
-        mol = organic_molecule(rng, int(rng.integers(nmin, nmax + 1)))
+        if kind == "fullerene":
+            k = int(rng.integers(max(1, nmin // 60), max(1, nmax // 60) + 1))
+            mol = fullerene_c60(seed=int(rng.integers(1 << 30)), copies=k, bond=1.60)
+        else:
+            mol = organic_molecule(rng, int(rng.integers(nmin, nmax + 1)))
         out.append((t, mol, int(rng.integers(smin, smax + 1))))
     return out
