@@ -38,6 +38,7 @@ WORKLOAD = dict(workload="840-atom random carbon packing, 2.2 g/cc, open box (se
                 l2="working set > L2 (no flush needed)")
 METRIC = "atom-steps/s (KSA-XL-BOMD MD step)"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk x 2 flop x max clock
+TRIDIAG_TRAFFIC_BYTES = 0.909e9 + 40.228e9       # dram read + write, one launch at n = 3360
 
 
 def _dist():
@@ -231,8 +232,11 @@ def _roofline(name, ph, per_launch_s):
     work = ph["work"]
     if name in ("eig_tridiag", "eig_backtransform", "density_gemm") or (name == "krylov_dmpt_gemm" and False):
         achieved = work / per_launch_s / 1e12
+        # DRAM bytes of one tridiag_kernel launch from the ncu capture summarised in
+        # profiles/tridiag_kernel_c840_n3360.md (same kernel and workload)
+        traffic = TRIDIAG_TRAFFIC_BYTES if name == "eig_tridiag" else None
         return {"kernel_phase": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "derived FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"}
     if name == "krylov_dmpt_gemm":
         achieved = work / per_launch_s / 1e12
