@@ -48,6 +48,23 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device):
+    """Largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(total_ms, steps, natoms_per_rank, world):
+    """(ms per step, whole-job atom-steps/s): every rank steps its own replica."""
+    ms_per_step = total_ms / steps
+    return ms_per_step, world * natoms_per_rank / (ms_per_step / 1e3)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -164,12 +181,8 @@ def run_ours(args):
     total_ms = evs[0].elapsed_time(evs[-1])
     phases = kx.sim_phase_times(h)
     kx.sim_profile_enable(h, False)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * N / (ms_per_step / 1e3)
+    total_ms = max_over_ranks(total_ms, world, "cuda")
+    ms_per_step, value = job_throughput(total_ms, args.steps, N, world)
 
     # ---- end to end through the C ABI with pinned host buffers --------------------
     pin = lambda: torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
@@ -187,10 +200,7 @@ def run_ours(args):
         R_h[:] = R_o
         V_h[:] = V_o
     e2e_s = (time.perf_counter() - te) / n_e2e
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, "cuda")
     kx.sim_destroy(h)
 
     # ---- dominant phase roofline -----------------------------------------------
