@@ -207,12 +207,20 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
 
 // Gershgorin interval, squared off-diagonals, pivmin; one block
 __global__ void gersh_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
-                             double* __restrict__ e2, double* __restrict__ scal) {
+                             double* __restrict__ e2, double* __restrict__ scal, float* __restrict__ df,
+                             float* __restrict__ e2f) {
   double lo = 1e300, hi = -1e300, em = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double r = 0.0;
+    df[i] = (float)d[i];                 // FP32 copies for the coarse phase (no per-step conversions)
+    e2f[i] = 0.0f;
     if (i > 0) r += fabs(e[i - 1]);
-    if (i < n - 1) { r += fabs(e[i]); e2[i] = e[i] * e[i]; em = fmax(em, e[i] * e[i]); }
+    if (i < n - 1) {
+      r += fabs(e[i]);
+      e2[i] = e[i] * e[i];
+      e2f[i] = (float)e2[i];
+      em = fmax(em, e[i] * e[i]);
+    }
     lo = fmin(lo, d[i] - r);
     hi = fmax(hi, d[i] + r);
   }
@@ -270,13 +278,13 @@ __device__ __forceinline__ int sturm_count(int n, const double* __restrict__ d,
 }
 
 // FP32 Sturm count (ratio form with a pivot floor) for the coarse phase
-__device__ __forceinline__ int sturm_count_f32(int n, const double* __restrict__ d,
-                                               const double* __restrict__ e2, float x, float pivmin) {
-  float q = (float)d[0] - x;
+__device__ __forceinline__ int sturm_count_f32(int n, const float* __restrict__ d,
+                                               const float* __restrict__ e2, float x, float pivmin) {
+  float q = d[0] - x;
   if (fabsf(q) <= pivmin) q = -pivmin;
   int c = (q < 0.0f);
   for (int j = 1; j < n; ++j) {
-    q = ((float)d[j] - x) - (float)e2[j - 1] / q;
+    q = (d[j] - x) - e2[j - 1] / q;
     if (fabsf(q) <= pivmin) q = -pivmin;
     c += (q < 0.0f);
   }
@@ -287,7 +295,8 @@ __device__ __forceinline__ int sturm_count_f32(int n, const double* __restrict__
 // Gershgorin width, a bracket check in FP64 (widened until
 // count(lo) <= i < count(hi)), then FP64 bisection to full accuracy.
 __global__ void bisect_kernel(int n, const double* __restrict__ d, const double* __restrict__ e2,
-                              const double* __restrict__ scal, double* __restrict__ ev) {
+                              const double* __restrict__ scal, const float* __restrict__ df,
+                              const float* __restrict__ e2f, double* __restrict__ ev) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double glo = scal[0], ghi = scal[1], pivmin = scal[3];
@@ -297,7 +306,7 @@ __global__ void bisect_kernel(int n, const double* __restrict__ d, const double*
   const float piv32 = fmaxf((float)(1e-30 * fmax(1.0, width)), 1e-30f);
   for (int it = 0; it < 22; ++it) {
     float mid = 0.5f * (lo32 + hi32);
-    if (sturm_count_f32(n, d, e2, mid, piv32) > i) hi32 = mid; else lo32 = mid;
+    if (sturm_count_f32(n, df, e2f, mid, piv32) > i) hi32 = mid; else lo32 = mid;
   }
   // bracket check in FP64, widening geometrically if the FP32 counts erred
   double w = fmax((double)hi32 - (double)lo32, 1e-12 * width);
@@ -338,7 +347,11 @@ __device__ __forceinline__ double start_value(int row, int col) {
   return ((double)(h & 0xFFFFF) / 524288.0) - 1.0 + 1e-3;
 }
 
-// inverse iteration; one thread per cluster leader; lu: 5 x n x n workspace
+// inverse iteration; one thread per cluster leader; lu: 5 x n x n workspace.
+// The recurrences carry their running values in registers (a global store
+// followed by a dependent reload would put memory latency on the critical
+// path); the arithmetic and its order are those of the textbook pivoted
+// tridiagonal LU and its forward/backward substitutions.
 __global__ void invit_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
                              const double* __restrict__ ev, const double* __restrict__ scal,
                              const int* __restrict__ clus, double* __restrict__ lu,
@@ -350,11 +363,11 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
   const double tn = fmax(scal[2], 1e-300);
   const double tiny = kEps * tn;
   const size_t nn = (size_t)n * n;
-  double* dl = lu + 0 * nn;
-  double* dd = lu + 1 * nn;
-  double* du = lu + 2 * nn;
-  double* du2 = lu + 3 * nn;
-  double* pv = lu + 4 * nn;
+  double* __restrict__ dl = lu + 0 * nn;
+  double* __restrict__ rdd = lu + 1 * nn;   // reciprocal pivots
+  double* __restrict__ du = lu + 2 * nn;
+  double* __restrict__ du2 = lu + 3 * nn;
+  double* __restrict__ pv = lu + 4 * nn;
 #define LU(a, r) a[(size_t)(r) * n + L]
 #define ZC(r, c) Z[(size_t)(r) * n + (c)]
   double prevlam = 0.0;
@@ -363,53 +376,69 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
     if (j > L && lam - prevlam < 10.0 * tiny) lam = prevlam + 10.0 * tiny;
     prevlam = lam;
     if (n == 1) { ZC(0, j) = 1.0; continue; }
-    // LU of T - lam I with partial pivoting
-    for (int r = 0; r < n; ++r) {
-      LU(dd, r) = d[r] - lam;
-      if (r < n - 1) { LU(dl, r) = e[r]; LU(du, r) = e[r]; }
-      LU(du2, r) = 0.0;
-    }
+    // LU of T - lam I with partial pivoting; a, u: pivot-row diagonal and superdiagonal
+    double a = d[0] - lam, u = e[0];
     for (int r = 0; r < n - 1; ++r) {
-      double a = LU(dd, r), b = LU(dl, r);
+      const double b = e[r];
+      const double dn = d[r + 1] - lam;
+      const double un = (r < n - 2) ? e[r + 1] : 0.0;
       if (fabs(a) >= fabs(b)) {
         LU(pv, r) = 0.0;
-        if (fabs(a) < tiny) { a = (a >= 0.0) ? tiny : -tiny; LU(dd, r) = a; }
-        double f = b / a;
+        if (fabs(a) < tiny) a = (a >= 0.0) ? tiny : -tiny;
+        const double f = b / a;
         LU(dl, r) = f;
-        LU(dd, r + 1) = LU(dd, r + 1) - f * LU(du, r);
+        LU(rdd, r) = 1.0 / a;
+        LU(du, r) = u;
+        LU(du2, r) = 0.0;
+        a = dn - f * u;
+        u = un;
       } else {
         LU(pv, r) = 1.0;
-        double f = a / b;
-        LU(dd, r) = b;
+        const double f = a / b;
+        LU(rdd, r) = 1.0 / b;
         LU(dl, r) = f;
-        double t = LU(du, r);
-        LU(du, r) = LU(dd, r + 1);
-        LU(dd, r + 1) = t - f * LU(dd, r + 1);
+        LU(du, r) = dn;
+        const double na = u - f * dn;
         if (r < n - 2) {
-          LU(du2, r) = LU(du, r + 1);
-          LU(du, r + 1) = -f * LU(du, r + 1);
+          LU(du2, r) = un;
+          u = -f * un;
+        } else {
+          LU(du2, r) = 0.0;
         }
+        a = na;
       }
     }
-    if (fabs(LU(dd, n - 1)) < tiny) LU(dd, n - 1) = (LU(dd, n - 1) >= 0.0) ? tiny : -tiny;
-    for (int r = 0; r < n; ++r) LU(dd, r) = 1.0 / LU(dd, r);      // reciprocal pivots
+    if (fabs(a) < tiny) a = (a >= 0.0) ? tiny : -tiny;
+    LU(rdd, n - 1) = 1.0 / a;
     for (int r = 0; r < n; ++r) ZC(r, j) = start_value(r, j);
     for (int it = 0; it < 2; ++it) {
-      // forward (L with pivots)
+      // forward (L with pivots); cur = current row r of the right-hand side
+      double cur = ZC(0, j);
       for (int r = 0; r < n - 1; ++r) {
-        double br = ZC(r, j), br1 = ZC(r + 1, j);
+        const double nxt = ZC(r + 1, j);
+        const double f = LU(dl, r);
         if (LU(pv, r) == 0.0) {
-          ZC(r + 1, j) = br1 - LU(dl, r) * br;
+          ZC(r, j) = cur;
+          cur = nxt - f * cur;
         } else {
-          ZC(r, j) = br1;
-          ZC(r + 1, j) = br - LU(dl, r) * br1;
+          ZC(r, j) = nxt;
+          cur = cur - f * nxt;
         }
       }
-      // backward (U, three diagonals; dd holds reciprocal pivots)
-      ZC(n - 1, j) = ZC(n - 1, j) * LU(dd, n - 1);
-      if (n > 1) ZC(n - 2, j) = (ZC(n - 2, j) - LU(du, n - 2) * ZC(n - 1, j)) * LU(dd, n - 2);
-      for (int r = n - 3; r >= 0; --r)
-        ZC(r, j) = (ZC(r, j) - LU(du, r) * ZC(r + 1, j) - LU(du2, r) * ZC(r + 2, j)) * LU(dd, r);
+      // backward (U, three diagonals, reciprocal pivots); z1 = x[r+1], z2 = x[r+2]
+      double z2 = cur * LU(rdd, n - 1);
+      ZC(n - 1, j) = z2;
+      double z1 = z2;
+      if (n > 1) {
+        z1 = (ZC(n - 2, j) - LU(du, n - 2) * z2) * LU(rdd, n - 2);
+        ZC(n - 2, j) = z1;
+      }
+      for (int r = n - 3; r >= 0; --r) {
+        const double x = (ZC(r, j) - LU(du, r) * z1 - LU(du2, r) * z2) * LU(rdd, r);
+        ZC(r, j) = x;
+        z2 = z1;
+        z1 = x;
+      }
       // scale, re-orthogonalise within the cluster, normalise
       double mx = 0.0;
       for (int r = 0; r < n; ++r) mx = fmax(mx, fabs(ZC(r, j)));
@@ -553,9 +582,12 @@ int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* 
 void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w) {
   if (n <= 0) return;
   // 2. eigenvalues
-  gersh_kernel<<<1, 1024, 0, s>>>(n, w.d, w.e, w.e2, w.scal);
+  // pbuf (2n doubles, free after the tridiagonalisation) holds the FP32 copies
+  float* df = (float*)w.pbuf;
+  float* e2f = df + n;
+  gersh_kernel<<<1, 1024, 0, s>>>(n, w.d, w.e, w.e2, w.scal, df, e2f);
   count_launch();
-  bisect_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e2, w.scal, eps);   // spread over all SMs
+  bisect_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e2, w.scal, df, e2f, eps);   // spread over all SMs
   count_launch();
 }
 
