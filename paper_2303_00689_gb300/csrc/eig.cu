@@ -385,17 +385,19 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
       if (fabs(a) >= fabs(b)) {
         LU(pv, r) = 0.0;
         if (fabs(a) < tiny) a = (a >= 0.0) ? tiny : -tiny;
-        const double f = b / a;
+        const double ra = 1.0 / a;          // one division per row (the FP64 divide is slow)
+        const double f = b * ra;
         LU(dl, r) = f;
-        LU(rdd, r) = 1.0 / a;
+        LU(rdd, r) = ra;
         LU(du, r) = u;
         LU(du2, r) = 0.0;
         a = dn - f * u;
         u = un;
       } else {
         LU(pv, r) = 1.0;
-        const double f = a / b;
-        LU(rdd, r) = 1.0 / b;
+        const double rb = 1.0 / b;
+        const double f = a * rb;
+        LU(rdd, r) = rb;
         LU(dl, r) = f;
         LU(du, r) = dn;
         const double na = u - f * dn;
@@ -462,8 +464,8 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
 
 // T factor of a block of kb reflectors (forward, columnwise): one block,
 // T held in shared memory, each entry a dot product split over 4 partial sums
-__global__ void tfactor_kernel(int kb, const double* __restrict__ tau, const double* __restrict__ G,
-                               int ldg, double* __restrict__ T, int ldt) {
+__device__ void tfactor_body(int kb, const double* __restrict__ tau, const double* __restrict__ G, int ldg,
+                             double* __restrict__ T, int ldt) {
   extern __shared__ double ts[];          // kb x kb
   __shared__ double gcol[kBtBlockTc];
   const int i = threadIdx.x;
@@ -490,10 +492,30 @@ __global__ void tfactor_kernel(int kb, const double* __restrict__ tau, const dou
   for (int e = i; e < kb * kb; e += blockDim.x) T[(e / kb) * ldt + e % kb] = ts[e];
 }
 
+__global__ void tfactor_kernel(int kb, const double* __restrict__ tau, const double* __restrict__ G,
+                               int ldg, double* __restrict__ T, int ldt) {
+  tfactor_body(kb, tau, G, ldg, T, ldt);
+}
+
+// T factors of every block of kblk reflectors at once (block b: reflectors
+// b*kblk .. ; they depend on the reflectors only, not on the vectors updated)
+__global__ void tfactor_all_kernel(int nref, int kblk, const double* __restrict__ tau,
+                                   const double* __restrict__ Gall, double* __restrict__ Tall) {
+  const int b = blockIdx.x;
+  const int k0 = b * kblk;
+  const int kb = (k0 + kblk < nref) ? kblk : nref - k0;
+  const size_t off = (size_t)b * kblk * kblk;
+  tfactor_body(kb, tau + k0, Gall + off, kblk, Tall + off, kblk);
+}
+
+// number of blocks of kBtBlockTc reflectors (n - 2 reflectors)
+static int tc_blocks(int n) { return n > 2 ? (n - 2 + kBtBlockTc - 1) / kBtBlockTc : 1; }
+
 size_t eig_work_bytes(int n) {
   size_t nn = (size_t)n * n;
   size_t doubles = nn /*A*/ + nn /*Vst*/ + 4 * (size_t)n /*d e e2 tau*/ + 2 * (size_t)n /*pbuf*/ +
-                   5 * nn /*lu*/ + 2 * (size_t)kBtBlockTc * kBtBlockTc + 2 * (size_t)kBtBlockTc * n + 16;
+                   5 * nn /*lu*/ + 2 * (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc + 2 * (size_t)kBtBlockTc * n +
+                   16;
   return doubles * sizeof(double) + 64 + (size_t)n * sizeof(int) + 256;
 }
 
@@ -508,8 +530,8 @@ void eig_work_bind(EigWork& w, void* base, int n) {
   w.tau = p; p += n;
   w.pbuf = p; p += 2 * (size_t)n;
   w.lu = p; p += 5 * nn;
-  w.Tm = p; p += (size_t)kBtBlockTc * kBtBlockTc;
-  w.Gm = p; p += (size_t)kBtBlockTc * kBtBlockTc;
+  w.Tm = p; p += (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc;   // T and Gram of every reflector block
+  w.Gm = p; p += (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc;
   w.Wt = p; p += (size_t)kBtBlockTc * n;
   w.Wt2 = p; p += (size_t)kBtBlockTc * n;
   w.scal = p; p += 16;
@@ -631,6 +653,8 @@ static void eig_backtransform_tc(cudaStream_t s, int n, double* Q, EigWork& w, c
   std::call_once(attr, [] {
     cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kBtBlockTc * kBtBlockTc * (int)sizeof(double));
+    cudaFuncSetAttribute(tfactor_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kBtBlockTc * kBtBlockTc * (int)sizeof(double));
   });
   const int nref = n - 2;
   const int nblk = (nref + kBtBlockTc - 1) / kBtBlockTc;
@@ -638,22 +662,35 @@ static void eig_backtransform_tc(cudaStream_t s, int n, double* Q, EigWork& w, c
   int* err = tc_error_flag(tw);
   double* Zt = w.A;                      // tridiagonalisation workspace is free now
   transpose_sq(s, n, Q, Zt);
+  // Gram matrices V_b V_b^T and T factors of all blocks first (one launch for the T's)
+  for (int b = 0; b < nblk; ++b) {
+    int k0 = b * kBtBlockTc, k1 = (k0 + kBtBlockTc < nref) ? k0 + kBtBlockTc : nref;
+    int kb = k1 - k0, c0 = k0 + 1, m = n - c0;
+    const double* Vb = w.Vst + (size_t)k0 * n + c0;
+    int ldm = tc_ld(m);
+    __nv_bfloat16* sV = tc_slot_base(tw, kSlotQ);
+    tc_split_rc(s, kb, m, Vb, n, 0, 4, tc_slot_exponents(tw, kSlotQ), sV, ldm, stride);
+    tc_gemm_rc(s, kb, kb, m, sV, ldm, stride, sV, ldm, stride, 10, 1.0,
+               w.Gm + (size_t)b * kBtBlockTc * kBtBlockTc, kBtBlockTc, 0, err);
+  }
+  if (nblk > 0) {
+    tfactor_all_kernel<<<nblk, kBtBlockTc, kBtBlockTc * kBtBlockTc * sizeof(double), s>>>(nref, kBtBlockTc,
+                                                                                          w.tau, w.Gm, w.Tm);
+    count_launch();
+  }
   for (int b = nblk - 1; b >= 0; --b) {
     int k0 = b * kBtBlockTc, k1 = (k0 + kBtBlockTc < nref) ? k0 + kBtBlockTc : nref;
     int kb = k1 - k0, c0 = k0 + 1, m = n - c0;
     const double* Vb = w.Vst + (size_t)k0 * n + c0;      // kb x m, ld n
+    const double* Tb = w.Tm + (size_t)b * kBtBlockTc * kBtBlockTc;
     double* Zs = Zt + c0;                                // n x m, ld n
     int ldm = tc_ld(m), ldk = tc_ld(kb);
     __nv_bfloat16* sV = tc_slot_base(tw, kSlotQ);
     tc_split_rc(s, kb, m, Vb, n, 0, 4, tc_slot_exponents(tw, kSlotQ), sV, ldm, stride);
-    tc_gemm_rc(s, kb, kb, m, sV, ldm, stride, sV, ldm, stride, 10, 1.0, w.Gm, kBtBlockTc, 0, err);
-    tfactor_kernel<<<1, kBtBlockTc, kb * kb * sizeof(double), s>>>(kb, w.tau + k0, w.Gm, kBtBlockTc, w.Tm,
-                                                                    kBtBlockTc);
-    count_launch();
     __nv_bfloat16* sZ = tc_slot_base(tw, kSlotT0);
     tc_split_rc(s, n, m, Zs, n, 0, 4, tc_slot_exponents(tw, kSlotT0), sZ, ldm, stride);
     tc_gemm_rc(s, n, kb, m, sZ, ldm, stride, sV, ldm, stride, 10, 1.0, w.Wt, kb, 0, err);      // U
-    dgemm(s, 0, 1, n, kb, kb, 1.0, w.Wt, kb, w.Tm, kBtBlockTc, 0.0, w.Wt2, kb);               // U2 = U T^T
+    dgemm(s, 0, 1, n, kb, kb, 1.0, w.Wt, kb, Tb, kBtBlockTc, 0.0, w.Wt2, kb);                 // U2 = U T^T
     __nv_bfloat16* sU = tc_slot_base(tw, kSlotT1);
     tc_split_rc(s, n, kb, w.Wt2, kb, 0, 4, tc_slot_exponents(tw, kSlotT1), sU, ldk, stride);
     __nv_bfloat16* sVt = tc_slot_base(tw, kSlotQt);
