@@ -292,8 +292,9 @@ __global__ void normalize_kernel(size_t len, double* __restrict__ v, const doubl
     if (blockIdx.x == 0 && threadIdx.x == 0) sc->active = 0;   // breakdown: invariant subspace
     return;
   }
+  const double rn = 1.0 / nv;             // one division per kernel, not per element
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < len) v[t] = v[t] / nv;
+  if (t < len) v[t] = v[t] * rn;
 }
 
 // k = number of existing vectors V_0..V_{k-1}; src -> v orthonormalised (CGS twice)
