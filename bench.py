@@ -37,6 +37,7 @@ WORKLOAD = dict(workload="840-atom random carbon packing, 2.2 g/cc, open box (se
                 param_table="synthetic NDDO seed 1", velocities="Maxwell-Boltzmann 300 K seed 2",
                 l2="working set > L2 (no flush needed)")
 METRIC = "atom-steps/s (KSA-XL-BOMD MD step)"
+KERNEL_MODE = [0]      # sim_kernel of the timed runs (--kernel)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk x 2 flop x max clock
 TRIDIAG_TRAFFIC_BYTES = 0.909e9 + 40.228e9       # dram read + write, one launch at n = 3360
 
@@ -130,7 +131,7 @@ def _create(kx, mol, V, table, precision, P0=None):
     cost does not depend on how far X(t0) is from self-consistency, and the
     residual reached is reported in the output line."""
     cfg = kx.sim_config_default(Te=WORKLOAD["Te_K"], dt=WORKLOAD["dt_fs"], m_max=6, m_min=6, precision=precision,
-                                scf_tol=1e-8, scf_max=30, scf_krylov=1, scf_accept=1)
+                                scf_tol=1e-8, scf_max=30, scf_krylov=1, scf_accept=1, kernel=KERNEL_MODE[0])
     return kx.sim_create(cfg, kx.param_table(table), mol.Z, mol.R, V=V, P0=P0)
 
 
@@ -213,7 +214,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+bf16-slices" if prec == kx.SIM_PREC_MIXED else "f64",
         "data": "synthetic (seeded generators; synthetic NDDO parameters)",
-        "config": dict(WORKLOAD, precision=args.precision, parallelism=f"replicas x{world}"),
+        "config": dict(WORKLOAD, precision=args.precision, kernel=args.kernel, parallelism=f"replicas x{world}"),
         "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
                        "per_step": [round(x, 3) for x in per_step]},
         "e2e": {"value": world * N / e2e_s, "unit": "atom-steps/s",
@@ -465,6 +466,49 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
+def run_drift(args):
+    """Energy conservation of the shadow dynamics (eq. 26) on six neutral C60
+    cages (360 atoms) at T_e = 5000 K, mixed precision, 200 steps of 0.5 fs:
+    adaptive-rank and fixed-rank Krylov kernels against the XL-BOMD kernel -cI."""
+    import collections
+    import synth
+    import paper_2303_00689_gb300 as kx
+    from paper_2303_00689_gb300 import build
+    build.build()
+    mol = synth.fullerene_c60(copies=6, bond=1.60)
+    table = kx.param_table(synth.table_to_array(synth.synthetic_table(1)))
+    V = synth.maxwell_boltzmann(mol.Z, 300.0, seed=5)
+    modes = [("krylov adaptive m 4-12, tol 1e-3", dict(m_max=12, m_min=4, krylov_tol=1e-3)),
+             ("krylov m 4", dict(m_max=4, m_min=4)),
+             ("xl -cI, c = 1", dict(kernel=kx.SIM_KERNEL_XL, xl_c=1.0)),
+             ("xl -cI, c = 0.9", dict(kernel=kx.SIM_KERNEL_XL, xl_c=0.9))]
+    nst = args.steps if args.steps > 10 else 200
+    runs = []
+    for name, kw in modes:
+        cfg = kx.sim_config_default(Te=5000.0, dt=0.5, precision=kx.SIM_PREC_MIXED, scf_tol=1e-7, scf_max=300,
+                                    scf_accept=1, **kw)
+        h = kx.sim_create(cfg, table, mol.Z, mol.R, V=V)
+        it, res = kx.sim_scf_info(h)
+        t = time.perf_counter()
+        recs = kx.sim_step(h, nst)
+        dt_s = time.perf_counter() - t
+        kx.sim_destroy(h)
+        E = np.array([r["E_tot"] for r in recs])
+        slope = np.polyfit(np.arange(len(E)) * 0.5e-3, E, 1)[0] / mol.natoms
+        runs.append({"kernel": name, "ms_per_step": 1e3 * dt_s / nst, "drift_eV_per_ps_atom": slope,
+                     "E_tot_std_eV": float(E.std()), "E_tot_ptp_eV": float(np.ptp(E)),
+                     "max_residual": max(r["res_norm"] for r in recs),
+                     "ranks": dict(sorted(collections.Counter(r["rank"] for r in recs).items())),
+                     "scf": {"iterations": it, "residual": res}})
+    out = {"metric": "energy drift (eV/ps/atom), shadow XL-BOMD", "value": runs[0]["drift_eV_per_ps_atom"],
+           "unit": "eV/ps/atom", "n_gpus": 1, "steps": nst, "warmup": 0,
+           "ms_per_step": runs[0]["ms_per_step"], "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64+bf16-slices", "data": "synthetic",
+           "config": {"workload": "6 C60 cages, 360 atoms, n = 1440, C-C 1.60 A", "Te_K": 5000.0, "dt_fs": 0.5},
+           "runs": runs}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -491,9 +535,11 @@ def main():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-timeout", type=float, default=600.0)
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
-    p.add_argument("--workload", choices=("md840", "batch", "serve"), default="md840",
+    p.add_argument("--workload", choices=("md840", "batch", "serve", "drift"), default="md840",
                    help="md840: the headline single-system step; batch: 128-molecule batch; serve: "
                         "Poisson-arrival serving")
+    p.add_argument("--kernel", choices=("krylov", "xl", "bomd"), default="krylov",
+                   help="kernel of eq. 25: Krylov (the method), XL-BOMD -cI or Born-Oppenheimer (comparison modes)")
     p.add_argument("--serve-requests", type=int, default=48)
     p.add_argument("--serve-nmax", type=int, default=600)
     p.add_argument("--serve-timeout", type=float, default=900.0)
@@ -510,12 +556,15 @@ def main():
         return
     if args.warmup < 3:
         args.warmup = 3
+    KERNEL_MODE[0] = {"krylov": 0, "xl": 1, "bomd": 2}[args.kernel]
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "drift":
+        run_drift(args)
     else:
         run_ours(args)
 

@@ -86,9 +86,14 @@ typedef struct sim_param_table {
 /* Kernel approximation in the electronic equation of motion (eq. 25). */
 enum sim_kernel {
   SIM_KERNEL_KRYLOV = 0,  /* low-rank Krylov subspace approximation, eqs. 31-35 */
-  SIM_KERNEL_XL = 1       /* original XL-BOMD scaled delta function K = -c I
+  SIM_KERNEL_XL = 1,      /* original XL-BOMD scaled delta function K = -c I
                              (Results, Langevin run of C240 2+); no response
                              calculations, rank reported as 0              */
+  SIM_KERNEL_BOMD = 2     /* comparison mode: Born-Oppenheimer MD, an SCF
+                             (scf_* settings) from the previous density at
+                             every step (Results: BOMD reusing the density);
+                             X(t) is the converged density, no X dynamics;
+                             host-synchronous (no graph capture)           */
 };
 
 /* ---- configuration ------------------------------------------------------ */

@@ -18,6 +18,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   no response calculation is made (Config.xl_c = c; None selects eq. 34).
   Pin: with every two-electron integral zero the Jacobian of D0 - X is -I, so
   the Krylov kernel at any rank equals the c = 1 kernel exactly.
+* comparison mode (Results, BOMD reusing the previous density): Config.bomd
+  re-converges the SCF (linear mixing from the previous density) at every
+  new geometry and takes forces at X = D_scf; there is no X dynamics.
 
 The damping constants (kappa, alpha, c_k for k_max = 6) are given in the
 paper's ref. 24 and not printed in the paper; the values below are that
@@ -41,9 +44,10 @@ CK = np.array([-14.0, 36.0, -27.0, -2.0, 12.0, -6.0, 1.0])
 
 class Config:
     def __init__(self, Te=1000.0, dt=0.5, m=4, m_min=None, tol=0.0,
-                 scf_tol=1e-10, scf_max=2000, mix=0.1, xl_c=None):
+                 scf_tol=1e-10, scf_max=2000, mix=0.1, xl_c=None, bomd=False):
         self.Te, self.dt, self.m = Te, dt, m
         self.xl_c = xl_c
+        self.bomd = bomd
         self.m_min = m if m_min is None else m_min
         self.tol, self.scf_tol, self.scf_max, self.mix = tol, scf_tol, scf_max, mix
 
@@ -148,8 +152,9 @@ class State:
         if X0 is None:
             X0, self.scf_iters = scf(sysm, self.R, cfg)
         self.X = [X0.copy() for _ in range(KMAX + 1)]
-        self.ev = evaluate(sysm, self.R, self.X[0], cfg)
+        self.ev = evaluate(sysm, self.R, self.X[0], cfg, krylov=not cfg.bomd)
         self.t = 0
+        self.scf_iters_last = 0
 
     @property
     def acc(self):
@@ -165,6 +170,13 @@ class State:
         dt = self.cfg.dt
         self.V = self.V + 0.5 * dt * self.acc
         self.R = self.R + dt * self.V
+        if self.cfg.bomd:
+            P, self.scf_iters_last = scf(self.sysm, self.R, self.cfg, P0=self.X[0])
+            self.X = [P] + self.X[:KMAX]
+            self.ev = evaluate(self.sysm, self.R, P, self.cfg, krylov=False)
+            self.V = self.V + 0.5 * dt * self.acc
+            self.t += 1
+            return self.ev
         Xn = 2.0 * self.X[0] - self.X[1] - KAPPA * self.ev["K"]
         Xn = Xn + ALPHA * sum(CK[k] * self.X[k] for k in range(KMAX + 1))
         self.X = [Xn] + self.X[:KMAX]

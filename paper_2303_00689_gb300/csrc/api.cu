@@ -304,18 +304,21 @@ static void krylov_kernel(sim_handle* h, const double* P) {
 }
 
 // Evaluate everything at (R, X(t)): pair blocks, F, D0, U, forces, Krylov kernel.
-static int evaluate(sim_handle* h, bool krylov = true) {
+static int evaluate(sim_handle* h, bool krylov = true, bool pairs_ready = false) {
   cudaStream_t s = h->stream;
   int n = h->n;
   size_t nn = (size_t)n * n;
   const double* X = xslot(h, 0);
   MolDev m = mol(h);
   PairDev pd = pairs(h);
-  phase_begin(h, PH_PAIRS);
-  launch_pair_derivs(s, h->npair, h->pA, h->pB, h->elem, h->R, h->tab, h->W, h->S, h->E, h->dW, h->dS, h->dE);
-  phase_end(h);
+  if (!pairs_ready) {
+    phase_begin(h, PH_PAIRS);
+    launch_pair_derivs(s, h->npair, h->pA, h->pB, h->elem, h->R, h->tab, h->W, h->S, h->E, h->dW, h->dS,
+                       h->dE);
+    phase_end(h);
+  }
   phase_begin(h, PH_FOCK);
-  launch_build_h(s, m, pd, h->tab, h->h);
+  if (!pairs_ready) launch_build_h(s, m, pd, h->tab, h->h);
   launch_pack_diag(s, m, X, h->Pd);
   launch_build_fock(s, m, pd, h->tab, X, h->Pd, h->h, h->Fock);
   phase_end(h);
@@ -373,7 +376,41 @@ static void reset_records(sim_handle* h) {
   h->rec_count = 0;
 }
 
+extern "C" {
+static int scf(sim_handle* h, int* iters, bool from_current);
+}
+
+// Born-Oppenheimer step (comparison mode, Results: BOMD reusing the previous
+// density): Verlet with forces at the SCF ground state of each geometry.
+static int bomd_step(sim_handle* h) {
+  cudaStream_t s = h->stream;
+  double dt = h->cfg.dt;
+  phase_begin(h, PH_UPDATE);
+  launch_half_kick(s, h->N, h->V, h->F, h->mass, dt);     // eq. 27
+  launch_drift(s, h->N, h->R, h->V, dt);                  // eq. 28
+  phase_end(h);
+  phase_begin(h, PH_PAIRS);
+  launch_pair_derivs(s, h->npair, h->pA, h->pB, h->elem, h->R, h->tab, h->W, h->S, h->E, h->dW, h->dS, h->dE);
+  launch_build_h(s, mol(h), pairs(h), h->tab, h->h);
+  phase_end(h);
+  int it = 0;
+  int rc = scf(h, &it, true);                             // from the previous density
+  if (rc) return rc;
+  rc = evaluate(h, false, true);                          // forces and energy at X = D_scf
+  if (rc) return rc;
+  phase_begin(h, PH_KRY_BLAS);
+  launch_krylov_start(s, (size_t)h->n * h->n, h->D, xslot(h, 0), h->W0, h->sc, h->red);   // ||D0 - X||
+  phase_end(h);
+  phase_begin(h, PH_UPDATE);
+  launch_half_kick(s, h->N, h->V, h->F, h->mass, dt);     // eq. 30
+  launch_kinetic(s, h->N, h->V, h->mass, h->sc);
+  record(h);
+  phase_end(h);
+  return SIM_OK;
+}
+
 static int one_step(sim_handle* h) {
+  if (h->cfg.kernel == SIM_KERNEL_BOMD) return bomd_step(h);
   cudaStream_t s = h->stream;
   size_t nn = (size_t)h->n * h->n;
   double dt = h->cfg.dt;
@@ -574,7 +611,9 @@ void* sim_stream(sim_handle* h) { return h ? (void*)h->stream : nullptr; }
 // P <- mix P + (1 - mix) D[P], or, with scf_krylov != 0, the low-rank Krylov
 // (Newton-like) update P <- P - K (D[P] - P) built from the same DMPT
 // responses as the MD kernel.  Stops when max|D[P] - P| < scf_tol.
-static int scf(sim_handle* h, int* iters) {
+// from_current: start from X(t) (BOMD reusing the previous density) instead of
+// the diagonal guess.
+static int scf(sim_handle* h, int* iters, bool from_current = false) {
   cudaStream_t s = h->stream;
   int n = h->n;
   size_t nn = (size_t)n * n;
@@ -584,16 +623,18 @@ static int scf(sim_handle* h, int* iters) {
   double* Dn = h->D;
   double* err_d = h->coef + 48;
   const bool trace = getenv("KSAXL_SCF_TRACE") != nullptr;
-  // diagonal guess: valence electrons spread over each atom's orbitals, trace N_occ
-  std::vector<double> P0(nn, 0.0);
-  double tr = 0.0;
-  for (int A = 0; A < h->N; ++A) {
-    int o = h->off_h[A], no = h->off_h[A + 1] - o;
-    double v = 0.5 * h->tab.e[h->elem_h[A]].zcore / no;
-    for (int k = 0; k < no; ++k) { P0[(size_t)(o + k) * n + o + k] = v; tr += v; }
+  if (!from_current) {
+    // diagonal guess: valence electrons spread over each atom's orbitals, trace N_occ
+    std::vector<double> P0(nn, 0.0);
+    double tr = 0.0;
+    for (int A = 0; A < h->N; ++A) {
+      int o = h->off_h[A], no = h->off_h[A + 1] - o;
+      double v = 0.5 * h->tab.e[h->elem_h[A]].zcore / no;
+      for (int k = 0; k < no; ++k) { P0[(size_t)(o + k) * n + o + k] = v; tr += v; }
+    }
+    for (int i = 0; i < n; ++i) P0[(size_t)i * n + i] *= h->nocc / tr;
+    CUDA_TRY(cudaMemcpyAsync(P, P0.data(), nn * sizeof(double), cudaMemcpyHostToDevice, s));
   }
-  for (int i = 0; i < n; ++i) P0[(size_t)i * n + i] *= h->nocc / tr;
-  CUDA_TRY(cudaMemcpyAsync(P, P0.data(), nn * sizeof(double), cudaMemcpyHostToDevice, s));
   double mix = h->cfg.scf_mix;
   double best = 1e300;
   double err = 0.0;
@@ -648,7 +689,8 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
   *out = nullptr;
   if (!(cfg->Te > 0.0) || !(cfg->dt > 0.0) || cfg->m_max < 1 || cfg->m_max > 16 || cfg->m_min < 1 ||
       cfg->m_min > cfg->m_max || cfg->scf_max < 1 || !(cfg->scf_mix >= 0.0 && cfg->scf_mix < 1.0) ||
-      (cfg->kernel != SIM_KERNEL_KRYLOV && cfg->kernel != SIM_KERNEL_XL) || !std::isfinite(cfg->xl_c))
+      (cfg->kernel != SIM_KERNEL_KRYLOV && cfg->kernel != SIM_KERNEL_XL && cfg->kernel != SIM_KERNEL_BOMD) ||
+      !std::isfinite(cfg->xl_c))
     return fail(SIM_EINVAL, "invalid configuration");
   if (cfg->precision != SIM_PREC_FP64 && cfg->precision != SIM_PREC_MIXED)
     return fail(SIM_EINVAL, "unknown precision mode");
@@ -762,7 +804,7 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
     }
     for (int k = 1; k < 7; ++k)
       cudaMemcpyAsync(xslot(h, k), xslot(h, 0), nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    rc = evaluate(h);
+    rc = evaluate(h, cfg->kernel != SIM_KERNEL_BOMD);
     if (rc) break;
     launch_kinetic(s, h->N, h->V, h->mass, h->sc);
     reset_records(h);
@@ -870,6 +912,8 @@ size_t sim_estimate_bytes(const sim_config* cfg, int natoms, const int* Z) {
 
 int sim_enable_graphs(sim_handle* h, int enable) {
   if (!h) return fail(SIM_EINVAL, "null handle");
+  if (enable && h->cfg.kernel == SIM_KERNEL_BOMD)
+    return fail(SIM_EINVAL, "Born-Oppenheimer steps read the SCF residual on the host and cannot be captured");
   if (enable && !h->graphs) {
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     int rc = capture_graphs(h);

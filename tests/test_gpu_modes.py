@@ -128,3 +128,31 @@ def test_krylov_scf_matches_oracle(m):
         assert max_abs(kx.sim_get_matrix(h, kx.SIM_MAT_X), D_ref) < 1e-9
     finally:
         kx.sim_destroy(h)
+
+
+def test_bomd_steps_match_oracle():
+    """Born-Oppenheimer comparison mode (SCF from the previous density at every
+    step): three FP64 steps of C4H6 against the oracle's BOMD steps."""
+    mol = synth.c4h6(1)
+    sysm = oracle_system(mol)
+    V = synth.maxwell_boltzmann(mol.Z, 300.0, seed=1)
+    cfg = dyn.Config(Te=1000.0, dt=0.5, scf_tol=1e-10, bomd=True)
+    st = dyn.State(sysm, mol.R, V, cfg)
+    E = []
+    for _ in range(3):
+        st.step()
+        E.append(st.total_energy())
+    h = create(mol, dict(Te=1000.0, dt=0.5, scf_tol=1e-10, kernel=kx.SIM_KERNEL_BOMD), V=V)
+    try:
+        recs = kx.sim_step(h, 3)
+        R, Vg, F, D = kx.sim_get_state(h, sysm.N)
+        assert max_abs(R, st.R) < 1e-10
+        assert max_abs(Vg, st.V) < 1e-9
+        assert max_abs(F, st.ev["forces"]) < F_TOL
+        assert max_abs(D, st.ev["D"]) < D_TOL
+        assert max_abs([r["E_tot"] for r in recs], E) < 1e-7
+        assert all(r["rank"] == 0 and r["res_norm"] < 1e-8 for r in recs)
+        with pytest.raises(kx.SimError):
+            kx.sim_enable_graphs(h)
+    finally:
+        kx.sim_destroy(h)

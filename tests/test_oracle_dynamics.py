@@ -97,3 +97,27 @@ def test_krylov_scf_reaches_the_linear_mixing_fixed_point():
     assert np.abs(D_kry - D_lin).max() < 1e-9
     assert it_kry < it_lin / 2
     assert hist[-1] < 1e-10
+
+
+def test_bomd_steps_conserve_the_born_oppenheimer_energy():
+    """Born-Oppenheimer comparison mode: forces at the SCF ground state of each
+    geometry.  E_kin + U is conserved to the Verlet error, which scales as dt^2
+    (forces consistent with U_BO), and U at X = D_scf equals the ground-state
+    energy evaluated from scratch at the final geometry."""
+    mol = synth.c4h6(1)
+    R0 = np.loadtxt(os.path.join(GOLDEN, "c4h6_seed1_relaxed.txt"))
+    sysm = ham.System(mol.Z, TAB)
+    V0 = synth.maxwell_boltzmann(mol.Z, 300.0, seed=1)
+    stds = []
+    for dt in (0.25, 0.125):
+        cfg = dyn.Config(Te=1000.0, dt=dt, scf_tol=1e-11, bomd=True)
+        st = dyn.State(sysm, R0, V0, cfg)
+        E = [st.total_energy()]
+        for _ in range(int(15.0 / dt)):
+            st.step()
+            E.append(st.total_energy())
+        stds.append(np.std(E))
+    assert 3.0 < stds[0] / stds[1] < 5.5
+    D, _ = dyn.scf(sysm, st.R, dyn.Config(Te=1000.0, scf_tol=1e-11))
+    fresh = dyn.evaluate(sysm, st.R, D, cfg, krylov=False)
+    assert abs(fresh["U"] - st.ev["U"]) < 1e-8
