@@ -305,6 +305,17 @@ int sim_get_state(sim_handle* h, double* R, double* V, double* F, double* D0);
  *   Xhist: 7 x n x n, Xhist[k] = X(t - k dt), k = 0..6 (eq. 29 history) */
 int sim_set_state(sim_handle* h, const double* R, const double* V, const double* Xhist);
 
+/* sim_save -- write the handle's dynamical state to a file: configuration,
+ * raw parameter table, atoms, charge, R, V and the X history X(t - k dt),
+ * k = 0..6 (everything eq. 29 and eqs. 27-30 carry from step to step).
+ * sim_load -- create a handle on `device` (launching on `stream`, or a private
+ * one for NULL) from such a file; it re-evaluates F, D0, forces and the kernel
+ * at (R, X(t)) with the same kernels, so stepping a loaded handle reproduces
+ * the saved trajectory bitwise.  Errors: SIM_EINVAL (unreadable, truncated or
+ * foreign file), SIM_EINTERNAL (write failure), and those of sim_create. */
+int sim_save(sim_handle* h, const char* path);
+int sim_load(const char* path, int device, void* stream, sim_handle** out);
+
 /* Matrices of the last evaluation, copied into an n x n caller buffer. */
 enum sim_matrix {
   SIM_MAT_X = 0,       /* X(t)                                              */

@@ -29,7 +29,7 @@ EXPORTED = (
     "sim_launch_count", "sim_stream", "sim_destroy", "sim_last_error", "sim_debug_tc_gemm",
     "sim_tc_gemm_noalloc", "sim_records", "sim_wait", "sim_enable_graphs", "sim_batch_step",
     "sim_estimate_bytes", "sim_server_create", "sim_submit", "sim_poll", "sim_server_stats_get",
-    "sim_server_drain", "sim_server_destroy",
+    "sim_server_drain", "sim_server_destroy", "sim_save", "sim_load",
 )
 
 
@@ -126,6 +126,8 @@ def lib():
         L.sim_tc_gemm_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                           C.c_void_p]
         L.sim_records.argtypes = [C.c_void_p, P(sim_step_result), C.c_int]
+        L.sim_save.argtypes = [C.c_void_p, C.c_char_p]
+        L.sim_load.argtypes = [C.c_char_p, C.c_int, C.c_void_p, P(C.c_void_p)]
         L.sim_wait.argtypes = [C.c_void_p]
         L.sim_enable_graphs.argtypes = [C.c_void_p, C.c_int]
         L.sim_batch_step.argtypes = [P(C.c_void_p), C.c_int, C.c_int]
@@ -316,6 +318,16 @@ def sim_records(h, count):
     out = (sim_step_result * max(1, count))()
     _check(lib().sim_records(h, out, int(count)))
     return [{f: getattr(r, f) for f, _ in sim_step_result._fields_} for r in out[:count]]
+
+
+def sim_save(h, path):
+    _check(lib().sim_save(h, os.fsencode(path)))
+
+
+def sim_load(path, device=0, stream=None):
+    h = C.c_void_p()
+    _check(lib().sim_load(os.fsencode(path), int(device), C.c_void_p(stream or 0), C.byref(h)))
+    return h
 
 
 def sim_wait(h):

@@ -57,6 +57,9 @@ struct sim_handle {
   int N = 0, n = 0, npair = 0, nocc = 0, mmax = 0;
   double beta = 0.0;
   std::vector<int> elem_h, off_h;
+  std::vector<int> Z_h;           // atomic numbers and raw inputs, kept for sim_save
+  sim_param_table table_raw{};
+  int charge = 0;
   std::vector<double> mass_h;
   // device memory (one arena)
   void* arena = nullptr;
@@ -698,6 +701,9 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
     return fail(SIM_EINVAL, "mixed precision needs the tensor-map driver entry point (tcgen05/TMA path)");
   sim_handle* h = new sim_handle();
   h->cfg = *cfg;
+  h->table_raw = *table;
+  h->Z_h.assign(Z, Z + natoms);
+  h->charge = charge;
   for (int e = 0; e < 4; ++e)
     if (build_elem(table->v[e], h->tab.e[e]) != 0) {
       delete h;
@@ -984,12 +990,88 @@ int sim_set_state(sim_handle* h, const double* R, const double* V, const double*
   if (Xhist)
     for (int k = 0; k < 7; ++k)
       CUDA_TRY(cudaMemcpyAsync(xslot(h, k), Xhist + k * nn, nn * sizeof(double), cudaMemcpyHostToDevice, s));
-  int rc = evaluate(h);
+  int rc = evaluate(h, h->cfg.kernel != SIM_KERNEL_BOMD);
   if (rc) return rc;
   launch_kinetic(s, h->N, h->V, h->mass, h->sc);
   reset_records(h);
   record(h);
   return check_status(h);
+}
+
+// ---- checkpoint / resume ----------------------------------------------------
+static const char kCkptMagic[8] = {'K', 'S', 'A', 'X', 'L', 'C', 'K', '1'};
+
+int sim_save(sim_handle* h, const char* path) {
+  if (!h || !path) return fail(SIM_EINVAL, "null argument");
+  size_t nn = (size_t)h->n * h->n;
+  std::vector<double> R(3 * (size_t)h->N), V(3 * (size_t)h->N), X(7 * nn);
+  cudaStream_t s = h->stream;
+  CUDA_TRY(cudaMemcpyAsync(R.data(), h->R, R.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(V.data(), h->V, V.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  for (int k = 0; k < 7; ++k)
+    CUDA_TRY(cudaMemcpyAsync(X.data() + k * nn, xslot(h, k), nn * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(SIM_EINVAL, std::string("cannot open ") + path + " for writing");
+  sim_config cfg = h->cfg;
+  cfg.stream = nullptr;
+  int head[4] = {1 /*version*/, h->N, h->n, h->charge};
+  bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(head, sizeof(int), 4, f) == 4 &&
+            std::fwrite(&cfg, sizeof(cfg), 1, f) == 1 && std::fwrite(&h->table_raw, sizeof(sim_param_table), 1, f) == 1 &&
+            std::fwrite(h->Z_h.data(), sizeof(int), h->N, f) == (size_t)h->N &&
+            std::fwrite(R.data(), sizeof(double), R.size(), f) == R.size() &&
+            std::fwrite(V.data(), sizeof(double), V.size(), f) == V.size() &&
+            std::fwrite(X.data(), sizeof(double), X.size(), f) == X.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? SIM_OK : fail(SIM_EINTERNAL, std::string("short write to ") + path);
+}
+
+int sim_load(const char* path, int device, void* stream, sim_handle** out) {
+  if (!path || !out) return fail(SIM_EINVAL, "null argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(SIM_EINVAL, std::string("cannot open ") + path);
+  char magic[8];
+  int head[4];
+  sim_config cfg;
+  sim_param_table table;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+            std::fread(head, sizeof(int), 4, f) == 4 && head[0] == 1 && head[1] >= 1 && head[1] <= 1000000 &&
+            head[2] >= 1 && head[2] <= 4 * head[1] && std::fread(&cfg, sizeof(cfg), 1, f) == 1 &&
+            std::fread(&table, sizeof(table), 1, f) == 1;
+  std::vector<int> Z;
+  std::vector<double> R, V, X;
+  if (ok) {
+    const int N = head[1];
+    const size_t nn = (size_t)head[2] * head[2];
+    Z.resize(N);
+    R.resize(3 * (size_t)N);
+    V.resize(3 * (size_t)N);
+    X.resize(7 * nn);
+    ok = std::fread(Z.data(), sizeof(int), N, f) == (size_t)N && std::fread(R.data(), sizeof(double), R.size(), f) == R.size() &&
+         std::fread(V.data(), sizeof(double), V.size(), f) == V.size() &&
+         std::fread(X.data(), sizeof(double), X.size(), f) == X.size() && std::fgetc(f) == EOF;
+  }
+  std::fclose(f);
+  if (!ok) return fail(SIM_EINVAL, std::string(path) + " is not a complete checkpoint of this library");
+  cfg.device = device;
+  cfg.stream = stream;
+  sim_handle* h = nullptr;
+  int rc = sim_create(&cfg, &table, head[1], Z.data(), R.data(), V.data(), head[3], X.data(), &h);
+  if (rc) return rc;
+  if (h->n != head[2]) {
+    sim_destroy(h);
+    return fail(SIM_EINVAL, "checkpoint basis size does not match its atoms");
+  }
+  rc = sim_set_state(h, nullptr, nullptr, X.data());   // full X history, re-evaluated
+  if (rc) {
+    std::string msg = t_err;
+    sim_destroy(h);
+    t_err = msg;
+    return rc;
+  }
+  *out = h;
+  return SIM_OK;
 }
 
 int sim_get_matrix(sim_handle* h, int which, double* out) {

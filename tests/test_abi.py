@@ -47,3 +47,14 @@ def test_binding_names_match_header():
 def test_config_defaults_without_gpu(library):
     cfg = kx.sim_config_default()
     assert cfg.Te == 1000.0 and cfg.dt == 0.5 and cfg.m_max == 4 and cfg.scf_mix == 0.1
+
+
+def test_load_rejects_files_that_are_not_checkpoints(tmp_path):
+    """sim_load validates the whole file before touching a device."""
+    import paper_2303_00689_gb300 as kx
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"not a checkpoint at all")
+    for path in (bad, tmp_path / "missing.ckpt"):
+        with pytest.raises(kx.SimError) as e:
+            kx.sim_load(str(path))
+        assert e.value.code == kx.SIM_EINVAL
