@@ -70,17 +70,22 @@ void launch_fermi(cudaStream_t s, int n, const double* eps, double nocc, double 
   count_launch();
 }
 
+// Qs = Q diag(f^1/2); each thread owns one column and 64 rows, so the square
+// root is taken once per column tile rather than once per element
+constexpr int kScaleRows = 64;
 __global__ void scale_columns_kernel(int n, const double* __restrict__ Q, const double* __restrict__ f,
                                      double* __restrict__ Qs) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)n * n) return;
-  int j = (int)(t % n);
-  Qs[t] = Q[t] * ::sqrt(fmax(f[j], 0.0));
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double sq = ::sqrt(fmax(f[j], 0.0));
+  const int r0 = blockIdx.y * kScaleRows;
+  const int r1 = (r0 + kScaleRows < n) ? r0 + kScaleRows : n;
+  for (int r = r0; r < r1; ++r) Qs[(size_t)r * n + j] = Q[(size_t)r * n + j] * sq;
 }
 
 void launch_scale_columns(cudaStream_t s, int n, const double* Q, const double* f, double* Qs) {
-  size_t tot = (size_t)n * n;
-  scale_columns_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, Q, f, Qs);
+  dim3 grid((n + 255) / 256, (n + kScaleRows - 1) / kScaleRows);
+  scale_columns_kernel<<<grid, 256, 0, s>>>(n, Q, f, Qs);
   count_launch();
 }
 
@@ -283,18 +288,23 @@ __global__ void sub_combo_kernel(size_t len, int k, PtrList V, const double* __r
   v[t] = x;
 }
 
-__global__ void normalize_kernel(size_t len, double* __restrict__ v, const double* __restrict__ nrm,
-                                 Scalars* sc) {
-  // nrm[0] = ||v||^2, nrm[1] = ||src||^2
+// scale[0] = 1 / ||v|| from nrm[0] = ||v||^2, nrm[1] = ||src||^2; breakdown
+// (invariant subspace) when orthogonalisation left < 1e-10 of the norm
+__global__ void norm_scale_kernel(const double* __restrict__ nrm, Scalars* sc, double* __restrict__ scale) {
   if (!sc->active) return;
   double nv = ::sqrt(nrm[0]), ns = ::sqrt(nrm[1]);
   if (nv < 1e-10 * ns || nv == 0.0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->active = 0;   // breakdown: invariant subspace
+    sc->active = 0;
     return;
   }
-  const double rn = 1.0 / nv;             // one division per kernel, not per element
+  scale[0] = 1.0 / nv;
+}
+
+__global__ void normalize_kernel(size_t len, double* __restrict__ v, const double* __restrict__ scale,
+                                 const Scalars* sc) {
+  if (!sc->active) return;
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < len) v[t] = v[t] * rn;
+  if (t < len) v[t] = v[t] * scale[0];
 }
 
 // k = number of existing vectors V_0..V_{k-1}; src -> v orthonormalised (CGS twice)
@@ -317,7 +327,9 @@ void launch_krylov_orth(cudaStream_t s, size_t len, int k, double* const* Vs, co
   }
   const double* a2[2] = {v, src};
   dots(s, len, 2, a2, a2, coef + 16, partial, &sc->active);
-  normalize_kernel<<<nb, 256, 0, s>>>(len, v, coef + 16, sc);
+  norm_scale_kernel<<<1, 1, 0, s>>>(coef + 16, sc, coef + 18);
+  count_launch();
+  normalize_kernel<<<nb, 256, 0, s>>>(len, v, coef + 18, sc);
   count_launch();
 }
 

@@ -11,7 +11,7 @@
 //     2 Tr[h D] + Tr[(2D - P) G(P)] + V_nn at fixed D, P contracted with the
 //     stored dW, dS, dE blocks; F_A += g, F_B -= g with g = dE/dd, d = R_B - R_A.
 //
-// Diagonal blocks are gathered per atom by one warp (deterministic order, no
+// Diagonal blocks are gathered per atom by one block (deterministic order, no
 // atomics); off-diagonal blocks are written by one thread per pair into the
 // upper triangle and mirrored by a tiled transpose.
 #include "common.cuh"
@@ -58,13 +58,18 @@ __global__ void pack_diag_kernel(int N, int n, const int* __restrict__ off, cons
 // Gather over partners of atom A: acc[P] = sum_B sum_q wq(B, q) W_AB[P][q]
 // where wq = scale * mult(q) * dens_B[q] (Coulomb) or -Z'_B for q = ss (h).
 // mode 0: Coulomb with packed densities; mode 1: electron-core attraction.
+// One block of kDiagThreads per atom: threads stride over the partners, then a
+// fixed-order reduction (warp shuffles, then warps in order) leaves the sums in
+// thread 0.
+constexpr int kDiagThreads = 256;
+
 __device__ void gather_diag(int A, const MolDev& m, const PairDev& pd, const ElemTable& tab,
                             const double* __restrict__ dens, int mode, double acc[10]) {
-  int lane = threadIdx.x & 31;
+  __shared__ double part[kDiagThreads / 32][10];
   for (int P = 0; P < 10; ++P) acc[P] = 0.0;
   int N = m.N;
   size_t np = (size_t)m.npair;
-  for (int B = lane; B < N; B += 32) {
+  for (int B = threadIdx.x; B < N; B += blockDim.x) {
     if (B == A) continue;
     int first = (A < B);
     int pi = first ? pair_index(A, B, N) : pair_index(B, A, N);
@@ -87,15 +92,26 @@ __device__ void gather_diag(int A, const MolDev& m, const PairDev& pd, const Ele
       }
     }
   }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int P = 0; P < 10; ++P) acc[P] = warp_sum(acc[P]);
+  if (lane == 0)
+    for (int P = 0; P < 10; ++P) part[warp][P] = acc[P];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int P = 0; P < 10; ++P) {
+      double t = part[0][P];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t += part[w][P];
+      acc[P] = t;
+    }
 }
 
-__global__ void h_diag_kernel(MolDev m, PairDev pd, ElemTable tab, double* __restrict__ h) {
-  int A = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void __launch_bounds__(kDiagThreads) h_diag_kernel(MolDev m, PairDev pd, ElemTable tab,
+                                                              double* __restrict__ h) {
+  int A = blockIdx.x;
   if (A >= m.N) return;
   double acc[10];
   gather_diag(A, m, pd, tab, nullptr, 1, acc);
-  if ((threadIdx.x & 31) != 0) return;
+  if (threadIdx.x != 0) return;
   const Elem& e = tab.e[m.elem[A]];
   int o = m.off[A], no = m.off[A + 1] - o;
   for (int mu = 0; mu < no; ++mu)
@@ -122,15 +138,16 @@ __global__ void h_offdiag_kernel(MolDev m, PairDev pd, ElemTable tab, double* __
     }
 }
 
-__global__ void fock_diag_kernel(MolDev m, PairDev pd, ElemTable tab, const double* __restrict__ P,
-                                 const double* __restrict__ Pd, const double* __restrict__ h,
-                                 double* __restrict__ out, const int* gate) {
+__global__ void __launch_bounds__(kDiagThreads)
+    fock_diag_kernel(MolDev m, PairDev pd, ElemTable tab, const double* __restrict__ P,
+                     const double* __restrict__ Pd, const double* __restrict__ h, double* __restrict__ out,
+                     const int* gate) {
   if (gate && *gate == 0) return;
-  int A = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int A = blockIdx.x;
   if (A >= m.N) return;
   double acc[10];
   gather_diag(A, m, pd, tab, Pd, 0, acc);
-  if ((threadIdx.x & 31) != 0) return;
+  if (threadIdx.x != 0) return;
   const Elem& e = tab.e[m.elem[A]];
   int o = m.off[A], no = m.off[A + 1] - o;
   const double* pa = Pd + (size_t)A * 10;
@@ -286,7 +303,7 @@ static void mirror(cudaStream_t s, int n, double* a, const int* gate) {
 
 void launch_build_h(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,
                     double* h) {
-  h_diag_kernel<<<blocks_for((long long)m.N * 32, 128), 128, 0, s>>>(m, pd, tab, h);
+  h_diag_kernel<<<m.N, kDiagThreads, 0, s>>>(m, pd, tab, h);
   count_launch();
   if (m.npair > 0) {
     h_offdiag_kernel<<<blocks_for(m.npair, 128), 128, 0, s>>>(m, pd, tab, h);
@@ -296,7 +313,7 @@ void launch_build_h(cudaStream_t s, const MolDev& m, const PairDev& pd, const El
 
 void launch_build_fock(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,
                        const double* P, const double* Pd, const double* h, double* out, const int* gate) {
-  fock_diag_kernel<<<blocks_for((long long)m.N * 32, 128), 128, 0, s>>>(m, pd, tab, P, Pd, h, out, gate);
+  fock_diag_kernel<<<m.N, kDiagThreads, 0, s>>>(m, pd, tab, P, Pd, h, out, gate);
   count_launch();
   if (m.npair > 0) {
     fock_offdiag_kernel<<<blocks_for(m.npair, 128), 128, 0, s>>>(m, pd, tab, P, h, out, gate);
