@@ -88,9 +88,8 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
                                                               double* __restrict__ pbuf,
                                                               unsigned* bar, int* status) {
   extern __shared__ double sm[];
-  // previous reflector v and previous w interleaved (one 16-byte shared load
-  // per element in the update loop), valid for indices >= k
-  double2* vw = reinterpret_cast<double2*>(sm);
+  double* vp = sm;           // previous reflector (valid for indices >= k)
+  double* wp = sm + n;       // previous w
   double* vc = sm + 2 * n;   // current reflector
   double* red = sm + 3 * n;  // 32 doubles of reduction scratch
   __shared__ double s_par[4];  // beta, tau, scale, d_k
@@ -107,7 +106,7 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
     double loc = 0.0;
     for (int j = k + 2 + tid; j < n; j += blockDim.x) {
       double x = A[(size_t)k * n + j];
-      if (prev) x -= vw[k].x * vw[j].y + vw[k].y * vw[j].x;
+      if (prev) x -= vp[k] * wp[j] + wp[k] * vp[j];
       vc[j] = x;
       loc += x * x;
     }
@@ -116,8 +115,8 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
       double xk = A[(size_t)k * n + k];
       double x1 = A[(size_t)k * n + k + 1];
       if (prev) {
-        xk -= 2.0 * vw[k].x * vw[k].y;
-        x1 -= vw[k].x * vw[k + 1].y + vw[k].y * vw[k + 1].x;
+        xk -= 2.0 * vp[k] * wp[k];
+        x1 -= vp[k] * wp[k + 1] + wp[k] * vp[k + 1];
       }
       double beta, t, scale;
       if (sigma == 0.0) {
@@ -146,15 +145,13 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
       double* row = A + (size_t)i * n;
       double acc = 0.0, acc2 = 0.0, acc3 = 0.0, acc4 = 0.0;   // four chains hide the FP64 latency
       if (prev) {
-        const double2 qi = vw[i];
-        const double vi = qi.x, wi = qi.y;
+        const double vi = vp[i], wi = wp[i];
         int j = k + 1 + lane;
         for (; j + 96 < n; j += 128) {
-          const double2 q0 = vw[j], q1 = vw[j + 32], q2 = vw[j + 64], q3 = vw[j + 96];
-          double a = fma(-vi, q0.y, fma(-wi, q0.x, row[j]));
-          double b = fma(-vi, q1.y, fma(-wi, q1.x, row[j + 32]));
-          double c = fma(-vi, q2.y, fma(-wi, q2.x, row[j + 64]));
-          double e = fma(-vi, q3.y, fma(-wi, q3.x, row[j + 96]));
+          double a = fma(-vi, wp[j], fma(-wi, vp[j], row[j]));
+          double b = fma(-vi, wp[j + 32], fma(-wi, vp[j + 32], row[j + 32]));
+          double c = fma(-vi, wp[j + 64], fma(-wi, vp[j + 64], row[j + 64]));
+          double e = fma(-vi, wp[j + 96], fma(-wi, vp[j + 96], row[j + 96]));
           row[j] = a;
           row[j + 32] = b;
           row[j + 64] = c;
@@ -165,8 +162,7 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
           acc4 = fma(e, vc[j + 96], acc4);
         }
         for (; j < n; j += 32) {
-          const double2 q = vw[j];
-          double a = fma(-vi, q.y, fma(-wi, q.x, row[j]));
+          double a = fma(-vi, wp[j], fma(-wi, vp[j], row[j]));
           row[j] = a;
           acc = fma(a, vc[j], acc);
         }
@@ -187,7 +183,8 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
     for (int j = k + 1 + tid; j < n; j += blockDim.x) loc += pb[j] * vc[j];
     double pv = block_sum(loc, red);
     for (int j = k + 1 + tid; j < n; j += blockDim.x) {
-      vw[j] = make_double2(vc[j], pb[j] - 0.5 * t * pv * vc[j]);
+      wp[j] = pb[j] - 0.5 * t * pv * vc[j];
+      vp[j] = vc[j];
     }
     prev = true;
     __syncthreads();
@@ -199,9 +196,9 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
       int a = n - 2, b = n - 1;
       double a00 = A[(size_t)a * n + a], a10 = A[(size_t)b * n + a], a11 = A[(size_t)b * n + b];
       if (prev) {
-        a00 -= 2.0 * vw[a].x * vw[a].y;
-        a10 -= vw[b].x * vw[a].y + vw[b].y * vw[a].x;
-        a11 -= 2.0 * vw[b].x * vw[b].y;
+        a00 -= 2.0 * vp[a] * wp[a];
+        a10 -= vp[b] * wp[a] + wp[b] * vp[a];
+        a11 -= 2.0 * vp[b] * wp[b];
       }
       d[a] = a00; d[b] = a11; e[a] = a10;
     }
