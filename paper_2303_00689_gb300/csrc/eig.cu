@@ -296,7 +296,7 @@ __device__ __forceinline__ int sturm_count_f32(int n, const float* __restrict__ 
 // count(lo) <= i < count(hi)), then FP64 bisection to full accuracy.
 __global__ void bisect_kernel(int n, const double* __restrict__ d, const double* __restrict__ e2,
                               const double* __restrict__ scal, const float* __restrict__ df,
-                              const float* __restrict__ e2f, double* __restrict__ ev) {
+                              const float* __restrict__ e2f, double rel_tol, double* __restrict__ ev) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double glo = scal[0], ghi = scal[1], pivmin = scal[3];
@@ -319,9 +319,10 @@ __global__ void bisect_kernel(int n, const double* __restrict__ d, const double*
     if (!ok_lo) lo = fmax(glo, lo - w);
     if (!ok_hi) hi = fmin(ghi, hi + w);
   }
-  // 1e-12 of the spectral range is far below what the occupations and the DMPT
-  // weights resolve, and inverse iteration converges from such a shift in two steps
-  const double tol = fmax(2.0 * kEps * fmax(fabs(lo), fabs(hi)), 1e-12 * fmax(1.0, scal[2])) + pivmin;
+  // rel_tol of the spectral range (1e-12 on the FP64 path, 1e-9 on the mixed
+  // path) is far below what the occupations and the DMPT weights resolve, and
+  // inverse iteration converges from such a shift in two steps
+  const double tol = fmax(2.0 * kEps * fmax(fabs(lo), fabs(hi)), rel_tol * fmax(1.0, scal[2])) + pivmin;
   for (int it = 0; it < 200; ++it) {
     double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;
@@ -601,7 +602,7 @@ int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* 
   return 0;
 }
 
-void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w) {
+void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w, double rel_tol) {
   if (n <= 0) return;
   // 2. eigenvalues
   // pbuf (2n doubles, free after the tridiagonalisation) holds the FP32 copies
@@ -609,7 +610,7 @@ void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w) {
   float* e2f = df + n;
   gersh_kernel<<<1, 1024, 0, s>>>(n, w.d, w.e, w.e2, w.scal, df, e2f);
   count_launch();
-  bisect_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e2, w.scal, df, e2f, eps);   // spread over all SMs
+  bisect_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e2, w.scal, df, e2f, rel_tol, eps);   // spread over all SMs
   count_launch();
 }
 
