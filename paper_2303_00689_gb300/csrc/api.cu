@@ -261,7 +261,7 @@ static int eig(sim_handle* h) {
   phase_end(h);
   if (st != 0) return fail(SIM_EINTERNAL, "tridiagonalisation launch failed (code " + std::to_string(st) + ")");
   phase_begin(h, PH_BISECT);
-  eig_bisect(h->stream, h->n, h->eps, h->ew, mixed(h) ? 1e-9 : 1e-12);
+  eig_bisect(h->stream, h->n, h->eps, h->ew, 1e-12);
   phase_end(h);
   phase_begin(h, PH_TRIEIG);
   eig_vectors(h->stream, h->n, h->eps, h->Q, h->ew);

@@ -319,9 +319,11 @@ __global__ void bisect_kernel(int n, const double* __restrict__ d, const double*
     if (!ok_lo) lo = fmax(glo, lo - w);
     if (!ok_hi) hi = fmin(ghi, hi + w);
   }
-  // rel_tol of the spectral range (1e-12 on the FP64 path, 1e-9 on the mixed
-  // path) is far below what the occupations and the DMPT weights resolve, and
-  // inverse iteration converges from such a shift in two steps
+  // rel_tol (1e-12) of the spectral range is far below what the occupations and
+  // the DMPT weights resolve, and inverse iteration converges from such a shift
+  // in two steps.  A looser shift costs orthogonality: after two steps the
+  // component along a neighbour at distance g is ~(shift error / g)^2, which at
+  // 1e-9 of the range left Q^T Q - I at 5e-7 for n = 3360.
   const double tol = fmax(2.0 * kEps * fmax(fabs(lo), fabs(hi)), rel_tol * fmax(1.0, scal[2])) + pivmin;
   for (int it = 0; it < 200; ++it) {
     double mid = 0.5 * (lo + hi);
