@@ -96,7 +96,7 @@ def test_c4h6_one_step_teacher_forced(c4h6):
 
 
 def test_c4h6_scf_and_20_step_trajectory(c4h6):
-    """Config 1: GPU SCF start and 20 FP64 steps against the oracle trajectory."""
+    """C4H6 (22 orbitals): GPU SCF start and 20 FP64 steps against the oracle trajectory."""
     mol, sysm, cfg, Dmin = c4h6
     V = synth.maxwell_boltzmann(mol.Z, 300.0, seed=1)
     h = create(mol, dict(Te=1000.0, dt=0.5, m_max=4, m_min=4), V=V)
