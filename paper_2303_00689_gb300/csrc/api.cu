@@ -240,7 +240,7 @@ static void dmpt(sim_handle* h, const double* F1, double* D1) {
     tc_split(s, h->tw, kSlotT1, h->T1, 3, 0, g);
     tc_gemm(s, h->tw, kSlotT1, kSlotQt, 6, 1.0, h->T2, 1, g);      // T2 = (Q^T F1) Q
     launch_dmu(s, n, h->T2, h->eps, h->f, h->beta, h->sc);
-    launch_dmpt_y(s, n, h->T2, h->eps, h->f, h->beta, h->sc, h->Y);
+    launch_dmpt_y(s, n, h->T2, h->K, h->sc, h->Y);     // h->K holds Lambda until the final combine
     tc_split(s, h->tw, kSlotT0, h->Y, 3, 0, g);
     tc_gemm(s, h->tw, kSlotQ, kSlotT0, 6, 1.0, h->T1, 0, g);       // T1 = Q Y
     tc_split(s, h->tw, kSlotT1, h->T1, 3, 0, g);
@@ -250,7 +250,7 @@ static void dmpt(sim_handle* h, const double* F1, double* D1) {
   dgemm(s, 0, 0, n, n, n, 1.0, F1, n, h->Q, n, 0.0, h->T1, n, 0, g);         // T1 = F1 Q
   dgemm(s, 1, 0, n, n, n, 1.0, h->Q, n, h->T1, n, 0.0, h->T2, n, 1, g);      // T2 = Q^T T1
   launch_dmu(s, n, h->T2, h->eps, h->f, h->beta, h->sc);
-  launch_dmpt_y(s, n, h->T2, h->eps, h->f, h->beta, h->sc, h->Y);
+  launch_dmpt_y(s, n, h->T2, h->K, h->sc, h->Y);       // h->K holds Lambda until the final combine
   dgemm(s, 0, 0, n, n, n, 1.0, h->Q, n, h->Y, n, 0.0, h->T1, n, 0, g);       // T1 = Q Y
   dgemm(s, 0, 1, n, n, n, 1.0, h->T1, n, h->Q, n, 0.0, D1, n, 1, g);         // D1 = T1 Q^T
 }
@@ -280,6 +280,10 @@ static void krylov_kernel(sim_handle* h, const double* P) {
   PairDev pd = pairs(h);
   phase_begin(h, PH_KRY_GEMM);
   dmpt_prepare(h);
+  phase_end(h);
+  phase_begin(h, PH_KRY_BLAS);
+  // Lambda of eq. 36 once per evaluation; K is free until launch_krylov_combine writes it
+  launch_lambda(s, h->n, h->eps, h->f, h->beta, h->sc, h->K);
   phase_end(h);
   phase_begin(h, PH_KRY_BLAS);
   launch_krylov_start(s, nn, h->D, P, h->W0, h->sc, h->red);

@@ -142,22 +142,37 @@ void launch_dmu(cudaStream_t s, int n, const double* F1p, const double* eps, con
   count_launch();
 }
 
-__global__ void dmpt_y_kernel(int n, const double* __restrict__ F1p, const double* __restrict__ eps,
-                              const double* __restrict__ f, double beta, const Scalars* sc,
-                              double* __restrict__ Y) {
-  if (!sc->active) return;
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)n * n) return;
-  int i = (int)(t / n), j = (int)(t % n);
-  double v = F1p[t];
-  if (i == j) v -= sc->dmu;
-  Y[t] = lambda_ij(eps[i], eps[j], f[i], f[j], sc->mu, beta) * v;
+// Lambda_ij of eq. 36 for the current eigenpairs (the same for every Krylov
+// vector of one evaluation); one row of tiles per blockIdx.y
+__global__ void lambda_kernel(int n, const double* __restrict__ eps, const double* __restrict__ f, double beta,
+                              const Scalars* sc, double* __restrict__ Lam) {
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  Lam[(size_t)i * n + j] = lambda_ij(eps[i], eps[j], f[i], f[j], sc->mu, beta);
 }
 
-void launch_dmpt_y(cudaStream_t s, int n, const double* F1p, const double* eps, const double* f,
-                   double beta, const Scalars* sc, double* Y) {
-  size_t tot = (size_t)n * n;
-  dmpt_y_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, F1p, eps, f, beta, sc, Y);
+void launch_lambda(cudaStream_t s, int n, const double* eps, const double* f, double beta, const Scalars* sc,
+                   double* Lam) {
+  lambda_kernel<<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, eps, f, beta, sc, Lam);
+  count_launch();
+}
+
+// Y = Lambda o (F1' - dmu I)
+__global__ void dmpt_y_kernel(int n, const double* __restrict__ F1p, const double* __restrict__ Lam,
+                              const Scalars* sc, double* __restrict__ Y) {
+  if (!sc->active) return;
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const size_t t = (size_t)i * n + j;
+  double v = F1p[t];
+  if (i == j) v -= sc->dmu;
+  Y[t] = Lam[t] * v;
+}
+
+void launch_dmpt_y(cudaStream_t s, int n, const double* F1p, const double* Lam, const Scalars* sc, double* Y) {
+  dmpt_y_kernel<<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, F1p, Lam, sc, Y);
   count_launch();
 }
 

@@ -91,8 +91,11 @@ void launch_scale_columns(cudaStream_t s, int n, const double* Q, const double* 
 void launch_transpose(cudaStream_t s, int n, const double* A, double* At);
 void launch_dmu(cudaStream_t s, int n, const double* F1p, const double* eps, const double* f,
                 double beta, Scalars* sc);
-void launch_dmpt_y(cudaStream_t s, int n, const double* F1p, const double* eps, const double* f,
-                   double beta, const Scalars* sc, double* Y);
+// Lambda_ij of eq. 36 for the current eigenpairs and mu (n x n), then
+// Y = Lambda o (F1' - dmu I) per Krylov vector
+void launch_lambda(cudaStream_t s, int n, const double* eps, const double* f, double beta, const Scalars* sc,
+                   double* Lam);
+void launch_dmpt_y(cudaStream_t s, int n, const double* F1p, const double* Lam, const Scalars* sc, double* Y);
 // U = 2 Tr[h D] + Tr[(2D - X)(F - h)] and V_nn = sum E_pair
 void launch_energy(cudaStream_t s, int n, int npair, const double* h, const double* D,
                    const double* X, const double* F, const double* E, Scalars* sc, double* partial);
