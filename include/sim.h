@@ -121,12 +121,22 @@ typedef struct sim_config {
                          (eq. 25) used by sim_step                           */
   double xl_c;        /* SIM_KERNEL_XL only: K = -xl_c I (Results, C240 2+
                          run: c = 1 originally, 0.9 tuned); any finite value */
+  double langevin_gamma; /* Langevin friction, 1/fs (Results: Langevin runs at
+                         300 K); 0 = NVE.  Scheme (not printed in the paper):
+                         Ornstein-Uhlenbeck half steps around the Verlet step
+                         (OBABO), V <- c V + sqrt((1 - c^2) k_B T / M) xi,
+                         c = exp(-gamma dt / 2)                              */
+  double langevin_T;  /* thermostat temperature, K                           */
+  unsigned long long langevin_seed; /* key of the Philox4x32-10 stream; xi of
+                         component 3A + k at half step p of MD step s uses
+                         counter (3A + k, p, s low, s high)                  */
 } sim_config;
 
 /* Fills a config with the defaults used by the paper-shaped workloads:
  * Te 1000 K, dt 0.5 fs, m = 4, fixed rank, FP64, scf_tol 1e-10,
  * scf_max 5000, mix 0.1, linear mixing, device 0, private stream,
- * Krylov kernel (xl_c = 1).
+ * Krylov kernel (xl_c = 1), no thermostat (langevin_gamma = 0, T 300 K,
+ * seed 0).
  * The SCF prints max|D[P] - P| per iteration to stderr when the
  * environment variable KSAXL_SCF_TRACE is set. */
 void sim_config_default(sim_config* cfg);

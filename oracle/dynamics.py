@@ -18,6 +18,10 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   no response calculation is made (Config.xl_c = c; None selects eq. 34).
   Pin: with every two-electron integral zero the Jacobian of D0 - X is -I, so
   the Krylov kernel at any rank equals the c = 1 kernel exactly.
+* Langevin thermostat (Results: Langevin runs at 300 K; the scheme and the
+  friction are not printed): reading, the Ornstein-Uhlenbeck half steps of the
+  OBABO splitting around the Verlet step, V <- c V + sqrt((1 - c^2) k_B T / M) xi
+  with c = exp(-gamma dt / 2), xi from the counter-based generator of rng.py.
 * comparison mode (Results, BOMD reusing the previous density): Config.bomd
   re-converges the SCF (linear mixing from the previous density) at every
   new geometry and takes forces at X = D_scf; there is no X dynamics.
@@ -33,6 +37,7 @@ import numpy as np
 
 from . import hamiltonian as ham
 from . import electronic as el
+from . import rng
 
 KB = el.KB
 ACC = 9.648533212e-3          # Angstrom/fs^2 per (eV/Angstrom)/amu
@@ -44,10 +49,12 @@ CK = np.array([-14.0, 36.0, -27.0, -2.0, 12.0, -6.0, 1.0])
 
 class Config:
     def __init__(self, Te=1000.0, dt=0.5, m=4, m_min=None, tol=0.0,
-                 scf_tol=1e-10, scf_max=2000, mix=0.1, xl_c=None, bomd=False):
+                 scf_tol=1e-10, scf_max=2000, mix=0.1, xl_c=None, bomd=False,
+                 langevin_T=300.0, gamma=0.0, seed=0):
         self.Te, self.dt, self.m = Te, dt, m
         self.xl_c = xl_c
         self.bomd = bomd
+        self.langevin_T, self.gamma, self.seed = langevin_T, gamma, seed
         self.m_min = m if m_min is None else m_min
         self.tol, self.scf_tol, self.scf_max, self.mix = tol, scf_tol, scf_max, mix
 
@@ -166,7 +173,26 @@ class State:
     def total_energy(self):
         return self.kinetic() + self.ev["U"]
 
+    def thermostat(self, phase):
+        """Ornstein-Uhlenbeck half step (Langevin, OBABO splitting)."""
+        cfg = self.cfg
+        c = np.exp(-0.5 * cfg.gamma * cfg.dt)
+        sigma = np.sqrt((1.0 - c * c) * KB * cfg.langevin_T * ACC / self.sysm.mass)
+        xi = rng.normals(3 * self.sysm.N, phase, self.t, cfg.seed).reshape(-1, 3)
+        self.V = c * self.V + sigma[:, None] * xi
+
     def step(self):
+        if self.cfg.gamma > 0.0:
+            self.thermostat(0)
+            ev = self._verlet_step()
+            self.thermostat(1)
+            self.t += 1
+            return ev
+        ev = self._verlet_step()
+        self.t += 1
+        return ev
+
+    def _verlet_step(self):
         dt = self.cfg.dt
         self.V = self.V + 0.5 * dt * self.acc
         self.R = self.R + dt * self.V
@@ -175,14 +201,12 @@ class State:
             self.X = [P] + self.X[:KMAX]
             self.ev = evaluate(self.sysm, self.R, P, self.cfg, krylov=False)
             self.V = self.V + 0.5 * dt * self.acc
-            self.t += 1
             return self.ev
         Xn = 2.0 * self.X[0] - self.X[1] - KAPPA * self.ev["K"]
         Xn = Xn + ALPHA * sum(CK[k] * self.X[k] for k in range(KMAX + 1))
         self.X = [Xn] + self.X[:KMAX]
         self.ev = evaluate(self.sysm, self.R, self.X[0], self.cfg)
         self.V = self.V + 0.5 * dt * self.acc
-        self.t += 1
         return self.ev
 
 

@@ -44,7 +44,8 @@ class sim_config(C.Structure):
                 ("krylov_tol", C.c_double), ("precision", C.c_int), ("scf_tol", C.c_double),
                 ("scf_max", C.c_int), ("scf_mix", C.c_double), ("device", C.c_int),
                 ("stream", C.c_void_p), ("scf_krylov", C.c_int), ("scf_accept", C.c_int),
-                ("kernel", C.c_int), ("xl_c", C.c_double)]
+                ("kernel", C.c_int), ("xl_c", C.c_double), ("langevin_gamma", C.c_double),
+                ("langevin_T", C.c_double), ("langevin_seed", C.c_ulonglong)]
 
 
 class sim_param_table(C.Structure):

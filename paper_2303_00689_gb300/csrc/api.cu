@@ -387,12 +387,23 @@ extern "C" {
 static int scf(sim_handle* h, int* iters, bool from_current);
 }
 
+static bool langevin(const sim_handle* h) { return h->cfg.langevin_gamma > 0.0; }
+
+// Langevin Ornstein-Uhlenbeck half step (phase 0 before the first half-kick,
+// phase 1 after the second); nothing when the thermostat is off
+static void thermostat_half(sim_handle* h, int phase) {
+  if (!langevin(h)) return;
+  launch_langevin_half(h->stream, h->N, h->V, h->mass, h->cfg.langevin_gamma, h->cfg.dt, h->cfg.langevin_T,
+                       h->cfg.langevin_seed, phase, h->sc);
+}
+
 // Born-Oppenheimer step (comparison mode, Results: BOMD reusing the previous
 // density): Verlet with forces at the SCF ground state of each geometry.
 static int bomd_step(sim_handle* h) {
   cudaStream_t s = h->stream;
   double dt = h->cfg.dt;
   phase_begin(h, PH_UPDATE);
+  thermostat_half(h, 0);
   launch_half_kick(s, h->N, h->V, h->F, h->mass, dt);     // eq. 27
   launch_drift(s, h->N, h->R, h->V, dt);                  // eq. 28
   phase_end(h);
@@ -410,6 +421,8 @@ static int bomd_step(sim_handle* h) {
   phase_end(h);
   phase_begin(h, PH_UPDATE);
   launch_half_kick(s, h->N, h->V, h->F, h->mass, dt);     // eq. 30
+  thermostat_half(h, 1);
+  if (langevin(h)) launch_step_advance(s, h->sc);
   launch_kinetic(s, h->N, h->V, h->mass, h->sc);
   record(h);
   phase_end(h);
@@ -422,6 +435,7 @@ static int one_step(sim_handle* h) {
   size_t nn = (size_t)h->n * h->n;
   double dt = h->cfg.dt;
   phase_begin(h, PH_UPDATE);
+  thermostat_half(h, 0);
   launch_half_kick(s, h->N, h->V, h->F, h->mass, dt);     // eq. 27
   launch_drift(s, h->N, h->R, h->V, dt);                  // eq. 28
   double* Xh[7];
@@ -434,6 +448,8 @@ static int one_step(sim_handle* h) {
   if (rc) return rc;
   phase_begin(h, PH_UPDATE);
   launch_half_kick(s, h->N, h->V, h->F, h->mass, dt);     // eq. 30
+  thermostat_half(h, 1);
+  if (langevin(h)) launch_step_advance(s, h->sc);
   launch_kinetic(s, h->N, h->V, h->mass, h->sc);
   record(h);
   phase_end(h);
@@ -598,6 +614,9 @@ void sim_config_default(sim_config* c) {
   c->scf_krylov = 0;
   c->kernel = SIM_KERNEL_KRYLOV;
   c->xl_c = 1.0;
+  c->langevin_gamma = 0.0;
+  c->langevin_T = 300.0;
+  c->langevin_seed = 0;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -697,7 +716,8 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
   if (!(cfg->Te > 0.0) || !(cfg->dt > 0.0) || cfg->m_max < 1 || cfg->m_max > 16 || cfg->m_min < 1 ||
       cfg->m_min > cfg->m_max || cfg->scf_max < 1 || !(cfg->scf_mix >= 0.0 && cfg->scf_mix < 1.0) ||
       (cfg->kernel != SIM_KERNEL_KRYLOV && cfg->kernel != SIM_KERNEL_XL && cfg->kernel != SIM_KERNEL_BOMD) ||
-      !std::isfinite(cfg->xl_c))
+      !std::isfinite(cfg->xl_c) || !(cfg->langevin_gamma >= 0.0) || !std::isfinite(cfg->langevin_gamma) ||
+      !(cfg->langevin_T >= 0.0) || !std::isfinite(cfg->langevin_T))
     return fail(SIM_EINVAL, "invalid configuration");
   if (cfg->precision != SIM_PREC_FP64 && cfg->precision != SIM_PREC_MIXED)
     return fail(SIM_EINVAL, "unknown precision mode");
@@ -1019,9 +1039,12 @@ int sim_save(sim_handle* h, const char* path) {
   if (!f) return fail(SIM_EINVAL, std::string("cannot open ") + path + " for writing");
   sim_config cfg = h->cfg;
   cfg.stream = nullptr;
-  int head[4] = {1 /*version*/, h->N, h->n, h->charge};
+  unsigned long long step = 0;
+  CUDA_TRY(cudaMemcpy(&step, &h->sc->step, sizeof(step), cudaMemcpyDeviceToHost));
+  int head[4] = {2 /*version*/, h->N, h->n, h->charge};
   bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(head, sizeof(int), 4, f) == 4 &&
             std::fwrite(&cfg, sizeof(cfg), 1, f) == 1 && std::fwrite(&h->table_raw, sizeof(sim_param_table), 1, f) == 1 &&
+            std::fwrite(&step, sizeof(step), 1, f) == 1 &&
             std::fwrite(h->Z_h.data(), sizeof(int), h->N, f) == (size_t)h->N &&
             std::fwrite(R.data(), sizeof(double), R.size(), f) == R.size() &&
             std::fwrite(V.data(), sizeof(double), V.size(), f) == V.size() &&
@@ -1040,11 +1063,13 @@ int sim_load(const char* path, int device, void* stream, sim_handle** out) {
   sim_config cfg;
   sim_param_table table;
   bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
-            std::fread(head, sizeof(int), 4, f) == 4 && head[0] == 1 && head[1] >= 1 && head[1] <= 1000000 &&
+            std::fread(head, sizeof(int), 4, f) == 4 && head[0] == 2 && head[1] >= 1 && head[1] <= 1000000 &&
             head[2] >= 1 && head[2] <= 4 * head[1] && std::fread(&cfg, sizeof(cfg), 1, f) == 1 &&
             std::fread(&table, sizeof(table), 1, f) == 1;
   std::vector<int> Z;
   std::vector<double> R, V, X;
+  unsigned long long step = 0;
+  if (ok) ok = std::fread(&step, sizeof(step), 1, f) == 1;
   if (ok) {
     const int N = head[1];
     const size_t nn = (size_t)head[2] * head[2];
@@ -1068,6 +1093,8 @@ int sim_load(const char* path, int device, void* stream, sim_handle** out) {
     return fail(SIM_EINVAL, "checkpoint basis size does not match its atoms");
   }
   rc = sim_set_state(h, nullptr, nullptr, X.data());   // full X history, re-evaluated
+  if (rc == SIM_OK && cudaMemcpy(&h->sc->step, &step, sizeof(step), cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = fail(SIM_EINTERNAL, "restoring the step counter failed");
   if (rc) {
     std::string msg = t_err;
     sim_destroy(h);

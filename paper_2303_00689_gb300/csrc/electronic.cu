@@ -516,6 +516,48 @@ void launch_x_update(cudaStream_t s, size_t len, double* const* Xh, const double
   count_launch();
 }
 
+// ---- Langevin thermostat ----------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC 2011): ten rounds of 32x32 -> 64-bit products with the
+// multipliers 0xD2511F53, 0xCD9E8D57; the key is bumped by 0x9E3779B9, 0xBB67AE85 per round.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+__global__ void langevin_half_kernel(int N, double* __restrict__ V, const double* __restrict__ mass, double c,
+                                     double kT, unsigned long long seed, int phase, const Scalars* sc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * N) return;
+  const unsigned long long step = sc->step;
+  uint32_t ctr[4] = {(uint32_t)t, (uint32_t)phase, (uint32_t)(step & 0xFFFFFFFFull), (uint32_t)(step >> 32)};
+  philox4x32_10(ctr, (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
+  const double u1 = ((double)ctr[0] + 0.5) * (1.0 / 4294967296.0);
+  const double u2 = ((double)ctr[1] + 0.5) * (1.0 / 4294967296.0);
+  const double xi = ::sqrt(-2.0 * ::log(u1)) * ::cos(2.0 * 3.141592653589793 * u2);   // Box-Muller
+  const double sigma = ::sqrt((1.0 - c * c) * kT * kAccel / mass[t / 3]);
+  V[t] = c * V[t] + sigma * xi;
+}
+
+void launch_langevin_half(cudaStream_t s, int N, double* V, const double* mass, double gamma, double dt,
+                          double T, unsigned long long seed, int phase, const Scalars* sc) {
+  const double c = ::exp(-0.5 * gamma * dt);
+  langevin_half_kernel<<<(3 * N + 127) / 128, 128, 0, s>>>(N, V, mass, c, kBoltz * T, seed, phase, sc);
+  count_launch();
+}
+
+__global__ void step_advance_kernel(Scalars* sc) { sc->step += 1; }
+
+void launch_step_advance(cudaStream_t s, Scalars* sc) {
+  step_advance_kernel<<<1, 1, 0, s>>>(sc);
+  count_launch();
+}
+
 // ---- nuclei (eqs. 27, 28, 30) ---------------------------------------------------------------
 __global__ void half_kick_kernel(int N, double* __restrict__ V, const double* __restrict__ F,
                                  const double* __restrict__ mass, double dt) {

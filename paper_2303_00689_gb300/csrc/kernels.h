@@ -84,6 +84,7 @@ struct Scalars {         // device-resident per-evaluation scalars
   double e_elec, vnn, e_kin, res2, fit;
   double O[16 * 16], b[16], c[16], w0n2;
   int rank, active, status, pad;
+  unsigned long long step;   // MD steps taken (counter of the thermostat's random numbers)
 };
 void launch_fermi(cudaStream_t s, int n, const double* eps, double nocc, double beta, double* f,
                   Scalars* sc);
@@ -124,6 +125,11 @@ void launch_half_kick(cudaStream_t s, int N, double* V, const double* F, const d
                       double dt);
 void launch_drift(cudaStream_t s, int N, double* R, const double* V, double dt);
 void launch_kinetic(cudaStream_t s, int N, const double* V, const double* mass, Scalars* sc);
+// Langevin (OBABO) Ornstein-Uhlenbeck half step V <- c V + sqrt((1 - c^2) k_B T / M) xi with
+// c = exp(-gamma dt / 2); xi from Philox4x32-10, counter (3A + k, phase, step), key seed
+void launch_langevin_half(cudaStream_t s, int N, double* V, const double* mass, double gamma, double dt,
+                          double T, unsigned long long seed, int phase, const Scalars* sc);
+void launch_step_advance(cudaStream_t s, Scalars* sc);
 void launch_check_finite(cudaStream_t s, size_t len, const double* a, Scalars* sc);
 void launch_fill(cudaStream_t s, size_t len, double* a, double v);
 void launch_axpby(cudaStream_t s, size_t len, double a, const double* x, double b, const double* y,

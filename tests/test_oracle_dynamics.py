@@ -121,3 +121,44 @@ def test_bomd_steps_conserve_the_born_oppenheimer_energy():
     D, _ = dyn.scf(sysm, st.R, dyn.Config(Te=1000.0, scf_tol=1e-11))
     fresh = dyn.evaluate(sysm, st.R, D, cfg, krylov=False)
     assert abs(fresh["U"] - st.ev["U"]) < 1e-8
+
+
+def test_philox_known_answers():
+    """Philox4x32-10 against the known-answer vectors published with the generator."""
+    from oracle import rng
+    cases = [((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+             ((0xFFFFFFFF,) * 4, (0xFFFFFFFF, 0xFFFFFFFF), (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+             ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+              (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1))]
+    for ctr, key, want in cases:
+        out = rng.philox4x32_10([[c] for c in ctr], key)
+        assert tuple(int(o[0]) for o in out) == want
+
+
+def test_langevin_half_steps_keep_the_maxwell_boltzmann_distribution():
+    """The Ornstein-Uhlenbeck half step is exact for free particles: applied
+    repeatedly it drives any velocities to <v^2> = k_B T ACC / M per component,
+    and its normals are standard (mean 0, variance 1)."""
+    from oracle import rng
+    xi = rng.normals(200000, 0, 7, 12345)
+    assert abs(xi.mean()) < 0.01 and abs(xi.var() - 1.0) < 0.01
+    mol = synth.c4h6(1)
+    sysm = ham.System(mol.Z, TAB)
+
+    class Free(dyn.State):
+        def __init__(self):
+            self.sysm, self.cfg = sysm, dyn.Config(dt=0.5, langevin_T=500.0, gamma=0.5, seed=3)
+            self.V = np.zeros((sysm.N, 3))
+            self.t = 0
+
+    st = Free()
+    acc = np.zeros((sysm.N, 3))
+    for t in range(4000):
+        st.t = t
+        st.thermostat(t % 2)
+        if t >= 1000:
+            acc += st.V ** 2
+    v2 = acc / 3000
+    # equipartition: sum M <v^2> / ACC = 3 N k_B T (about 1 % statistical error here)
+    ratio = np.sum(sysm.mass[:, None] * v2) / dyn.ACC / (3 * sysm.N * dyn.KB * 500.0)
+    assert abs(ratio - 1.0) < 0.05
