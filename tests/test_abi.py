@@ -58,3 +58,22 @@ def test_load_rejects_files_that_are_not_checkpoints(tmp_path):
         with pytest.raises(kx.SimError) as e:
             kx.sim_load(str(path))
         assert e.value.code == kx.SIM_EINVAL
+
+
+def test_memory_estimate_is_host_arithmetic():
+    """sim_estimate_bytes (used by the server's HBM-budget admission) needs no
+    device: it grows with the basis, the mixed path adds its BF16 slice slots,
+    and invalid input gives 0."""
+    import numpy as np
+    import paper_2303_00689_gb300 as kx
+    small = np.array([6, 6, 1, 1], dtype=np.int32)
+    big = np.array([6] * 40 + [1] * 20, dtype=np.int32)
+    c64 = kx.sim_config_default(m_max=4, m_min=4)
+    cmx = kx.sim_config_default(m_max=4, m_min=4, precision=kx.SIM_PREC_MIXED)
+    assert 0 < kx.sim_estimate_bytes(c64, small) < kx.sim_estimate_bytes(c64, big)
+    assert kx.sim_estimate_bytes(cmx, big) > kx.sim_estimate_bytes(c64, big)
+    n = 40 * 4 + 20
+    # at least the ~30 n x n FP64 matrices of the layout
+    assert kx.sim_estimate_bytes(c64, big) > 30 * n * n * 8
+    bad = kx.sim_config_default(m_max=0)
+    assert kx.sim_estimate_bytes(bad, big) == 0
