@@ -155,7 +155,8 @@ void admission_loop(sim_server* s, int slot) {
     int rc = sim_create(&c, &j->req.table, j->req.natoms, j->Z.data(), j->R.data(),
                         j->has_V ? j->V.data() : nullptr, j->req.charge, nullptr, &j->h);
     mark(s, slot, A_GRAPHS, j->ticket);
-    if (rc == SIM_OK && s->cfg.use_graphs) rc = sim_enable_graphs(j->h, 1);
+    // Born-Oppenheimer steps read the SCF residual on the host: they run without graphs
+    if (rc == SIM_OK && s->cfg.use_graphs && c.kernel != SIM_KERNEL_BOMD) rc = sim_enable_graphs(j->h, 1);
     mark(s, slot, A_EVENTS, j->ticket);
     for (int k = 0; rc == SIM_OK && k < kInFlight; ++k)
       if (cudaEventCreateWithFlags(&j->ev[k], cudaEventDisableTiming) != cudaSuccess) rc = SIM_EINTERNAL;
