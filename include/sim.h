@@ -241,8 +241,9 @@ size_t sim_estimate_bytes(const sim_config* cfg, int natoms, const int* Z);
  * the persistent eigensolver grids of all live trajectories fit on the
  * device at once (their grid barriers need every block resident),
  * and a stepping thread that keeps one step in flight per live trajectory
- * (each on its own stream, through CUDA graphs when use_graphs != 0) and
- * retires a trajectory when its steps are done.  Every trajectory computes
+ * (each on its own stream, through CUDA graphs when use_graphs != 0, except
+ * for Born-Oppenheimer trajectories) and retires a trajectory when its steps
+ * are done.  Every trajectory computes
  * exactly what sim_create + sim_step compute for it alone: no data is shared
  * between trajectories, so results do not depend on the rest of the mix. */
 typedef struct sim_server sim_server;
