@@ -231,6 +231,22 @@ int sim_enable_graphs(sim_handle* h, int enable);
  * error.  Records of the steps are read with sim_records. */
 int sim_batch_step(sim_handle* const* handles, int count, int nsteps);
 
+/* sim_batch_create -- capture one MD step of every handle into one CUDA graph
+ * (one graph per phase of the X ring): each molecule's step is a branch forked
+ * from and joined to a private stream, and groups of molecules whose persistent
+ * eigensolver grids fit on the device together run one after the other inside
+ * the graph.  The handles must be distinct, on distinct streams, have taken the
+ * same number of steps, and not use SIM_KERNEL_BOMD or phase profiling; they
+ * stay owned by the caller and must outlive the batch.
+ * sim_batch_run -- nsteps steps of the whole batch, one graph launch per step;
+ * synchronous; results are bitwise those of stepping each handle alone; the
+ * records are read per handle with sim_records.  Stepping a member on its own
+ * between runs is rejected (SIM_EINVAL). */
+typedef struct sim_batch sim_batch;
+int sim_batch_create(sim_handle* const* handles, int count, sim_batch** out);
+int sim_batch_run(sim_batch* b, int nsteps);
+void sim_batch_destroy(sim_batch* b);
+
 /* Bytes of device memory sim_create allocates for this molecule/config. */
 size_t sim_estimate_bytes(const sim_config* cfg, int natoms, const int* Z);
 

@@ -29,7 +29,8 @@ EXPORTED = (
     "sim_launch_count", "sim_stream", "sim_destroy", "sim_last_error", "sim_debug_tc_gemm",
     "sim_tc_gemm_noalloc", "sim_records", "sim_wait", "sim_enable_graphs", "sim_batch_step",
     "sim_estimate_bytes", "sim_server_create", "sim_submit", "sim_poll", "sim_server_stats_get",
-    "sim_server_drain", "sim_server_destroy", "sim_save", "sim_load",
+    "sim_server_drain", "sim_server_destroy", "sim_save", "sim_load", "sim_batch_create", "sim_batch_run",
+    "sim_batch_destroy",
 )
 
 
@@ -128,6 +129,10 @@ def lib():
                                           C.c_void_p]
         L.sim_records.argtypes = [C.c_void_p, P(sim_step_result), C.c_int]
         L.sim_save.argtypes = [C.c_void_p, C.c_char_p]
+        L.sim_batch_create.argtypes = [P(C.c_void_p), C.c_int, P(C.c_void_p)]
+        L.sim_batch_run.argtypes = [C.c_void_p, C.c_int]
+        L.sim_batch_destroy.argtypes = [C.c_void_p]
+        L.sim_batch_destroy.restype = None
         L.sim_load.argtypes = [C.c_char_p, C.c_int, C.c_void_p, P(C.c_void_p)]
         L.sim_wait.argtypes = [C.c_void_p]
         L.sim_enable_graphs.argtypes = [C.c_void_p, C.c_int]
@@ -342,6 +347,22 @@ def sim_enable_graphs(h, enable=True):
 def sim_batch_step(handles, nsteps):
     arr = (C.c_void_p * max(1, len(handles)))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
     _check(lib().sim_batch_step(arr, len(handles), int(nsteps)))
+
+
+def sim_batch_create(handles):
+    arr = (C.c_void_p * max(1, len(handles)))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    b = C.c_void_p()
+    _check(lib().sim_batch_create(arr, len(handles), C.byref(b)))
+    return b
+
+
+def sim_batch_run(b, nsteps):
+    _check(lib().sim_batch_run(b, int(nsteps)))
+
+
+def sim_batch_destroy(b):
+    if b:
+        lib().sim_batch_destroy(b)
 
 
 def sim_estimate_bytes(cfg, Z):

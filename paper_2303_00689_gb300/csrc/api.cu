@@ -958,6 +958,150 @@ int sim_enable_graphs(sim_handle* h, int enable) {
   return SIM_OK;
 }
 
+// ---- whole-batch graphs -----------------------------------------------------
+// One CUDA graph per phase of the X ring holds one MD step of every molecule of
+// the batch: each molecule's step is a branch forked from and joined back to a
+// master stream, and groups of molecules whose persistent eigensolver grids fit
+// on the device together follow one another inside the graph.
+struct sim_batch {
+  std::vector<sim_handle*> hs;
+  std::vector<int> group_end;            // exclusive end index of each group
+  cudaStream_t master = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t gexec[8] = {};
+  long long gnodes[8] = {};
+};
+
+static void batch_release(sim_batch* b) {
+  if (!b) return;
+  if (b->master) cudaStreamSynchronize(b->master);
+  for (int p = 0; p < 8; ++p)
+    if (b->gexec[p]) cudaGraphExecDestroy(b->gexec[p]);
+  for (auto e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->master) cudaStreamDestroy(b->master);
+  delete b;
+}
+
+static int batch_capture(sim_batch* b, int p) {
+  const int count = (int)b->hs.size();
+  for (auto* h : b->hs) h->xhead = p;
+  long long c0 = g_launches.load();
+  CUDA_TRY(cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal));
+  int rc = SIM_OK;
+  int g0 = 0;
+  for (size_t g = 0; g < b->group_end.size() && rc == SIM_OK; ++g) {
+    const int g1 = b->group_end[g];
+    if (cudaEventRecord(b->fork, b->master) != cudaSuccess) rc = SIM_EINTERNAL;
+    for (int i = g0; i < g1 && rc == SIM_OK; ++i)
+      if (cudaStreamWaitEvent(b->hs[i]->stream, b->fork, 0) != cudaSuccess) rc = SIM_EINTERNAL;
+    for (int i = g0; i < g1 && rc == SIM_OK; ++i) rc = one_step(b->hs[i]);
+    for (int i = g0; i < g1 && rc == SIM_OK; ++i)
+      if (cudaEventRecord(b->join[i], b->hs[i]->stream) != cudaSuccess ||
+          cudaStreamWaitEvent(b->master, b->join[i], 0) != cudaSuccess)
+        rc = SIM_EINTERNAL;
+    g0 = g1;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(b->master, &graph);
+  long long nodes = g_launches.load() - c0;
+  g_launches.fetch_sub(nodes);
+  for (auto* h : b->hs) h->rec_count -= 1;   // one_step counted a record per molecule
+  if (rc != SIM_OK || ee != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return fail(SIM_EINTERNAL, std::string("capture of the batch step failed: ") + cudaGetErrorString(ee));
+  }
+  cudaError_t ie = cudaGraphInstantiate(&b->gexec[p], graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    b->gexec[p] = nullptr;
+    return fail(SIM_EINTERNAL, std::string("batch graph instantiation failed: ") + cudaGetErrorString(ie));
+  }
+  b->gnodes[p] = nodes;
+  (void)count;
+  return SIM_OK;
+}
+
+int sim_batch_create(sim_handle* const* hs, int count, sim_batch** out) {
+  if (!hs || count < 1 || !out) return fail(SIM_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return fail(SIM_EINVAL, "null handle in batch");
+    if (hs[i]->xhead != hs[0]->xhead) return fail(SIM_EINVAL, "batch members must have taken the same number of steps");
+    if (hs[i]->cfg.kernel == SIM_KERNEL_BOMD) return fail(SIM_EINVAL, "Born-Oppenheimer steps cannot be captured");
+    if (hs[i]->prof) return fail(SIM_EINVAL, "phase profiling is on for a batch member");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i] || hs[j]->stream == hs[i]->stream)
+        return fail(SIM_EINVAL, "batch members need distinct handles on distinct streams");
+  }
+  sim_batch* b = new sim_batch();
+  b->hs.assign(hs, hs + count);
+  const long long cap = 1000LL * hs[0]->sms;
+  long long load = 0;
+  for (int i = 0; i < count; ++i) {
+    long long w = eig_tridiag_weight(hs[i]->n, hs[i]->sms);
+    if (i > 0 && load + w > cap) {
+      b->group_end.push_back(i);
+      load = 0;
+    }
+    load += w;
+  }
+  b->group_end.push_back(count);
+  b->join.assign(count, nullptr);
+  int rc = SIM_OK;
+  if (cudaStreamCreateWithFlags(&b->master, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+    rc = fail(SIM_EINTERNAL, "stream or event creation failed");
+  for (int i = 0; i < count && rc == SIM_OK; ++i)
+    if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess)
+      rc = fail(SIM_EINTERNAL, "event creation failed");
+  for (int i = 0; i < count && rc == SIM_OK; ++i)
+    if (cudaStreamSynchronize(hs[i]->stream) != cudaSuccess) rc = fail(SIM_EINTERNAL, "synchronisation failed");
+  const int head = hs[0]->xhead;
+  for (int p = 0; p < 8 && rc == SIM_OK; ++p) rc = batch_capture(b, p);
+  for (auto* h : b->hs) h->xhead = head;
+  if (rc != SIM_OK) {
+    std::string msg = t_err;
+    batch_release(b);
+    t_err = msg;
+    return rc;
+  }
+  *out = b;
+  return SIM_OK;
+}
+
+int sim_batch_run(sim_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return fail(SIM_EINVAL, "bad batch run arguments");
+  for (auto* h : b->hs) {
+    if (h->xhead != b->hs[0]->xhead) return fail(SIM_EINVAL, "a batch member was stepped on its own");
+    reset_records(h);
+    // the members' streams must be idle before the graph writes their buffers
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    const int p = b->hs[0]->xhead;
+    CUDA_TRY(cudaGraphLaunch(b->gexec[p], b->master));
+    g_launches.fetch_add(b->gnodes[p]);
+    for (auto* h : b->hs) {
+      h->xhead = (p + 7) % 8;
+      h->rec_count += 1;
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(b->master));
+  int first = SIM_OK;
+  for (auto* h : b->hs) {
+    int rc = check_status(h);
+    if (rc && first == SIM_OK) first = rc;
+  }
+  return first;
+}
+
+void sim_batch_destroy(sim_batch* b) { batch_release(b); }
+
 int sim_batch_step(sim_handle* const* hs, int count, int nsteps) {
   if (!hs || count < 0 || nsteps < 0) return fail(SIM_EINVAL, "bad batch arguments");
   for (int i = 0; i < count; ++i)

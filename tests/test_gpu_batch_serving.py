@@ -185,3 +185,32 @@ def test_server_trajectory_matches_oracle():
     assert max_abs(r["R"], st.R) < 1e-8
     assert max_abs(r["F"], st.ev["forces"]) < 1e-4
     assert max_abs([x["E_tot"] for x in r["records"]], E) < 1e-7
+
+
+def test_whole_batch_graph_equals_individual_steps():
+    """One CUDA graph per batch step (every molecule a branch): records and
+    states bitwise equal to stepping each molecule alone, across the X ring."""
+    mols = _small_batch(4, seed=5)
+    cfg = _cfg(precision=kx.SIM_PREC_MIXED)
+    Vs = [synth.maxwell_boltzmann(m.Z, 300.0, seed=30 + i) for i, m in enumerate(mols)]
+    hs_b = [kx.sim_create(cfg, _table(), m.Z, m.R, V=v, charge=m.charge) for m, v in zip(mols, Vs)]
+    hs_i = [kx.sim_create(cfg, _table(), m.Z, m.R, V=v, charge=m.charge) for m, v in zip(mols, Vs)]
+    b = kx.sim_batch_create(hs_b)
+    try:
+        kx.sim_batch_run(b, 6)
+        kx.sim_batch_run(b, 5)                  # 11 steps: the ring wraps
+        for h in hs_i:
+            kx.sim_step(h, 6)
+            kx.sim_step(h, 5)
+        for m, hb, hi in zip(mols, hs_b, hs_i):
+            assert kx.sim_records(hb, 5) == kx.sim_records(hi, 5)
+            for a, c in zip(_state(hb, m.natoms), _state(hi, m.natoms)):
+                assert np.array_equal(a, c)
+        kx.sim_step(hs_b[0], 1)                 # a member stepped on its own leaves the batch's phase
+        with pytest.raises(kx.SimError) as e:
+            kx.sim_batch_run(b, 1)
+        assert e.value.code == kx.SIM_EINVAL
+    finally:
+        kx.sim_batch_destroy(b)
+        for h in hs_b + hs_i:
+            kx.sim_destroy(h)
