@@ -296,8 +296,12 @@ int sim_server_create(const sim_server_config* cfg, sim_server** out) {
   if (s->cfg.max_active <= 0) s->cfg.max_active = 64;
   if (s->cfg.hbm_budget_bytes == 0) {
     size_t fr = 0, tot = 0;
+    int prev = 0;
+    cudaGetDevice(&prev);                 // leave the caller's current device as it was
     cudaSetDevice(s->cfg.device);
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { delete s; return SIM_EINTERNAL; }
+    cudaError_t me = cudaMemGetInfo(&fr, &tot);
+    cudaSetDevice(prev);
+    if (me != cudaSuccess) { delete s; return SIM_EINTERNAL; }
     s->cfg.hbm_budget_bytes = (size_t)(0.9 * (double)fr);
   }
   if (s->cfg.admission_threads <= 0) s->cfg.admission_threads = 4;
