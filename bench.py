@@ -329,7 +329,7 @@ BATCH = dict(workload="128 organic molecules, 12-200 atoms (C/N/O/H, seed 3)", m
              krylov_rank=4, dt_fs=0.5, precision="mixed", param_table="synthetic NDDO seed 1")
 
 
-def _batch_handles(kx, mols, table, graphs, stream_per_handle=True):
+def _batch_handles(kx, mols, table, graphs):
     cfg = kx.sim_config_default(Te=BATCH["Te_K"], dt=BATCH["dt_fs"], m_max=4, m_min=4,
                                 precision=kx.SIM_PREC_MIXED, scf_tol=1e-7, scf_max=40, scf_krylov=1,
                                 scf_accept=1)
