@@ -240,8 +240,11 @@ int sim_batch_step(sim_handle* const* handles, int count, int nsteps);
  * stay owned by the caller and must outlive the batch.
  * sim_batch_run -- nsteps steps of the whole batch, one graph launch per step;
  * synchronous; results are bitwise those of stepping each handle alone; the
- * records are read per handle with sim_records.  Stepping a member on its own
- * between runs is rejected (SIM_EINVAL). */
+ * records are read per handle with sim_records.  A run is rejected
+ * (SIM_EINVAL) when a member's X-ring phase differs from the batch's, which
+ * is what stepping a member on its own a number of times other than a
+ * multiple of 8 between runs leads to; members stepped alone by a multiple of
+ * 8 steps stay consistent with the captured graphs. */
 typedef struct sim_batch sim_batch;
 int sim_batch_create(sim_handle* const* handles, int count, sim_batch** out);
 int sim_batch_run(sim_batch* b, int nsteps);
@@ -256,7 +259,7 @@ size_t sim_estimate_bytes(const sim_config* cfg, int natoms, const int* Z);
  * their estimated memory fits the budget, fewer than max_active are live and
  * the persistent eigensolver grids of all live trajectories fit on the
  * device at once (their grid barriers need every block resident),
- * and a stepping thread that keeps one step in flight per live trajectory
+ * and a stepping thread that keeps up to two steps in flight per live trajectory
  * (each on its own stream, through CUDA graphs when use_graphs != 0, except
  * for Born-Oppenheimer trajectories) and retires a trajectory when its steps
  * are done.  Every trajectory computes
@@ -401,7 +404,7 @@ int sim_tc_gemm_noalloc(int n, const double* A, const double* B, int terms, int 
  * mixed-precision path (no counterpart in the paper; it exposes one building
  * block of eq. 19 / eq. 36 so tests can check it in isolation).
  * C = sum over `terms` BF16-piece products A_i B_j^T of the FP64 inputs:
- * terms = 1 (plain BF16), 3 (2 pieces) or 6 (3 pieces).  A, B, C are host
+ * terms = 1 (plain BF16), 3 (2 pieces), 6 (3 pieces) or 10 (4 pieces).  A, B, C are host
  * n x n row-major arrays; sym != 0 computes only the upper tiles and mirrors
  * (use only when A B^T is symmetric).  Allocates and frees its own device
  * memory; synchronous. */

@@ -29,8 +29,14 @@ complex-step method (exact to rounding, independent of any hand derivation).
 
 Pins (tests/test_oracle_nddo.py): 1s-1s overlap closed form, overlaps vs 3-D
 quadrature, R -> 0 and R -> infinity limits, rotational invariance, complex
-step vs finite differences.  Parity with MOPAC/PySeQM values: unpinned
-(synthetic parameters, no printed example).
+step vs finite differences.  (tests/test_oracle_multipoles_corecore.py): the
+charge sets reproduce the monopole, dipole and traceless quadrupole of every
+Slater orbital product (radial and angular quadrature); the far field follows
+those moments; integrals at bonding distances equal a direct 3-D charge sum;
+the core-core term reduces to Z'Z'(ss|ss) (x1, x2, x3 with the exponentials
+off / half on / on), decays at each atom's own alpha, carries both atoms'
+Gaussians with 1/R, is symmetric in A and B and tends to Z'Z'e^2/R.  Parity
+with MOPAC/PySeQM values: unpinned (synthetic parameters, no printed example).
 """
 import math
 import numpy as np

@@ -32,6 +32,22 @@ static int fail(int code, const std::string& msg) {
       return fail(SIM_EINTERNAL, std::string(#x) + ": " + cudaGetErrorString(_e));   \
   } while (0)
 
+// Makes a handle's device current for the duration of a call and gives the
+// caller back its own current device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (dev >= 0 && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 // damping constants of the modified Verlet scheme, k_max = 6 (eq. 29; the
 // paper takes kappa, alpha, c_k from its ref. 24)
 static const double kKappa = 1.84;
@@ -763,7 +779,13 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
   h->mmax = cfg->m_max;
   h->beta = 1.0 / (kBoltz * cfg->Te);
   h->dev = cfg->device;
-  if (cudaSetDevice(h->dev) != cudaSuccess) { delete h; return fail(SIM_EINVAL, "cudaSetDevice failed"); }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || h->dev < 0 || h->dev >= ndev) {
+    cudaGetLastError();
+    delete h;
+    return fail(SIM_EINVAL, "no such CUDA device: " + std::to_string(cfg->device));
+  }
+  DeviceGuard dg(h->dev);   // the caller's current device is restored on every return
   cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
   if (!upload_overlap_tables()) { delete h; return fail(SIM_EINTERNAL, "overlap table upload failed"); }
   if (cfg->stream) {
@@ -853,6 +875,7 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
 
 int sim_step_async(sim_handle* h, int nsteps) {
   if (!h || nsteps < 0) return fail(SIM_EINVAL, "bad handle or nsteps");
+  DeviceGuard dg(h->dev);
   for (int i = 0; i < nsteps; ++i) {
     int rc = launch_step(h);
     if (rc) return rc;
@@ -862,6 +885,7 @@ int sim_step_async(sim_handle* h, int nsteps) {
 
 int sim_step(sim_handle* h, int nsteps, sim_step_result* out) {
   if (!h || nsteps < 0) return fail(SIM_EINVAL, "bad handle or nsteps");
+  DeviceGuard dg(h->dev);
   int done = 0;
   while (done < nsteps) {
     int chunk = nsteps - done;
@@ -886,6 +910,7 @@ int sim_step(sim_handle* h, int nsteps, sim_step_result* out) {
 int sim_step_host(sim_handle* h, const double* R_in, const double* V_in, double* R_out, double* V_out,
                   double* F_out, sim_step_result* out) {
   if (!h) return fail(SIM_EINVAL, "null handle");
+  DeviceGuard dg(h->dev);
   cudaStream_t s = h->stream;
   size_t b3 = 3 * (size_t)h->N * sizeof(double);
   if (R_in) CUDA_TRY(cudaMemcpyAsync(h->R, R_in, b3, cudaMemcpyHostToDevice, s));
@@ -903,6 +928,7 @@ int sim_step_host(sim_handle* h, const double* R_in, const double* V_in, double*
 
 int sim_last_result(sim_handle* h, sim_step_result* out) {
   if (!h || !out) return fail(SIM_EINVAL, "null argument");
+  DeviceGuard dg(h->dev);
   long long i = h->rec_count > 0 ? (h->rec_count - 1) % kRecCap : 0;
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   CUDA_TRY(cudaMemcpy(out, h->rec + i, sizeof(sim_step_result), cudaMemcpyDeviceToHost));
@@ -911,6 +937,7 @@ int sim_last_result(sim_handle* h, sim_step_result* out) {
 
 int sim_records(sim_handle* h, sim_step_result* out, int count) {
   if (!h || !out || count < 0) return fail(SIM_EINVAL, "bad arguments");
+  DeviceGuard dg(h->dev);
   if (count > kRecCap || count > h->rec_count) return fail(SIM_EINVAL, "fewer records available than requested");
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   for (int i = 0; i < count; ++i) {
@@ -922,6 +949,7 @@ int sim_records(sim_handle* h, sim_step_result* out, int count) {
 
 int sim_wait(sim_handle* h) {
   if (!h) return fail(SIM_EINVAL, "null handle");
+  DeviceGuard dg(h->dev);
   return check_status(h);
 }
 
@@ -942,6 +970,7 @@ size_t sim_estimate_bytes(const sim_config* cfg, int natoms, const int* Z) {
 
 int sim_enable_graphs(sim_handle* h, int enable) {
   if (!h) return fail(SIM_EINVAL, "null handle");
+  DeviceGuard dg(h->dev);
   if (enable && h->cfg.kernel == SIM_KERNEL_BOMD)
     return fail(SIM_EINVAL, "Born-Oppenheimer steps read the SCF residual on the host and cannot be captured");
   if (enable && !h->graphs) {
@@ -975,6 +1004,7 @@ struct sim_batch {
 
 static void batch_release(sim_batch* b) {
   if (!b) return;
+  DeviceGuard dg(b->hs.empty() ? 0 : b->hs[0]->dev);
   if (b->master) cudaStreamSynchronize(b->master);
   for (int p = 0; p < 8; ++p)
     if (b->gexec[p]) cudaGraphExecDestroy(b->gexec[p]);
@@ -1038,6 +1068,7 @@ int sim_batch_create(sim_handle* const* hs, int count, sim_batch** out) {
       if (hs[j] == hs[i] || hs[j]->stream == hs[i]->stream)
         return fail(SIM_EINVAL, "batch members need distinct handles on distinct streams");
   }
+  DeviceGuard dg(hs[0]->dev);
   sim_batch* b = new sim_batch();
   b->hs.assign(hs, hs + count);
   const long long cap = 1000LL * hs[0]->sms;
@@ -1076,6 +1107,7 @@ int sim_batch_create(sim_handle* const* hs, int count, sim_batch** out) {
 
 int sim_batch_run(sim_batch* b, int nsteps) {
   if (!b || nsteps < 0) return fail(SIM_EINVAL, "bad batch run arguments");
+  DeviceGuard dg(b->hs[0]->dev);
   for (auto* h : b->hs) {
     if (h->xhead != b->hs[0]->xhead) return fail(SIM_EINVAL, "a batch member was stepped on its own");
     reset_records(h);
@@ -1106,6 +1138,7 @@ int sim_batch_step(sim_handle* const* hs, int count, int nsteps) {
   if (!hs || count < 0 || nsteps < 0) return fail(SIM_EINVAL, "bad batch arguments");
   for (int i = 0; i < count; ++i)
     if (!hs[i]) return fail(SIM_EINVAL, "null handle in batch");
+  DeviceGuard dg(count > 0 ? hs[0]->dev : -1);
   int first = SIM_OK;
   // groups of consecutive handles whose persistent eigensolver grids fit on
   // the device at the same time (their grid barriers need every block resident)
@@ -1138,6 +1171,7 @@ int sim_batch_step(sim_handle* const* hs, int count, int nsteps) {
 
 int sim_get_state(sim_handle* h, double* R, double* V, double* F, double* D0) {
   if (!h) return fail(SIM_EINVAL, "null handle");
+  DeviceGuard dg(h->dev);
   cudaStream_t s = h->stream;
   size_t b3 = 3 * (size_t)h->N * sizeof(double);
   if (R) CUDA_TRY(cudaMemcpyAsync(R, h->R, b3, cudaMemcpyDeviceToHost, s));
@@ -1150,6 +1184,7 @@ int sim_get_state(sim_handle* h, double* R, double* V, double* F, double* D0) {
 
 int sim_set_state(sim_handle* h, const double* R, const double* V, const double* Xhist) {
   if (!h) return fail(SIM_EINVAL, "null handle");
+  DeviceGuard dg(h->dev);
   cudaStream_t s = h->stream;
   size_t nn = (size_t)h->n * h->n;
   size_t b3 = 3 * (size_t)h->N * sizeof(double);
@@ -1171,6 +1206,7 @@ static const char kCkptMagic[8] = {'K', 'S', 'A', 'X', 'L', 'C', 'K', '1'};
 
 int sim_save(sim_handle* h, const char* path) {
   if (!h || !path) return fail(SIM_EINVAL, "null argument");
+  DeviceGuard dg(h->dev);
   size_t nn = (size_t)h->n * h->n;
   std::vector<double> R(3 * (size_t)h->N), V(3 * (size_t)h->N), X(7 * nn);
   cudaStream_t s = h->stream;
@@ -1232,6 +1268,7 @@ int sim_load(const char* path, int device, void* stream, sim_handle** out) {
   sim_handle* h = nullptr;
   int rc = sim_create(&cfg, &table, head[1], Z.data(), R.data(), V.data(), head[3], X.data(), &h);
   if (rc) return rc;
+  DeviceGuard dg(h->dev);
   if (h->n != head[2]) {
     sim_destroy(h);
     return fail(SIM_EINVAL, "checkpoint basis size does not match its atoms");
@@ -1251,6 +1288,7 @@ int sim_load(const char* path, int device, void* stream, sim_handle** out) {
 
 int sim_get_matrix(sim_handle* h, int which, double* out) {
   if (!h || !out) return fail(SIM_EINVAL, "null argument");
+  DeviceGuard dg(h->dev);
   const double* src = nullptr;
   switch (which) {
     case SIM_MAT_X: src = xslot(h, 0); break;
@@ -1268,6 +1306,7 @@ int sim_get_matrix(sim_handle* h, int which, double* out) {
 
 int sim_get_vector(sim_handle* h, int which, double* out) {
   if (!h || !out) return fail(SIM_EINVAL, "null argument");
+  DeviceGuard dg(h->dev);
   const double* src = (which == 0) ? h->eps : (which == 1) ? h->f : nullptr;
   if (!src) return fail(SIM_EINVAL, "unknown vector id");
   CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1277,6 +1316,7 @@ int sim_get_vector(sim_handle* h, int which, double* out) {
 
 int sim_profile_enable(sim_handle* h, int enable) {
   if (!h) return fail(SIM_EINVAL, "null handle");
+  DeviceGuard dg(h->dev);
   if (h->prof && !enable) collect_events(h);
   h->prof = enable != 0;
   for (int i = 0; i < PH_COUNT; ++i) { h->ph_ms[i] = 0.0; h->ph_n[i] = 0; }
@@ -1288,6 +1328,7 @@ const char* sim_phase_name(int p) { return (p >= 0 && p < PH_COUNT) ? kPhaseName
 
 int sim_phase_times(sim_handle* h, double* ms, long long* launches, double* work) {
   if (!h) return fail(SIM_EINVAL, "null handle");
+  DeviceGuard dg(h->dev);
   collect_events(h);
   double n = h->n, np = h->npair;
   // algorithmic work of one timed phase instance (bytes for HBM-bound phases,
@@ -1353,6 +1394,7 @@ int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sy
 
 void sim_destroy(sim_handle* h) {
   if (!h) return;
+  DeviceGuard dg(h->dev);
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (int p = 0; p < 8; ++p)
     if (h->gexec[p]) cudaGraphExecDestroy(h->gexec[p]);

@@ -4,6 +4,8 @@
 #include <stdint.h>
 #include <math.h>
 
+#include <mutex>
+
 #ifndef KX_HOST_DEVICE
 #define KX_HOST_DEVICE __host__ __device__ __forceinline__
 #endif
@@ -15,6 +17,26 @@ namespace kx {
 // ---------------------------------------------------------------------------
 void count_launch();            // increments the library-wide launch counter
 cudaError_t last_launch_error(); // cudaGetLastError wrapper
+
+// Set-up that belongs to a device (function attributes, __constant__ tables):
+// done once per device ordinal, with that device current.  A process-wide
+// "once" would leave every device but the first one unconfigured.
+constexpr int kMaxDevices = 64;
+struct PerDeviceOnce {
+  std::mutex mu;
+  unsigned long long done = 0;   // bit d: device d is set up
+};
+template <typename Fn>
+bool once_per_device(PerDeviceOnce& flag, Fn&& fn) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+  std::lock_guard<std::mutex> lk(flag.mu);
+  const unsigned long long bit = 1ull << dev;
+  if (flag.done & bit) return true;
+  if (!fn()) return false;
+  flag.done |= bit;
+  return true;
+}
 
 // physical constants (this library's own copy)
 constexpr double kE2 = 14.399645;            // e^2/(4 pi eps0), eV*Angstrom

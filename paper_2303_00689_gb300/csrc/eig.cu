@@ -552,19 +552,22 @@ static int tridiag_blocks(int n, int sm_count) {
 
 static size_t tridiag_smem(int n) { return (3 * (size_t)n + 32) * sizeof(double); }
 
-// raise the kernel's opt-in dynamic shared memory monotonically (thread-safe)
+// raise the kernel's opt-in dynamic shared memory monotonically, per device
+// (the attribute belongs to the device that is current; thread-safe)
 static bool tridiag_smem_attribute(size_t smem) {
   if (smem <= 48 * 1024) return true;
   static std::mutex mu;
-  static size_t smem_set = 0;
+  static size_t smem_set[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
   std::lock_guard<std::mutex> lk(mu);
-  if (smem > smem_set) {
+  if (smem > smem_set[dev]) {
     if (cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
       cudaGetLastError();
       return false;
     }
-    smem_set = smem;
+    smem_set[dev] = smem;
   }
   return true;
 }
@@ -652,12 +655,12 @@ static void transpose_sq(cudaStream_t s, int n, const double* A, double* At) {
 }
 
 static void eig_backtransform_tc(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork& tw) {
-  static std::once_flag attr;
-  std::call_once(attr, [] {
-    cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kBtBlockTc * kBtBlockTc * (int)sizeof(double));
-    cudaFuncSetAttribute(tfactor_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kBtBlockTc * kBtBlockTc * (int)sizeof(double));
+  static PerDeviceOnce attr;
+  once_per_device(attr, [] {
+    return cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kBtBlockTc * kBtBlockTc * (int)sizeof(double)) == cudaSuccess &&
+           cudaFuncSetAttribute(tfactor_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kBtBlockTc * kBtBlockTc * (int)sizeof(double)) == cudaSuccess;
   });
   const int nref = n - 2;
   const int nblk = (nref + kBtBlockTc - 1) / kBtBlockTc;

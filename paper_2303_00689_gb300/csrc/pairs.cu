@@ -318,7 +318,7 @@ __global__ void pair_derivs_kernel(int npair, const int* __restrict__ pA, const 
 }
 
 // ---------------------------------------------------------------------------
-// host side: overlap polynomial tables (built once per process)
+// host side: overlap polynomial tables (built and uploaded once per device)
 // ---------------------------------------------------------------------------
 namespace {
 struct Poly {
@@ -381,11 +381,10 @@ static bool upload_overlap_tables_once() {
   return true;
 }
 
+// __constant__ memory is per device: upload on every device the library runs on
 bool upload_overlap_tables() {
-  static std::once_flag once;
-  static bool ok = false;
-  std::call_once(once, [] { ok = upload_overlap_tables_once(); });
-  return ok;
+  static PerDeviceOnce flag;
+  return once_per_device(flag, [] { return upload_overlap_tables_once(); });
 }
 
 void launch_pair_values(cudaStream_t s, int npair, const int* pA, const int* pB, const int* elem,

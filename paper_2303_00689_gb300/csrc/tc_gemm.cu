@@ -541,10 +541,12 @@ bool tc_ready(const TcWork& w) { return w.base && ((TcBuffers*)w.base)->maps_ok;
 
 int* tc_error_flag(const TcWork& w) { return w.base ? ((TcBuffers*)w.base)->err : nullptr; }
 
+// the opt-in shared-memory size is a per-device attribute of the kernel
 static void set_smem_attribute() {
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  static PerDeviceOnce flag;
+  once_per_device(flag, [] {
+    return cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) ==
+           cudaSuccess;
   });
 }
 
