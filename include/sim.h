@@ -354,6 +354,8 @@ enum sim_matrix {
   SIM_MAT_H = 3,       /* core Hamiltonian h                                */
   SIM_MAT_KERNEL = 4,  /* sum_i V_i c_i ~ K (D0 - X) (eq. 34)               */
   SIM_MAT_Q = 5,       /* eigenvectors of F as columns                      */
+  SIM_MAT_XHIST = 6,   /* SIM_MAT_XHIST + k, k = 0..6: X(t - k dt), the
+                          history eq. 29 carries (SIM_MAT_XHIST + 0 = X(t))   */
 };
 int sim_get_matrix(sim_handle* h, int which, double* out);
 

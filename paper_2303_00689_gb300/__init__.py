@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libksaxl.so")
 SIM_OK, SIM_PENDING, SIM_EINVAL, SIM_ENOMEM, SIM_ENOCONV, SIM_ENUMERIC, SIM_ETIMEOUT, SIM_EINTERNAL = range(8)
 SIM_PREC_FP64, SIM_PREC_MIXED = 0, 1
 SIM_KERNEL_KRYLOV, SIM_KERNEL_XL, SIM_KERNEL_BOMD = 0, 1, 2
-SIM_MAT_X, SIM_MAT_D0, SIM_MAT_FOCK, SIM_MAT_H, SIM_MAT_KERNEL, SIM_MAT_Q = range(6)
+SIM_MAT_X, SIM_MAT_D0, SIM_MAT_FOCK, SIM_MAT_H, SIM_MAT_KERNEL, SIM_MAT_Q, SIM_MAT_XHIST = range(7)
 SIM_NFIELDS = 23
 
 EXPORTED = (

@@ -273,7 +273,7 @@ static void dmpt(sim_handle* h, const double* F1, double* D1) {
 
 static int eig(sim_handle* h) {
   phase_begin(h, PH_TRIDIAG);
-  int st = eig_tridiagonalize(h->stream, h->n, h->Fock, h->ew, &h->sc->status, h->sms);
+  int st = eig_tridiagonalize(h->stream, h->n, h->Fock, h->ew, &h->sc->status, h->sms, mixed(h));
   phase_end(h);
   if (st != 0) return fail(SIM_EINTERNAL, "tridiagonalisation launch failed (code " + std::to_string(st) + ")");
   phase_begin(h, PH_BISECT);
@@ -1297,7 +1297,12 @@ int sim_get_matrix(sim_handle* h, int which, double* out) {
     case SIM_MAT_H: src = h->h; break;
     case SIM_MAT_KERNEL: src = h->K; break;
     case SIM_MAT_Q: src = h->Q; break;
-    default: return fail(SIM_EINVAL, "unknown matrix id");
+    default:
+      if (which >= SIM_MAT_XHIST && which <= SIM_MAT_XHIST + 6) {
+        src = xslot(h, which - SIM_MAT_XHIST);
+        break;
+      }
+      return fail(SIM_EINVAL, "unknown matrix id");
   }
   CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)h->n * h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));

@@ -9,6 +9,11 @@
 //     order, bitwise identical), so no broadcast is needed.  The barrier is a
 //     counter/generation pair with a bounded spin: on expiry the kernel sets
 //     kStatusTimeout and returns.
+//     The mixed-precision path runs the same algorithm in double-float
+//     arithmetic (df.cuh): the trailing matrix is held as FP32 (hi, lo)
+//     pairs and the O(n^2)-per-column update and matrix-vector product run on
+//     the FP32 pipe, 64 times GB300's FP64 rate, at about 48 significant bits;
+//     the reflector scalars (beta, tau) stay FP64.
 //  2. Eigenvalues of the tridiagonal matrix by bisection on Sturm counts,
 //     one thread per eigenvalue (ascending order by construction): a coarse
 //     FP32 phase, an FP64 bracket check, then FP64 bisection.
@@ -23,6 +28,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "df.cuh"
 #include "kernels.h"
 #include "tc_gemm.h"
 
@@ -205,6 +211,247 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
   }
 }
 
+// ---- double-float tridiagonalisation (mixed path) -------------------------
+__device__ __forceinline__ dfl df_shfl_xor(dfl a, int o) {
+  return dfl{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ dfl df_warp_sum(dfl v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  return v;
+}
+// block-wide double-float sum in a fixed order; every thread gets the total.
+// `scratch` holds >= 32 dfl of shared memory.
+__device__ __forceinline__ dfl df_block_sum(dfl v, dfl* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = df_warp_sum(df_norm(v));
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  dfl t = (threadIdx.x < nw) ? scratch[threadIdx.x] : dfl{0.0f, 0.0f};
+  if (wid == 0) t = df_warp_sum(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  dfl r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void to_df_kernel(size_t len, const double* __restrict__ x, dfl* __restrict__ y) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < len) y[i] = df_from_double(x[i]);
+}
+
+// Same reduction as tridiag_kernel (rows dealt round-robin, lazy rank-2 update
+// fused with the matrix-vector product, one grid barrier per column), with
+// the per-column critical path shortened for a kernel that is latency- rather
+// than FP64-bound:
+//  * after the barrier every block reads p_{k-1} and row k in one pass, forms
+//    w_{k-1} = p - (tau/2)(p.v)v and the updated row k (x = row k of A_k);
+//  * the matrix-vector product uses the unscaled x (x_{k+1} = x_1) and
+//    keeps a_{i,k+1}, so it need not wait for beta, tau and the scale, which
+//    thread 0 computes in FP64 meanwhile:
+//    p_i = tau scale (sum_j a_ij x_j - beta a_{i,k+1}) since v = scale (x - beta e_{k+1});
+//  * block reductions use one CTA barrier each.
+// Shared memory: two reflector buffers (ping-pong: v_{k-1} and x_k / v_k),
+// w (holding p_{k-1} until w is formed) and reduction scratch.
+constexpr int kDfRed = 32;
+constexpr int kDfSeg = 256;           // columns per (row, segment) work item: 8 per lane
+// rows per block at the first column, for a grid of G blocks
+static int tridiag_df_rmax(int n, int G) { return (n - 1 + G - 1) / G; }
+static size_t tridiag_smem_df(int n, int G) {
+  const size_t rmax = (size_t)tridiag_df_rmax(n, G), smax = (size_t)(n - 1 + kDfSeg - 1) / kDfSeg;
+  return (3 * (size_t)n + 2 * kDfRed + rmax + rmax * smax) * sizeof(dfl);
+}
+
+// Loads of data other blocks wrote since the last grid barrier (and of rows
+// this block does not own in every column) go past L1 to L2.
+__device__ __forceinline__ dfl ldcg_df(const dfl* p) {
+  const float2 v = __ldcg((const float2*)p);
+  return dfl{v.x, v.y};
+}
+
+// every thread gets the sum of the warps' partials (written to scratch[warp]
+// by lane 0 before the call); one CTA barrier
+__device__ __forceinline__ dfl df_sum_partials(const dfl* scratch, int nw) {
+  dfl t = {0.0f, 0.0f};
+  for (int w = 0; w < nw; ++w) t = df_add(t, scratch[w]);
+  return t;
+}
+
+__global__ void __launch_bounds__(kTriThreads) tridiag_df_kernel(int n, dfl* __restrict__ A,
+                                                                 double* __restrict__ Vst,
+                                                                 double* __restrict__ d,
+                                                                 double* __restrict__ e,
+                                                                 double* __restrict__ tau,
+                                                                 dfl* __restrict__ pbuf,
+                                                                 unsigned* bar, int* status, int rmax) {
+  extern __shared__ double sm[];
+  dfl* buf0 = (dfl*)sm;
+  dfl* buf1 = buf0 + n;
+  dfl* wp = buf0 + 2 * n;            // p_{k-1}, then w_{k-1}
+  dfl* redA = buf0 + 3 * n;          // partials of p.v
+  dfl* redB = redA + kDfRed;         // partials of sigma
+  dfl* ak1s = redB + kDfRed;         // a_{i,k+1} of the block's rows (rmax)
+  dfl* part = ak1s + rmax;           // (row, segment) partial sums (rmax x smax)
+  __shared__ double s_par[4];        // beta, tau, scale, tau * scale
+  __shared__ dfl s_df[3];            // beta, tau * scale, tau as double-float
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int T = blockDim.x, nw = T >> 5;
+  const int G = gridDim.x;
+  dfl tau_prev = {0.0f, 0.0f};       // tau_{k-1}
+  if (n == 1) {
+    if (blockIdx.x == 0 && tid == 0) d[0] = df_to_double(A[0]);
+    return;
+  }
+  for (int k = 0;; ++k) {
+    const bool prev = k > 0;
+    const bool last = (k == n - 2);
+    dfl* vpv = ((k + 1) & 1) ? buf1 : buf0;   // v_{k-1}, valid for indices >= k
+    dfl* vcv = (k & 1) ? buf1 : buf0;         // x_k, then v_k
+    const dfl* pbp = pbuf + (size_t)((k + 1) & 1) * n;   // p_{k-1}
+    // pass 1: p_{k-1} and row k in one sweep of loads; partial p.v
+    dfl loc = {0.0f, 0.0f};
+    for (int j = k + tid; j < n; j += T) {
+      vcv[j] = ldcg_df(A + (size_t)k * n + j);
+      if (prev) {
+        const dfl p = ldcg_df(pbp + j);
+        wp[j] = p;
+        df_acc_mul(loc, p, vpv[j]);
+      }
+    }
+    dfl wk = {0.0f, 0.0f}, vk = {0.0f, 0.0f}, coef = {0.0f, 0.0f};
+    if (prev) {
+      loc = df_warp_sum(df_norm(loc));
+      if (lane == 0) redA[wid] = loc;
+      __syncthreads();
+      const dfl pv = df_sum_partials(redA, nw);
+      coef = df_mul(df_mul(dfl{0.5f, 0.0f}, tau_prev), pv);
+      vk = vpv[k];
+      wk = df_sub(wp[k], df_mul(coef, vk));      // wp[k] is never overwritten below
+    }
+    // pass 2: w_{k-1} and the updated row k; sigma = sum_{j >= k+2} x_j^2
+    dfl sig = {0.0f, 0.0f};
+    dfl dk = {0.0f, 0.0f};
+    for (int j = k + tid; j < n; j += T) {
+      dfl x = vcv[j];
+      if (prev) {
+        const dfl wj = (j == k) ? wk : df_sub(wp[j], df_mul(coef, vpv[j]));
+        if (j > k) wp[j] = wj;
+        x = df_rank2(x, vk, wj, wk, vpv[j]);
+      }
+      if (j == k) {
+        dk = x;
+      } else {
+        vcv[j] = x;
+        if (j >= k + 2) df_acc_mul(sig, x, x);
+      }
+    }
+    if (last) {
+      __syncthreads();
+      if (blockIdx.x == 0 && tid == 0) {
+        const int b = n - 1;
+        dfl abb = ldcg_df(A + (size_t)b * n + b);
+        if (prev) abb = df_rank2(abb, vpv[b], wp[b], wp[b], vpv[b]);
+        d[n - 2] = df_to_double(dk);
+        e[n - 2] = df_to_double(vcv[b]);
+        d[b] = df_to_double(abb);
+      }
+      return;
+    }
+    sig = df_warp_sum(df_norm(sig));
+    if (lane == 0) redB[wid] = sig;
+    __syncthreads();
+    // thread 0: reflector scalars in FP64 while the other warps start the product
+    if (tid == 0) {
+      const double sigma = df_to_double(df_sum_partials(redB, nw));
+      const double x1d = df_to_double(vcv[k + 1]);
+      double beta, t, scale;
+      if (sigma == 0.0) {
+        beta = x1d; t = 0.0; scale = 0.0;
+      } else {
+        double nrm = ::sqrt(x1d * x1d + sigma);
+        beta = (x1d >= 0.0) ? -nrm : nrm;
+        t = (beta - x1d) / beta;
+        scale = 1.0 / (x1d - beta);
+      }
+      s_par[0] = beta; s_par[1] = t; s_par[2] = scale; s_par[3] = t * scale;
+      s_df[0] = df_from_double(beta);
+      s_df[1] = df_from_double(t * scale);
+      s_df[2] = df_from_double(t);
+      if (blockIdx.x == 0) { d[k] = df_to_double(dk); e[k] = beta; tau[k] = t; }
+    }
+    // fused: pending rank-2 update (v_{k-1}, w_{k-1}) of rows/cols >= k+1 and
+    // sum_j a_ij x_j.  The block's rows (i = k+1+b+rG) are cut into segments
+    // of kDfSeg columns and the (row, segment) items dealt over the warps, so
+    // the warps stay balanced while the trailing matrix shrinks; every lane
+    // issues all loads of its item before the arithmetic.
+    const int R = (n - (k + 1) - (int)blockIdx.x + G - 1) / G;
+    const int S = (n - (k + 1) + kDfSeg - 1) / kDfSeg;
+    for (int q = wid; q < R * S; q += nw) {
+      const int r = q / S, sg = q - r * S;
+      const int i = k + 1 + (int)blockIdx.x + r * G;
+      dfl* row = A + (size_t)i * n;
+      const int jb = k + 1 + sg * kDfSeg + lane;
+      const int je = min(n, k + 1 + (sg + 1) * kDfSeg);
+      dfl xs[kDfSeg / 32];
+#pragma unroll
+      for (int u = 0; u < kDfSeg / 32; ++u) {
+        const int j = jb + 32 * u;
+        xs[u] = (j < je) ? ldcg_df(row + j) : dfl{0.0f, 0.0f};
+      }
+      dfl a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f};
+      if (prev) {
+        const dfl vi = vpv[i], wi = wp[i];
+#pragma unroll
+        for (int u = 0; u < kDfSeg / 32; ++u) {
+          const int j = jb + 32 * u;
+          if (j < je) {
+            const dfl x = df_rank2(xs[u], vi, wp[j], wi, vpv[j]);
+            row[j] = x;
+            xs[u] = x;
+            if (u & 1) df_acc_mul(a1, x, vcv[j]); else df_acc_mul(a0, x, vcv[j]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < kDfSeg / 32; ++u) {
+          const int j = jb + 32 * u;
+          if (j < je) {
+            if (u & 1) df_acc_mul(a1, xs[u], vcv[j]); else df_acc_mul(a0, xs[u], vcv[j]);
+          }
+        }
+      }
+      dfl acc = df_warp_sum(df_add(df_norm(a0), df_norm(a1)));
+      if (lane == 0) {
+        part[r * S + sg] = acc;
+        if (sg == 0) ak1s[r] = xs[0];      // lane 0, u = 0 is column k+1
+      }
+    }
+    __syncthreads();
+    const dfl beta_df = s_df[0], ts_df = s_df[1];
+    tau_prev = s_df[2];
+    const double scale = s_par[2];
+    // p_i = tau scale (sum_j a_ij x_j - beta a_{i,k+1}), segments summed in order
+    dfl* pb = pbuf + (size_t)(k & 1) * n;
+    for (int r = tid; r < R; r += T) {
+      dfl dot = {0.0f, 0.0f};
+      for (int sg = 0; sg < S; ++sg) dot = df_add(dot, part[r * S + sg]);
+      pb[k + 1 + (int)blockIdx.x + r * G] = df_mul(ts_df, df_sub(dot, df_mul(beta_df, ak1s[r])));
+    }
+    // v_k = scale x (v_{k+1} = 1); the reflector store row k, spread over blocks
+    const dfl scale_df = df_from_double(scale);
+    for (int j = k + tid; j < n; j += T) {
+      if (j == k) continue;
+      const dfl v = (j == k + 1) ? dfl{1.0f, 0.0f} : df_mul(vcv[j], scale_df);
+      vcv[j] = v;
+      if (j % G == (int)blockIdx.x) Vst[(size_t)k * n + j] = df_to_double(v);
+    }
+    if (!grid_barrier(bar, gridDim.x, status)) return;
+  }
+}
+
 // Gershgorin interval, squared off-diagonals, pivmin; one block
 __global__ void gersh_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
                              double* __restrict__ e2, double* __restrict__ scal, float* __restrict__ df,
@@ -351,10 +598,14 @@ __device__ __forceinline__ double start_value(int row, int col) {
 }
 
 // inverse iteration; one thread per cluster leader; lu: 5 x n x n workspace.
-// The recurrences carry their running values in registers (a global store
-// followed by a dependent reload would put memory latency on the critical
-// path); the arithmetic and its order are those of the textbook pivoted
-// tridiagonal LU and its forward/backward substitutions.
+// The recurrences carry their running values in registers, and the loads of
+// each sweep are issued kIvB rows at a time ahead of the dependent arithmetic
+// (one thread walks n rows of a column: a load-use chain per row would put
+// the memory latency on the critical path n times); the arithmetic and its
+// order are those of the textbook pivoted tridiagonal LU and its
+// forward/backward substitutions.
+constexpr int kIvB = 8;
+
 __global__ void invit_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
                              const double* __restrict__ ev, const double* __restrict__ scal,
                              const int* __restrict__ clus, double* __restrict__ lu,
@@ -419,15 +670,25 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
     for (int it = 0; it < 2; ++it) {
       // forward (L with pivots); cur = current row r of the right-hand side
       double cur = ZC(0, j);
-      for (int r = 0; r < n - 1; ++r) {
-        const double nxt = ZC(r + 1, j);
-        const double f = LU(dl, r);
-        if (LU(pv, r) == 0.0) {
-          ZC(r, j) = cur;
-          cur = nxt - f * cur;
-        } else {
-          ZC(r, j) = nxt;
-          cur = cur - f * nxt;
+      for (int r0 = 0; r0 < n - 1; r0 += kIvB) {
+        double nx[kIvB], fv[kIvB], pf[kIvB];
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 + q;
+          if (r < n - 1) { nx[q] = ZC(r + 1, j); fv[q] = LU(dl, r); pf[q] = LU(pv, r); }
+        }
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 + q;
+          if (r < n - 1) {
+            if (pf[q] == 0.0) {
+              ZC(r, j) = cur;
+              cur = nx[q] - fv[q] * cur;
+            } else {
+              ZC(r, j) = nx[q];
+              cur = cur - fv[q] * nx[q];
+            }
+          }
         }
       }
       // backward (U, three diagonals, reciprocal pivots); z1 = x[r+1], z2 = x[r+2]
@@ -438,26 +699,44 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
         z1 = (ZC(n - 2, j) - LU(du, n - 2) * z2) * LU(rdd, n - 2);
         ZC(n - 2, j) = z1;
       }
-      for (int r = n - 3; r >= 0; --r) {
-        const double x = (ZC(r, j) - LU(du, r) * z1 - LU(du2, r) * z2) * LU(rdd, r);
-        ZC(r, j) = x;
-        z2 = z1;
-        z1 = x;
+      for (int r0 = n - 3; r0 >= 0; r0 -= kIvB) {
+        double zv[kIvB], uv[kIvB], u2[kIvB], rv[kIvB];
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 - q;
+          if (r >= 0) { zv[q] = ZC(r, j); uv[q] = LU(du, r); u2[q] = LU(du2, r); rv[q] = LU(rdd, r); }
+        }
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 - q;
+          if (r >= 0) {
+            const double x = (zv[q] - uv[q] * z1 - u2[q] * z2) * rv[q];
+            ZC(r, j) = x;
+            z2 = z1;
+            z1 = x;
+          }
+        }
       }
       // scale, re-orthogonalise within the cluster, normalise
       double mx = 0.0;
+#pragma unroll 8
       for (int r = 0; r < n; ++r) mx = fmax(mx, fabs(ZC(r, j)));
       double s = (mx > 0.0) ? 1.0 / mx : 1.0;
+#pragma unroll 8
       for (int r = 0; r < n; ++r) ZC(r, j) *= s;
       for (int c = L; c < j; ++c) {
         double dot = 0.0;
+#pragma unroll 8
         for (int r = 0; r < n; ++r) dot += ZC(r, c) * ZC(r, j);
+#pragma unroll 8
         for (int r = 0; r < n; ++r) ZC(r, j) -= dot * ZC(r, c);
       }
       double nrm = 0.0;
+#pragma unroll 8
       for (int r = 0; r < n; ++r) nrm += ZC(r, j) * ZC(r, j);
       nrm = ::sqrt(nrm);
       s = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+#pragma unroll 8
       for (int r = 0; r < n; ++r) ZC(r, j) *= s;
     }
   }
@@ -516,7 +795,7 @@ static int tc_blocks(int n) { return n > 2 ? (n - 2 + kBtBlockTc - 1) / kBtBlock
 
 size_t eig_work_bytes(int n) {
   size_t nn = (size_t)n * n;
-  size_t doubles = nn /*A*/ + nn /*Vst*/ + 4 * (size_t)n /*d e e2 tau*/ + 2 * (size_t)n /*pbuf*/ +
+  size_t doubles = nn /*A*/ + nn /*Vst*/ + 4 * (size_t)n /*d e e2 tau*/ + 3 * (size_t)n /*pbuf*/ +
                    5 * nn /*lu*/ + 2 * (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc + 2 * (size_t)kBtBlockTc * n +
                    16;
   return doubles * sizeof(double) + 64 + (size_t)n * sizeof(int) + 256;
@@ -531,7 +810,7 @@ void eig_work_bind(EigWork& w, void* base, int n) {
   w.e = p; p += n;
   w.e2 = p; p += n;
   w.tau = p; p += n;
-  w.pbuf = p; p += 2 * (size_t)n;
+  w.pbuf = p; p += 3 * (size_t)n;
   w.lu = p; p += 5 * nn;
   w.Tm = p; p += (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc;   // T and Gram of every reflector block
   w.Gm = p; p += (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc;
@@ -542,9 +821,14 @@ void eig_work_bind(EigWork& w, void* base, int n) {
   w.clus = (int*)p;
 }
 
-static int tridiag_blocks(int n, int sm_count) {
-  long long work = (long long)n * n;
-  int blocks = (int)((work + (1 << 16) - 1) >> 16);
+// About 64K (FP64 kernel) or 32K (double-float kernel, whose columns cost
+// less arithmetic and more latency) elements of the initial matrix per block,
+// at most one block per SM; small systems keep small grids, so that many of
+// them fit on the device at once (molecule batches, serving).
+static int tridiag_blocks(int n, int sm_count, bool df) {
+  const int sh = df ? 15 : 16;
+  long long work = ((long long)n * n + (1LL << sh) - 1) >> sh;
+  int blocks = (int)work;
   if (blocks < 1) blocks = 1;
   if (blocks > sm_count) blocks = sm_count;           // one block per SM (two were slower)
   return blocks;
@@ -554,54 +838,71 @@ static size_t tridiag_smem(int n) { return (3 * (size_t)n + 32) * sizeof(double)
 
 // raise the kernel's opt-in dynamic shared memory monotonically, per device
 // (the attribute belongs to the device that is current; thread-safe)
-static bool tridiag_smem_attribute(size_t smem) {
+static bool tridiag_smem_attribute(size_t smem, bool df) {
   if (smem <= 48 * 1024) return true;
   static std::mutex mu;
-  static size_t smem_set[kMaxDevices] = {};
+  static size_t smem_set[2][kMaxDevices] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
   std::lock_guard<std::mutex> lk(mu);
-  if (smem > smem_set[dev]) {
-    if (cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
+  if (smem > smem_set[df][dev]) {
+    const void* fn = df ? (const void*)tridiag_df_kernel : (const void*)tridiag_kernel;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
-    smem_set[dev] = smem;
+    smem_set[df][dev] = smem;
   }
   return true;
 }
 
+// (the larger share of the FP64 and the double-float kernel)
 int eig_tridiag_weight(int n, int sm_count) {
   if (n <= 0) return 0;
-  size_t smem = tridiag_smem(n);
-  int per_sm = 0;
-  if (!tridiag_smem_attribute(smem) ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tridiag_kernel, kTriThreads, smem) != cudaSuccess ||
-      per_sm < 1) {
-    cudaGetLastError();
-    per_sm = 1;
+  int weight = 0;
+  for (int df = 0; df < 2; ++df) {
+    int p = 0;
+    const long long b = tridiag_blocks(n, sm_count, df != 0);
+    const size_t smem = df ? tridiag_smem_df(n, (int)b) : tridiag_smem(n);
+    const void* fn = df ? (const void*)tridiag_df_kernel : (const void*)tridiag_kernel;
+    if (!tridiag_smem_attribute(smem, df != 0) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, kTriThreads, smem) != cudaSuccess || p < 1) {
+      cudaGetLastError();
+      p = 1;
+    }
+    const int wgt = (int)((1000LL * b + p - 1) / p);
+    weight = (wgt > weight) ? wgt : weight;
   }
-  long long b = tridiag_blocks(n, sm_count);
-  return (int)((1000LL * b + per_sm - 1) / per_sm);
+  return weight;
 }
 
-int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* status, int sm_count) {
+int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* status, int sm_count, bool df) {
   if (n <= 0) return 0;
-  cudaMemcpyAsync(w.A, F, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  const size_t nn2 = (size_t)n * n;
+  if (df) {
+    // the workspace holds n x n (hi, lo) pairs: the same bytes as n x n doubles
+    to_df_kernel<<<(unsigned)((nn2 + 255) / 256), 256, 0, s>>>(nn2, F, (dfl*)w.A);
+    count_launch();
+  } else {
+    cudaMemcpyAsync(w.A, F, nn2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
   cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s);
   cudaMemsetAsync(w.e, 0, (size_t)n * sizeof(double), s);
   // 1. tridiagonalisation
-  int blocks = tridiag_blocks(n, sm_count);
-  size_t smem = tridiag_smem(n);
-  if (!tridiag_smem_attribute(smem)) return -1;
+  int blocks = tridiag_blocks(n, sm_count, df);
+  size_t smem = df ? tridiag_smem_df(n, blocks) : tridiag_smem(n);
+  if (!tridiag_smem_attribute(smem, df)) return -1;
+  if (df) cudaMemsetAsync(w.Vst, 0, nn2 * sizeof(double), s);   // entries left of the reflectors
   int nn = n;
   double *A = w.A, *V = w.Vst, *d = w.d, *e = w.e, *t = w.tau, *pb = w.pbuf;
   unsigned* bar = w.bar;
   int* st = status;
-  void* args[] = {&nn, &A, &V, &d, &e, &t, &pb, &bar, &st};
-  if (cudaLaunchCooperativeKernel((void*)tridiag_kernel, dim3(blocks), dim3(kTriThreads), args, smem, s) !=
-      cudaSuccess)
+  int rmax = tridiag_df_rmax(n, blocks);
+  void* args_fp64[] = {&nn, &A, &V, &d, &e, &t, &pb, &bar, &st};
+  void* args_df[] = {&nn, &A, &V, &d, &e, &t, &pb, &bar, &st, &rmax};
+  void** args = df ? args_df : args_fp64;
+  const void* fn = df ? (const void*)tridiag_df_kernel : (const void*)tridiag_kernel;
+  if (cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kTriThreads), args, smem, s) != cudaSuccess)
     return -2;
   count_launch();
   return 0;
@@ -731,7 +1032,7 @@ void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w, const TcWor
 
 int symmetric_eig(cudaStream_t s, int n, const double* F, double* eps, double* Q, EigWork& w,
                   int* status, int sm_count) {
-  int rc = eig_tridiagonalize(s, n, F, w, status, sm_count);
+  int rc = eig_tridiagonalize(s, n, F, w, status, sm_count, false);
   if (rc) return rc;
   eig_bisect(s, n, eps, w);
   eig_vectors(s, n, eps, Q, w);

@@ -53,7 +53,7 @@ struct EigWork {
   double *A;            // n x n copy of the input (overwritten)
   double *Vst;          // n x n Householder vectors (row k = v_k)
   double *d, *e, *e2, *tau;
-  double *pbuf;         // 2 x n
+  double *pbuf;         // 3 x n
   double *lu;           // 5 x n x n inverse-iteration workspace
   double *Tm, *Gm, *Wt, *Wt2;  // back-transform panels
   unsigned* bar;        // 2 words grid barrier
@@ -64,7 +64,9 @@ size_t eig_work_bytes(int n);
 void eig_work_bind(EigWork& w, void* base, int n);
 // F (n x n symmetric, row-major) -> eps ascending, Q (eigenvectors as columns),
 // in three stages (tridiagonalise; tridiagonal eigenpairs into Q; back-transform Q)
-int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* status, int sm_count);
+// df: double-float arithmetic on the FP32 pipe (mixed path), else FP64
+int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* status, int sm_count,
+                       bool df);
 // Share of the device, in thousandths of an SM, that the cooperative
 // tridiagonalisation grid of size n occupies while resident (blocks divided by
 // blocks per SM).  Grids that run concurrently must sum to <= 1000 x SMs.
