@@ -277,10 +277,10 @@ static int eig(sim_handle* h) {
   phase_end(h);
   if (st != 0) return fail(SIM_EINTERNAL, "tridiagonalisation launch failed (code " + std::to_string(st) + ")");
   phase_begin(h, PH_BISECT);
-  eig_bisect(h->stream, h->n, h->eps, h->ew, 1e-12);
+  eig_bisect(h->stream, h->n, h->eps, h->ew, 1e-12, mixed(h));
   phase_end(h);
   phase_begin(h, PH_TRIEIG);
-  eig_vectors(h->stream, h->n, h->eps, h->Q, h->ew);
+  eig_vectors(h->stream, h->n, h->eps, h->Q, h->ew, mixed(h));
   phase_end(h);
   phase_begin(h, PH_BACKTR);
   eig_backtransform(h->stream, h->n, h->Q, h->ew, mixed(h) ? &h->tw : nullptr);

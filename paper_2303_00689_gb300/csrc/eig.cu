@@ -272,6 +272,12 @@ __device__ __forceinline__ dfl ldcg_df(const dfl* p) {
   return dfl{v.x, v.y};
 }
 
+// read-only data of this launch (written by an earlier one): cached loads
+__device__ __forceinline__ dfl ldg_df(const dfl* p) {
+  const float2 v = __ldg((const float2*)p);
+  return dfl{v.x, v.y};
+}
+
 // every thread gets the sum of the warps' partials (written to scratch[warp]
 // by lane 0 before the call); one CTA barrier
 __device__ __forceinline__ dfl df_sum_partials(const dfl* scratch, int nw) {
@@ -455,17 +461,20 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_df_kernel(int n, dfl* __r
 // Gershgorin interval, squared off-diagonals, pivmin; one block
 __global__ void gersh_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
                              double* __restrict__ e2, double* __restrict__ scal, float* __restrict__ df,
-                             float* __restrict__ e2f) {
+                             float* __restrict__ e2f, dfl* __restrict__ d_dfl, dfl* __restrict__ e2_dfl) {
   double lo = 1e300, hi = -1e300, em = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double r = 0.0;
     df[i] = (float)d[i];                 // FP32 copies for the coarse phase (no per-step conversions)
     e2f[i] = 0.0f;
+    d_dfl[i] = df_from_double(d[i]);     // double-float copies for the multisection (mixed path)
+    e2_dfl[i] = dfl{0.0f, 0.0f};
     if (i > 0) r += fabs(e[i - 1]);
     if (i < n - 1) {
       r += fabs(e[i]);
       e2[i] = e[i] * e[i];
       e2f[i] = (float)e2[i];
+      e2_dfl[i] = df_from_double(e2[i]);
       em = fmax(em, e[i] * e[i]);
     }
     lo = fmin(lo, d[i] - r);
@@ -579,6 +588,64 @@ __global__ void bisect_kernel(int n, const double* __restrict__ d, const double*
     if (sturm_count(n, d, e2, mid, pivmin) > i) hi = mid; else lo = mid;
   }
   ev[i] = 0.5 * (lo + hi);
+}
+
+// Mixed path: eigenvalue i by multisection in double-float arithmetic.  A
+// group of kMsLanes lanes evaluates the Sturm count at kMsLanes interior
+// points of the current interval, which shrinks (kMsLanes + 1)-fold per round;
+// every group starts from the Gershgorin interval, so all groups take the same
+// number of rounds.  The count is the product form of sturm_count on the FP32
+// pipe (about 48-bit arithmetic), kept in range by exact power-of-two scaling.
+constexpr int kMsLanes = 8;
+
+__device__ __forceinline__ int sturm_count_df(int n, const dfl* __restrict__ d, const dfl* __restrict__ e2,
+                                              dfl x) {
+  dfl pm = {1.0f, 0.0f};
+  dfl p = df_sub(ldg_df(d), x);
+  int sp = (p.hi < 0.0f || p.hi == 0.0f) ? 1 : 0;        // zero counts as negative
+  int c = sp;
+#pragma unroll 4
+  for (int j = 1; j < n; ++j) {
+    const dfl dj = ldg_df(d + j), ej = ldg_df(e2 + j - 1);
+    const dfl pn = df_sub(df_mul(df_sub(dj, x), p), df_mul(ej, pm));
+    const int sn = (pn.hi == 0.0f) ? (sp ^ 1) : (int)(__float_as_uint(pn.hi) >> 31);
+    c += sn ^ sp;
+    sp = sn;
+    // keep |p| within [2^-32, 2^32] (both p and pm scale by the same power of two)
+    const int ex = (int)((__float_as_uint(pn.hi) >> 23) & 0xFF);
+    const float sc = (ex > 127 + 32) ? 0x1p-64f : ((ex < 127 - 32) ? 0x1p+64f : 1.0f);
+    pm = dfl{KX_FMUL(p.hi, sc), KX_FMUL(p.lo, sc)};
+    p = dfl{KX_FMUL(pn.hi, sc), KX_FMUL(pn.lo, sc)};
+  }
+  return c;
+}
+
+__global__ void bisect_df_kernel(int n, const dfl* __restrict__ d, const dfl* __restrict__ e2,
+                                 const double* __restrict__ scal, double rel_tol, double* __restrict__ ev) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / kMsLanes;                 // eigenvalue of this group
+  const int m = t % kMsLanes;                 // point m + 1 of the group
+  const int gbase = (threadIdx.x & 31) & ~(kMsLanes - 1);
+  const bool live = i < n;                    // whole groups are live or not (n * kMsLanes threads)
+  const double glo = scal[0], ghi = scal[1], pivmin = scal[3];
+  double lo = glo, hi = ghi;
+  const double tol = fmax(2.0 * kEps * fmax(fabs(glo), fabs(ghi)), rel_tol * fmax(1.0, scal[2])) + pivmin;
+  int rounds = 0;
+  for (double w = ghi - glo; w > tol && rounds < 64; w /= (double)(kMsLanes + 1)) ++rounds;
+  for (int r = 0; r < rounds; ++r) {
+    const double h = (hi - lo) / (double)(kMsLanes + 1);
+    const double x = lo + (double)(m + 1) * h;
+    const bool above = live && sturm_count_df(n, d, e2, df_from_double(x)) > i;
+    const unsigned bal = __ballot_sync(0xffffffffu, above);
+    const unsigned g = (bal >> gbase) & ((1u << kMsLanes) - 1u);
+    // counts grow with x: the first point with count > i is the new upper end
+    const int f = g ? (__ffs(g) - 1) : kMsLanes;      // 0-based point index, kMsLanes: none
+    const double nlo = (f == 0) ? lo : lo + (double)f * h;
+    const double nhi = (f == kMsLanes) ? hi : lo + (double)(f + 1) * h;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (live && m == 0) ev[i] = 0.5 * (lo + hi);
 }
 
 __global__ void cluster_kernel(int n, const double* __restrict__ ev, const double* __restrict__ scal,
@@ -740,6 +807,168 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
       for (int r = 0; r < n; ++r) ZC(r, j) *= s;
     }
   }
+#undef LU
+#undef ZC
+}
+
+// Mixed path: the same inverse iteration in double-float arithmetic.  The LU
+// factors and the iterates are held as (hi, lo) pairs in the same workspace
+// (the iterates in Q, converted to FP64 at the end); one reciprocal per row
+// from the FP32 estimate and one Newton step; the pivot floor and the shift
+// separation use the double-float unit 2^-46 |T| instead of the FP64 epsilon.
+__device__ __forceinline__ dfl df_recip(dfl a) {
+  const float r0 = 1.0f / a.hi;
+  const dfl r = dfl{r0, 0.0f};
+  const dfl one_minus = df_sub(dfl{1.0f, 0.0f}, df_mul(a, r));   // 1 - a r0
+  return df_add(r, df_mul(r, one_minus));
+}
+__device__ __forceinline__ float df_abs_hi(dfl a) { return fabsf(a.hi); }
+
+__global__ void invit_df_kernel(int n, const dfl* __restrict__ d, const double* __restrict__ e,
+                                const double* __restrict__ ev, const double* __restrict__ scal,
+                                const int* __restrict__ clus, dfl* __restrict__ lu,
+                                double* __restrict__ Zout) {
+  int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= n || !clus[L]) return;
+  int end = L + 1;
+  while (end < n && !clus[end]) ++end;
+  const double tn = fmax(scal[2], 1e-300);
+  const double tiny_d = 0x1p-46 * tn;
+  const dfl tiny = df_from_double(tiny_d);
+  const size_t nn = (size_t)n * n;
+  dfl* __restrict__ dl = lu + 0 * nn;
+  dfl* __restrict__ rdd = lu + 1 * nn;   // reciprocal pivots
+  dfl* __restrict__ du = lu + 2 * nn;
+  dfl* __restrict__ du2 = lu + 3 * nn;
+  int* __restrict__ pv = (int*)(lu + 4 * nn);
+  dfl* __restrict__ Z = (dfl*)Zout;      // iterates in place of the FP64 output
+#define LU(a, r) a[(size_t)(r) * n + L]
+#define ZC(r, c) Z[(size_t)(r) * n + (c)]
+  double prevlam = 0.0;
+  for (int j = L; j < end; ++j) {
+    double lamd = ev[j];
+    if (j > L && lamd - prevlam < 10.0 * tiny_d) lamd = prevlam + 10.0 * tiny_d;
+    prevlam = lamd;
+    if (n == 1) { ZC(0, j) = dfl{1.0f, 0.0f}; continue; }
+    const dfl lam = df_from_double(lamd);
+    // LU of T - lam I with partial pivoting; a, u: pivot-row diagonal and superdiagonal
+    dfl a = df_sub(ldg_df(d), lam), u = df_from_double(e[0]);
+    for (int r = 0; r < n - 1; ++r) {
+      const dfl b = df_from_double(e[r]);
+      const dfl dn = df_sub(ldg_df(d + r + 1), lam);
+      const dfl un = (r < n - 2) ? df_from_double(e[r + 1]) : dfl{0.0f, 0.0f};
+      if (df_abs_hi(a) >= df_abs_hi(b)) {
+        LU(pv, r) = 0;
+        if (df_abs_hi(a) < tiny.hi) a = (a.hi >= 0.0f) ? tiny : df_neg(tiny);
+        const dfl ra = df_recip(a);
+        const dfl f = df_mul(b, ra);
+        LU(dl, r) = f;
+        LU(rdd, r) = ra;
+        LU(du, r) = u;
+        LU(du2, r) = dfl{0.0f, 0.0f};
+        a = df_sub(dn, df_mul(f, u));
+        u = un;
+      } else {
+        LU(pv, r) = 1;
+        const dfl rb = df_recip(b);
+        const dfl f = df_mul(a, rb);
+        LU(rdd, r) = rb;
+        LU(dl, r) = f;
+        LU(du, r) = dn;
+        const dfl na = df_sub(u, df_mul(f, dn));
+        if (r < n - 2) {
+          LU(du2, r) = un;
+          u = df_neg(df_mul(f, un));
+        } else {
+          LU(du2, r) = dfl{0.0f, 0.0f};
+        }
+        a = na;
+      }
+    }
+    if (df_abs_hi(a) < tiny.hi) a = (a.hi >= 0.0f) ? tiny : df_neg(tiny);
+    LU(rdd, n - 1) = df_recip(a);
+    for (int r = 0; r < n; ++r) ZC(r, j) = df_from_double(start_value(r, j));
+    for (int it = 0; it < 2; ++it) {
+      // forward (L with pivots)
+      dfl cur = ZC(0, j);
+      for (int r0 = 0; r0 < n - 1; r0 += kIvB) {
+        dfl nx[kIvB], fv[kIvB];
+        int pf[kIvB];
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 + q;
+          if (r < n - 1) { nx[q] = ZC(r + 1, j); fv[q] = LU(dl, r); pf[q] = LU(pv, r); }
+        }
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 + q;
+          if (r < n - 1) {
+            if (pf[q] == 0) {
+              ZC(r, j) = cur;
+              cur = df_sub(nx[q], df_mul(fv[q], cur));
+            } else {
+              ZC(r, j) = nx[q];
+              cur = df_sub(cur, df_mul(fv[q], nx[q]));
+            }
+          }
+        }
+      }
+      // backward (U, three diagonals, reciprocal pivots)
+      dfl z2 = df_mul(cur, LU(rdd, n - 1));
+      ZC(n - 1, j) = z2;
+      dfl z1 = z2;
+      if (n > 1) {
+        z1 = df_mul(df_sub(ZC(n - 2, j), df_mul(LU(du, n - 2), z2)), LU(rdd, n - 2));
+        ZC(n - 2, j) = z1;
+      }
+      for (int r0 = n - 3; r0 >= 0; r0 -= kIvB) {
+        dfl zv[kIvB], uv[kIvB], u2[kIvB], rv[kIvB];
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 - q;
+          if (r >= 0) { zv[q] = ZC(r, j); uv[q] = LU(du, r); u2[q] = LU(du2, r); rv[q] = LU(rdd, r); }
+        }
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 - q;
+          if (r >= 0) {
+            const dfl x = df_mul(df_sub(df_sub(zv[q], df_mul(uv[q], z1)), df_mul(u2[q], z2)), rv[q]);
+            ZC(r, j) = x;
+            z2 = z1;
+            z1 = x;
+          }
+        }
+      }
+      // scale, re-orthogonalise within the cluster, normalise
+      float mx = 0.0f;
+#pragma unroll 8
+      for (int r = 0; r < n; ++r) mx = fmaxf(mx, df_abs_hi(ZC(r, j)));
+      dfl sc = (mx > 0.0f) ? df_recip(dfl{mx, 0.0f}) : dfl{1.0f, 0.0f};
+#pragma unroll 8
+      for (int r = 0; r < n; ++r) ZC(r, j) = df_mul(ZC(r, j), sc);
+      for (int c = L; c < j; ++c) {
+        dfl dot = {0.0f, 0.0f};
+#pragma unroll 8
+        for (int r = 0; r < n; ++r) df_acc_mul(dot, ZC(r, c), ZC(r, j));
+        dot = df_norm(dot);
+#pragma unroll 8
+        for (int r = 0; r < n; ++r) ZC(r, j) = df_sub(ZC(r, j), df_mul(dot, ZC(r, c)));
+      }
+      dfl nrm = {0.0f, 0.0f};
+#pragma unroll 8
+      for (int r = 0; r < n; ++r) df_acc_mul(nrm, ZC(r, j), ZC(r, j));
+      const double nd = ::sqrt(df_to_double(df_norm(nrm)));
+      sc = (nd > 0.0) ? df_from_double(1.0 / nd) : dfl{0.0f, 0.0f};
+#pragma unroll 8
+      for (int r = 0; r < n; ++r) ZC(r, j) = df_mul(ZC(r, j), sc);
+    }
+  }
+  // FP64 output (same slots, same thread)
+  for (int j = L; j < end; ++j)
+    for (int r = 0; r < n; ++r) {
+      const dfl z = ZC(r, j);
+      Zout[(size_t)r * n + j] = df_to_double(z);
+    }
 #undef LU
 #undef ZC
 }
@@ -908,24 +1137,36 @@ int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* 
   return 0;
 }
 
-void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w, double rel_tol) {
+void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w, double rel_tol, bool df_path) {
   if (n <= 0) return;
   // 2. eigenvalues
-  // pbuf (2n doubles, free after the tridiagonalisation) holds the FP32 copies
+  // pbuf (3n doubles, free after the tridiagonalisation) holds the FP32 and double-float copies
   float* df = (float*)w.pbuf;
   float* e2f = df + n;
-  gersh_kernel<<<1, 1024, 0, s>>>(n, w.d, w.e, w.e2, w.scal, df, e2f);
+  dfl* d_dfl = (dfl*)(w.pbuf + n);
+  dfl* e2_dfl = d_dfl + n;
+  gersh_kernel<<<1, 1024, 0, s>>>(n, w.d, w.e, w.e2, w.scal, df, e2f, d_dfl, e2_dfl);
   count_launch();
-  bisect_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e2, w.scal, df, e2f, rel_tol, eps);   // spread over all SMs
+  if (df_path) {
+    const long long thr = (long long)n * kMsLanes;
+    bisect_df_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(n, d_dfl, e2_dfl, w.scal, rel_tol, eps);
+  } else {
+    bisect_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e2, w.scal, df, e2f, rel_tol, eps);   // spread over all SMs
+  }
   count_launch();
 }
 
-void eig_vectors(cudaStream_t s, int n, const double* eps, double* Q, EigWork& w) {
+void eig_vectors(cudaStream_t s, int n, const double* eps, double* Q, EigWork& w, bool df_path) {
   if (n <= 0) return;
   // 3. eigenvectors of the tridiagonal matrix
   cluster_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, eps, w.scal, w.clus);
   count_launch();
-  invit_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e, eps, w.scal, w.clus, w.lu, Q);
+  if (df_path) {
+    const dfl* d_dfl = (const dfl*)(w.pbuf + n);     // written by eig_bisect
+    invit_df_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, d_dfl, w.e, eps, w.scal, w.clus, (dfl*)w.lu, Q);
+  } else {
+    invit_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e, eps, w.scal, w.clus, w.lu, Q);
+  }
   count_launch();
 }
 
@@ -1034,8 +1275,8 @@ int symmetric_eig(cudaStream_t s, int n, const double* F, double* eps, double* Q
                   int* status, int sm_count) {
   int rc = eig_tridiagonalize(s, n, F, w, status, sm_count, false);
   if (rc) return rc;
-  eig_bisect(s, n, eps, w);
-  eig_vectors(s, n, eps, Q, w);
+  eig_bisect(s, n, eps, w, 1e-12, false);
+  eig_vectors(s, n, eps, Q, w, false);
   eig_backtransform(s, n, Q, w, nullptr);
   return 0;
 }

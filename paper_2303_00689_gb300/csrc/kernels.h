@@ -72,8 +72,10 @@ int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* 
 // blocks per SM).  Grids that run concurrently must sum to <= 1000 x SMs.
 int eig_tridiag_weight(int n, int sm_count);
 // rel_tol: eigenvalues to rel_tol x max(1, ||T||) (1e-12 FP64 path, 1e-9 mixed path)
-void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w, double rel_tol = 1e-12);  // to rel_tol x ||T||                       // eigenvalues
-void eig_vectors(cudaStream_t s, int n, const double* eps, double* Q, EigWork& w);     // tridiagonal vectors
+// eigenvalues to rel_tol x ||T||; df_path: double-float multisection (mixed path), else FP64 bisection
+void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w, double rel_tol, bool df_path);
+// tridiagonal eigenvectors by inverse iteration; df_path: double-float arithmetic (mixed path)
+void eig_vectors(cudaStream_t s, int n, const double* eps, double* Q, EigWork& w, bool df_path);
 struct TcWork;
 // tw != nullptr: the large products run on the tensor cores (mixed path)
 void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork* tw);
