@@ -92,6 +92,21 @@ __host__ __device__ __forceinline__ void df_acc(dfl& acc, dfl a) {
 }
 __host__ __device__ __forceinline__ dfl df_norm(dfl a) { return df_two_sum(a.hi, a.lo); }
 
+// 1 / a: FP32 estimate and one Newton step in double-float (a.hi != 0)
+__host__ __device__ __forceinline__ dfl df_recip(dfl a) {
+  const float r0 = 1.0f / a.hi;
+  const dfl r = dfl{r0, 0.0f};
+  const dfl one_minus = df_sub(dfl{1.0f, 0.0f}, df_mul(a, r));   // 1 - a r0
+  return df_add(r, df_mul(r, one_minus));
+}
+// sqrt(a), a >= 0: FP32 estimate s0 and one Newton correction (a - s0^2) / (2 s0)
+__host__ __device__ __forceinline__ dfl df_sqrt(dfl a) {
+  if (!(a.hi > 0.0f)) return dfl{0.0f, 0.0f};
+  const float s0 = sqrtf(a.hi);
+  const dfl e = df_sub(a, df_mul(dfl{s0, 0.0f}, dfl{s0, 0.0f}));
+  return df_fast_two_sum(s0, KX_FMUL(e.hi, 0.5f / s0));
+}
+
 // x - u1 * w1 - u2 * w2 (the rank-2 update of one matrix element)
 __host__ __device__ __forceinline__ dfl df_rank2(dfl x, dfl u1, dfl w1, dfl u2, dfl w2) {
   float p1 = KX_FMUL(u1.hi, w1.hi);

@@ -243,21 +243,26 @@ __global__ void to_df_kernel(size_t len, const double* __restrict__ x, dfl* __re
   if (i < len) y[i] = df_from_double(x[i]);
 }
 
-// Same reduction as tridiag_kernel (rows dealt round-robin, lazy rank-2 update
-// fused with the matrix-vector product, one grid barrier per column), with
-// the per-column critical path shortened for a kernel that is latency- rather
-// than FP64-bound:
+// Same reduction as tridiag_kernel (lazy rank-2 update fused with the
+// matrix-vector product, one grid barrier per column), with the per-column
+// critical path shortened for a kernel that is latency- rather than FP64-bound:
 //  * after the barrier every block reads p_{k-1} and row k in one pass, forms
 //    w_{k-1} = p - (tau/2)(p.v)v and the updated row k (x = row k of A_k);
 //  * the matrix-vector product uses the unscaled x (x_{k+1} = x_1) and
 //    keeps a_{i,k+1}, so it need not wait for beta, tau and the scale, which
-//    thread 0 computes in FP64 meanwhile:
+//    thread 0 forms meanwhile:
 //    p_i = tau scale (sum_j a_ij x_j - beta a_{i,k+1}) since v = scale (x - beta e_{k+1});
-//  * block reductions use one CTA barrier each.
-// Shared memory: two reflector buffers (ping-pong: v_{k-1} and x_k / v_k),
-// w (holding p_{k-1} until w is formed) and reduction scratch.
+//  * a block's rows (i = k+1+b+rG) are cut into segments of kDfSeg columns and
+//    the (row, segment) items dealt over the warps, so the warps stay balanced
+//    while the trailing matrix shrinks; each lane issues the loads of its item
+//    before the arithmetic;
+//  * block reductions take one CTA barrier each.
+// Shared memory: PW[j] = (v_{k-1}, w_{k-1}) as one 16-byte pair (during the
+// first passes it holds row k and p_{k-1}), VC[j] = x_k, then v_k, plus
+// reduction scratch and the (row, segment) partial sums.
 constexpr int kDfRed = 32;
 constexpr int kDfSeg = 256;           // columns per (row, segment) work item: 8 per lane
+constexpr int kDfPer = kDfSeg / 32;
 // rows per block at the first column, for a grid of G blocks
 static int tridiag_df_rmax(int n, int G) { return (n - 1 + G - 1) / G; }
 static size_t tridiag_smem_df(int n, int G) {
@@ -271,20 +276,29 @@ __device__ __forceinline__ dfl ldcg_df(const dfl* p) {
   const float2 v = __ldcg((const float2*)p);
   return dfl{v.x, v.y};
 }
-
 // read-only data of this launch (written by an earlier one): cached loads
 __device__ __forceinline__ dfl ldg_df(const dfl* p) {
   const float2 v = __ldg((const float2*)p);
   return dfl{v.x, v.y};
 }
 
-// every thread gets the sum of the warps' partials (written to scratch[warp]
-// by lane 0 before the call); one CTA barrier
-__device__ __forceinline__ dfl df_sum_partials(const dfl* scratch, int nw) {
-  dfl t = {0.0f, 0.0f};
-  for (int w = 0; w < nw; ++w) t = df_add(t, scratch[w]);
-  return t;
+// every thread gets the sum of the kTriThreads / 32 warp partials (written to
+// scratch[warp] by lane 0 before a CTA barrier), added as a pairwise tree
+__device__ __forceinline__ dfl df_sum_partials(const dfl* scratch) {
+  constexpr int NW = kTriThreads / 32;
+  dfl t[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) t[w] = scratch[w];
+#pragma unroll
+  for (int st = 1; st < NW; st <<= 1)
+#pragma unroll
+    for (int w = 0; w + st < NW; w += 2 * st) t[w] = df_add(t[w], t[w + st]);
+  return t[0];
 }
+
+__device__ __forceinline__ dfl lo2(float4 a) { return dfl{a.x, a.y}; }
+__device__ __forceinline__ dfl hi2(float4 a) { return dfl{a.z, a.w}; }
+__device__ __forceinline__ float4 pack4(dfl a, dfl b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
 
 __global__ void __launch_bounds__(kTriThreads) tridiag_df_kernel(int n, dfl* __restrict__ A,
                                                                  double* __restrict__ Vst,
@@ -293,20 +307,18 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_df_kernel(int n, dfl* __r
                                                                  double* __restrict__ tau,
                                                                  dfl* __restrict__ pbuf,
                                                                  unsigned* bar, int* status, int rmax) {
-  extern __shared__ double sm[];
-  dfl* buf0 = (dfl*)sm;
-  dfl* buf1 = buf0 + n;
-  dfl* wp = buf0 + 2 * n;            // p_{k-1}, then w_{k-1}
-  dfl* redA = buf0 + 3 * n;          // partials of p.v
-  dfl* redB = redA + kDfRed;         // partials of sigma
-  dfl* ak1s = redB + kDfRed;         // a_{i,k+1} of the block's rows (rmax)
-  dfl* part = ak1s + rmax;           // (row, segment) partial sums (rmax x smax)
-  __shared__ double s_par[4];        // beta, tau, scale, tau * scale
-  __shared__ dfl s_df[3];            // beta, tau * scale, tau as double-float
+  extern __shared__ float4 sm4[];
+  float4* PW = sm4;                          // n pairs
+  dfl* VC = (dfl*)(sm4 + n);                 // n
+  dfl* redA = VC + n;                        // partials of p.v
+  dfl* redB = redA + kDfRed;                 // partials of sigma
+  dfl* ak1s = redB + kDfRed;                 // a_{i,k+1} of the block's rows (rmax)
+  dfl* part = ak1s + rmax;                   // (row, segment) partial sums (rmax x smax)
+  __shared__ dfl s_df[4];                    // beta, tau * scale, tau, scale
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int T = blockDim.x, nw = T >> 5;
+  constexpr int T = kTriThreads, NW = kTriThreads / 32;
   const int G = gridDim.x;
-  dfl tau_prev = {0.0f, 0.0f};       // tau_{k-1}
+  dfl tau_prev = {0.0f, 0.0f};               // tau_{k-1}
   if (n == 1) {
     if (blockIdx.x == 0 && tid == 0) d[0] = df_to_double(A[0]);
     return;
@@ -314,43 +326,45 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_df_kernel(int n, dfl* __r
   for (int k = 0;; ++k) {
     const bool prev = k > 0;
     const bool last = (k == n - 2);
-    dfl* vpv = ((k + 1) & 1) ? buf1 : buf0;   // v_{k-1}, valid for indices >= k
-    dfl* vcv = (k & 1) ? buf1 : buf0;         // x_k, then v_k
     const dfl* pbp = pbuf + (size_t)((k + 1) & 1) * n;   // p_{k-1}
-    // pass 1: p_{k-1} and row k in one sweep of loads; partial p.v
+    // pass 1: row k and p_{k-1} in one sweep of loads (kept in PW); partial p.v
     dfl loc = {0.0f, 0.0f};
+#pragma unroll 4
     for (int j = k + tid; j < n; j += T) {
-      vcv[j] = ldcg_df(A + (size_t)k * n + j);
+      const dfl a = ldcg_df(A + (size_t)k * n + j);
+      dfl p = {0.0f, 0.0f};
       if (prev) {
-        const dfl p = ldcg_df(pbp + j);
-        wp[j] = p;
-        df_acc_mul(loc, p, vpv[j]);
+        p = ldcg_df(pbp + j);
+        df_acc_mul(loc, p, VC[j]);           // VC = v_{k-1}
       }
+      PW[j] = pack4(a, p);
     }
     dfl wk = {0.0f, 0.0f}, vk = {0.0f, 0.0f}, coef = {0.0f, 0.0f};
     if (prev) {
       loc = df_warp_sum(df_norm(loc));
       if (lane == 0) redA[wid] = loc;
       __syncthreads();
-      const dfl pv = df_sum_partials(redA, nw);
+      const dfl pv = df_sum_partials(redA);
       coef = df_mul(df_mul(dfl{0.5f, 0.0f}, tau_prev), pv);
-      vk = vpv[k];
-      wk = df_sub(wp[k], df_mul(coef, vk));      // wp[k] is never overwritten below
+      vk = VC[k];
+      wk = df_sub(hi2(PW[k]), df_mul(coef, vk));   // PW[k] is not overwritten below
     }
     // pass 2: w_{k-1} and the updated row k; sigma = sum_{j >= k+2} x_j^2
     dfl sig = {0.0f, 0.0f};
     dfl dk = {0.0f, 0.0f};
     for (int j = k + tid; j < n; j += T) {
-      dfl x = vcv[j];
+      const float4 ap = PW[j];
+      dfl x = lo2(ap);
       if (prev) {
-        const dfl wj = (j == k) ? wk : df_sub(wp[j], df_mul(coef, vpv[j]));
-        if (j > k) wp[j] = wj;
-        x = df_rank2(x, vk, wj, wk, vpv[j]);
+        const dfl vj = VC[j];
+        const dfl wj = (j == k) ? wk : df_sub(hi2(ap), df_mul(coef, vj));
+        x = df_rank2(x, vk, wj, wk, vj);
+        if (j > k) PW[j] = pack4(vj, wj);
       }
       if (j == k) {
         dk = x;
       } else {
-        vcv[j] = x;
+        VC[j] = x;
         if (j >= k + 2) df_acc_mul(sig, x, x);
       }
     }
@@ -359,9 +373,9 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_df_kernel(int n, dfl* __r
       if (blockIdx.x == 0 && tid == 0) {
         const int b = n - 1;
         dfl abb = ldcg_df(A + (size_t)b * n + b);
-        if (prev) abb = df_rank2(abb, vpv[b], wp[b], wp[b], vpv[b]);
+        if (prev) abb = df_rank2(abb, lo2(PW[b]), hi2(PW[b]), hi2(PW[b]), lo2(PW[b]));
         d[n - 2] = df_to_double(dk);
-        e[n - 2] = df_to_double(vcv[b]);
+        e[n - 2] = df_to_double(VC[b]);
         d[b] = df_to_double(abb);
       }
       return;
@@ -369,89 +383,117 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_df_kernel(int n, dfl* __r
     sig = df_warp_sum(df_norm(sig));
     if (lane == 0) redB[wid] = sig;
     __syncthreads();
-    // thread 0: reflector scalars in FP64 while the other warps start the product
+    // thread 0: reflector scalars (double-float: GB300's FP64 divide and square
+    // root are long dependent chains) while the other warps start the product
     if (tid == 0) {
-      const double sigma = df_to_double(df_sum_partials(redB, nw));
-      const double x1d = df_to_double(vcv[k + 1]);
-      double beta, t, scale;
-      if (sigma == 0.0) {
-        beta = x1d; t = 0.0; scale = 0.0;
+      const dfl sigma = df_sum_partials(redB);
+      const dfl x1 = VC[k + 1];
+      dfl beta, t, scale;
+      if (sigma.hi == 0.0f) {
+        beta = x1; t = dfl{0.0f, 0.0f}; scale = dfl{0.0f, 0.0f};
       } else {
-        double nrm = ::sqrt(x1d * x1d + sigma);
-        beta = (x1d >= 0.0) ? -nrm : nrm;
-        t = (beta - x1d) / beta;
-        scale = 1.0 / (x1d - beta);
+        const dfl nrm = df_sqrt(df_add(df_mul(x1, x1), sigma));
+        beta = (x1.hi >= 0.0f) ? df_neg(nrm) : nrm;
+        t = df_mul(df_sub(beta, x1), df_recip(beta));
+        scale = df_recip(df_sub(x1, beta));
       }
-      s_par[0] = beta; s_par[1] = t; s_par[2] = scale; s_par[3] = t * scale;
-      s_df[0] = df_from_double(beta);
-      s_df[1] = df_from_double(t * scale);
-      s_df[2] = df_from_double(t);
-      if (blockIdx.x == 0) { d[k] = df_to_double(dk); e[k] = beta; tau[k] = t; }
+      s_df[0] = beta;
+      s_df[1] = df_mul(t, scale);
+      s_df[2] = t;
+      s_df[3] = scale;
+      if (blockIdx.x == 0) { d[k] = df_to_double(dk); e[k] = df_to_double(beta); tau[k] = df_to_double(t); }
     }
     // fused: pending rank-2 update (v_{k-1}, w_{k-1}) of rows/cols >= k+1 and
-    // sum_j a_ij x_j.  The block's rows (i = k+1+b+rG) are cut into segments
-    // of kDfSeg columns and the (row, segment) items dealt over the warps, so
-    // the warps stay balanced while the trailing matrix shrinks; every lane
-    // issues all loads of its item before the arithmetic.
+    // sum_j a_ij x_j over (row, segment) items
     const int R = (n - (k + 1) - (int)blockIdx.x + G - 1) / G;
     const int S = (n - (k + 1) + kDfSeg - 1) / kDfSeg;
-    for (int q = wid; q < R * S; q += nw) {
+    for (int q = wid; q < R * S; q += NW) {
       const int r = q / S, sg = q - r * S;
       const int i = k + 1 + (int)blockIdx.x + r * G;
-      dfl* row = A + (size_t)i * n;
+      float2* row = (float2*)(A + (size_t)i * n);
       const int jb = k + 1 + sg * kDfSeg + lane;
-      const int je = min(n, k + 1 + (sg + 1) * kDfSeg);
-      dfl xs[kDfSeg / 32];
+      const bool full = (k + 1 + (sg + 1) * kDfSeg) <= n;
+      dfl a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, first = {0.0f, 0.0f};
+      if (full) {
+        float2 xr[kDfPer];
 #pragma unroll
-      for (int u = 0; u < kDfSeg / 32; ++u) {
-        const int j = jb + 32 * u;
-        xs[u] = (j < je) ? ldcg_df(row + j) : dfl{0.0f, 0.0f};
-      }
-      dfl a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f};
-      if (prev) {
-        const dfl vi = vpv[i], wi = wp[i];
+        for (int u = 0; u < kDfPer; ++u) xr[u] = __ldcg(row + jb + 32 * u);
+        if (prev) {
+          const float4 pwi = PW[i];
+          const dfl vi = lo2(pwi), wi = hi2(pwi);
 #pragma unroll
-        for (int u = 0; u < kDfSeg / 32; ++u) {
-          const int j = jb + 32 * u;
-          if (j < je) {
-            const dfl x = df_rank2(xs[u], vi, wp[j], wi, vpv[j]);
-            row[j] = x;
-            xs[u] = x;
-            if (u & 1) df_acc_mul(a1, x, vcv[j]); else df_acc_mul(a0, x, vcv[j]);
+          for (int u = 0; u < kDfPer; ++u) {
+            const int j = jb + 32 * u;
+            const float4 pw = PW[j];
+            const dfl x = df_rank2(dfl{xr[u].x, xr[u].y}, vi, hi2(pw), wi, lo2(pw));
+            row[j] = make_float2(x.hi, x.lo);
+            if (u == 0) first = x;
+            if (u & 1) df_acc_mul(a1, x, VC[j]); else df_acc_mul(a0, x, VC[j]);
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < kDfPer; ++u) {
+            const int j = jb + 32 * u;
+            const dfl x = dfl{xr[u].x, xr[u].y};
+            if (u == 0) first = x;
+            if (u & 1) df_acc_mul(a1, x, VC[j]); else df_acc_mul(a0, x, VC[j]);
           }
         }
       } else {
+        const int je = n;
+        float2 xr[kDfPer];
 #pragma unroll
-        for (int u = 0; u < kDfSeg / 32; ++u) {
+        for (int u = 0; u < kDfPer; ++u) {
+          const int j = jb + 32 * u;
+          xr[u] = (j < je) ? __ldcg(row + j) : make_float2(0.0f, 0.0f);
+        }
+        const float4 pwi = prev ? PW[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const dfl vi = lo2(pwi), wi = hi2(pwi);
+#pragma unroll
+        for (int u = 0; u < kDfPer; ++u) {
           const int j = jb + 32 * u;
           if (j < je) {
-            if (u & 1) df_acc_mul(a1, xs[u], vcv[j]); else df_acc_mul(a0, xs[u], vcv[j]);
+            dfl x = dfl{xr[u].x, xr[u].y};
+            if (prev) {
+              const float4 pw = PW[j];
+              x = df_rank2(x, vi, hi2(pw), wi, lo2(pw));
+              row[j] = make_float2(x.hi, x.lo);
+            }
+            if (u == 0) first = x;
+            if (u & 1) df_acc_mul(a1, x, VC[j]); else df_acc_mul(a0, x, VC[j]);
           }
         }
       }
-      dfl acc = df_warp_sum(df_add(df_norm(a0), df_norm(a1)));
+      const dfl acc = df_warp_sum(df_add(df_norm(a0), df_norm(a1)));
       if (lane == 0) {
         part[r * S + sg] = acc;
-        if (sg == 0) ak1s[r] = xs[0];      // lane 0, u = 0 is column k+1
+        if (sg == 0) ak1s[r] = first;        // lane 0, u = 0 is column k+1
       }
     }
     __syncthreads();
-    const dfl beta_df = s_df[0], ts_df = s_df[1];
+    const dfl beta_df = s_df[0], ts_df = s_df[1], scale_df = s_df[3];
     tau_prev = s_df[2];
-    const double scale = s_par[2];
-    // p_i = tau scale (sum_j a_ij x_j - beta a_{i,k+1}), segments summed in order
+    // p_i = tau scale (sum_j a_ij x_j - beta a_{i,k+1}), segments summed as a
+    // fixed tree (one warp per row while a row has at most 32 segments)
     dfl* pb = pbuf + (size_t)(k & 1) * n;
-    for (int r = tid; r < R; r += T) {
-      dfl dot = {0.0f, 0.0f};
-      for (int sg = 0; sg < S; ++sg) dot = df_add(dot, part[r * S + sg]);
-      pb[k + 1 + (int)blockIdx.x + r * G] = df_mul(ts_df, df_sub(dot, df_mul(beta_df, ak1s[r])));
+    if (S <= 32) {
+      for (int r = wid; r < R; r += NW) {
+        dfl v = (lane < S) ? part[r * S + lane] : dfl{0.0f, 0.0f};
+        v = df_warp_sum(v);
+        if (lane == 0) pb[k + 1 + (int)blockIdx.x + r * G] = df_mul(ts_df, df_sub(v, df_mul(beta_df, ak1s[r])));
+      }
+    } else {
+      for (int r = tid; r < R; r += T) {
+        dfl* pr = part + r * S;
+        for (int st = 1; st < S; st <<= 1)
+          for (int sg = 0; sg + st < S; sg += 2 * st) pr[sg] = df_add(pr[sg], pr[sg + st]);
+        pb[k + 1 + (int)blockIdx.x + r * G] = df_mul(ts_df, df_sub(pr[0], df_mul(beta_df, ak1s[r])));
+      }
     }
     // v_k = scale x (v_{k+1} = 1); the reflector store row k, spread over blocks
-    const dfl scale_df = df_from_double(scale);
-    for (int j = k + tid; j < n; j += T) {
-      if (j == k) continue;
-      const dfl v = (j == k + 1) ? dfl{1.0f, 0.0f} : df_mul(vcv[j], scale_df);
-      vcv[j] = v;
+    for (int j = k + 1 + tid; j < n; j += T) {
+      const dfl v = (j == k + 1) ? dfl{1.0f, 0.0f} : df_mul(VC[j], scale_df);
+      VC[j] = v;
       if (j % G == (int)blockIdx.x) Vst[(size_t)k * n + j] = df_to_double(v);
     }
     if (!grid_barrier(bar, gridDim.x, status)) return;
@@ -816,12 +858,6 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
 // (the iterates in Q, converted to FP64 at the end); one reciprocal per row
 // from the FP32 estimate and one Newton step; the pivot floor and the shift
 // separation use the double-float unit 2^-46 |T| instead of the FP64 epsilon.
-__device__ __forceinline__ dfl df_recip(dfl a) {
-  const float r0 = 1.0f / a.hi;
-  const dfl r = dfl{r0, 0.0f};
-  const dfl one_minus = df_sub(dfl{1.0f, 0.0f}, df_mul(a, r));   // 1 - a r0
-  return df_add(r, df_mul(r, one_minus));
-}
 __device__ __forceinline__ float df_abs_hi(dfl a) { return fabsf(a.hi); }
 
 __global__ void invit_df_kernel(int n, const dfl* __restrict__ d, const double* __restrict__ e,
