@@ -86,6 +86,39 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
   return s_ok != 0;
 }
 
+// Split-phase grid barrier on a monotonically increasing arrival counter
+// (reset to 0 before the launch): the e-th barrier of a block is passed once
+// the counter reaches e * nblocks.  grid_arrive makes the block's earlier
+// writes visible (CTA barrier, then a release reduction by thread 0), so
+// independent work can run before grid_wait (an acquire load, bounded in wall
+// time like grid_barrier; on expiry kStatusTimeout is set and false returned).
+__device__ __forceinline__ void grid_arrive(unsigned* cnt) {
+  __syncthreads();
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(cnt) : "memory");
+}
+__device__ bool grid_wait(const unsigned* cnt, unsigned target, int* status) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = global_ns();
+    long long it = 0;
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+      if ((int)(v - target) >= 0) break;
+      ++it;
+      if ((it & 63) == 0 && (global_ns() - t0 > kBarrierNs || it > (1LL << 27) ||
+                             ((*(volatile int*)status) & kStatusTimeout))) {
+        atomicOr(status, (int)kStatusTimeout);
+        break;
+      }
+      __nanosleep(16);
+    }
+    s_ok = ((*(volatile int*)status) & kStatusTimeout) ? 0 : 1;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __restrict__ A,
                                                               double* __restrict__ Vst,
                                                               double* __restrict__ d,
@@ -260,9 +293,11 @@ __global__ void to_df_kernel(size_t len, const double* __restrict__ x, dfl* __re
 // Shared memory: PW[j] = (v_{k-1}, w_{k-1}) as one 16-byte pair (during the
 // first passes it holds row k and p_{k-1}), VC[j] = x_k, then v_k, plus
 // reduction scratch and the (row, segment) partial sums.
+constexpr int kTriThreadsDf = 512;    // threads per block of the double-float kernel
 constexpr int kDfRed = 32;
-constexpr int kDfSeg = 256;           // columns per (row, segment) work item: 8 per lane
+constexpr int kDfSeg = 512;           // columns per (row, segment) work item: 16 per lane
 constexpr int kDfPer = kDfSeg / 32;
+static_assert(kTriThreadsDf / 32 <= kDfRed, "one reduction slot per warp");
 // rows per block at the first column, for a grid of G blocks
 static int tridiag_df_rmax(int n, int G) { return (n - 1 + G - 1) / G; }
 static size_t tridiag_smem_df(int n, int G) {
@@ -282,10 +317,10 @@ __device__ __forceinline__ dfl ldg_df(const dfl* p) {
   return dfl{v.x, v.y};
 }
 
-// every thread gets the sum of the kTriThreads / 32 warp partials (written to
+// every thread gets the sum of the kTriThreadsDf / 32 warp partials (written to
 // scratch[warp] by lane 0 before a CTA barrier), added as a pairwise tree
 __device__ __forceinline__ dfl df_sum_partials(const dfl* scratch) {
-  constexpr int NW = kTriThreads / 32;
+  constexpr int NW = kTriThreadsDf / 32;
   dfl t[NW];
 #pragma unroll
   for (int w = 0; w < NW; ++w) t[w] = scratch[w];
@@ -300,7 +335,7 @@ __device__ __forceinline__ dfl lo2(float4 a) { return dfl{a.x, a.y}; }
 __device__ __forceinline__ dfl hi2(float4 a) { return dfl{a.z, a.w}; }
 __device__ __forceinline__ float4 pack4(dfl a, dfl b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
 
-__global__ void __launch_bounds__(kTriThreads) tridiag_df_kernel(int n, dfl* __restrict__ A,
+__global__ void __launch_bounds__(kTriThreadsDf) tridiag_df_kernel(int n, dfl* __restrict__ A,
                                                                  double* __restrict__ Vst,
                                                                  double* __restrict__ d,
                                                                  double* __restrict__ e,
@@ -316,7 +351,7 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_df_kernel(int n, dfl* __r
   dfl* part = ak1s + rmax;                   // (row, segment) partial sums (rmax x smax)
   __shared__ dfl s_df[4];                    // beta, tau * scale, tau, scale
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int T = kTriThreads, NW = kTriThreads / 32;
+  constexpr int T = kTriThreadsDf, NW = kTriThreadsDf / 32;
   const int G = gridDim.x;
   dfl tau_prev = {0.0f, 0.0f};               // tau_{k-1}
   if (n == 1) {
@@ -477,10 +512,15 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_df_kernel(int n, dfl* __r
     // fixed tree (one warp per row while a row has at most 32 segments)
     dfl* pb = pbuf + (size_t)(k & 1) * n;
     if (S <= 32) {
-      for (int r = wid; r < R; r += NW) {
-        dfl v = (lane < S) ? part[r * S + lane] : dfl{0.0f, 0.0f};
-        v = df_warp_sum(v);
-        if (lane == 0) pb[k + 1 + (int)blockIdx.x + r * G] = df_mul(ts_df, df_sub(v, df_mul(beta_df, ak1s[r])));
+      int lpr = 1;                                  // lanes per row: power of two >= S
+      while (lpr < S) lpr <<= 1;
+      const int rpw = 32 / lpr;                     // rows per warp
+      const int sub = lane / lpr, sl = lane - sub * lpr;
+      for (int r0 = wid * rpw; r0 < R; r0 += NW * rpw) {
+        const int r = r0 + sub;
+        dfl v = (r < R && sl < S) ? part[r * S + sl] : dfl{0.0f, 0.0f};
+        for (int o = lpr >> 1; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+        if (r < R && sl == 0) pb[k + 1 + (int)blockIdx.x + r * G] = df_mul(ts_df, df_sub(v, df_mul(beta_df, ak1s[r])));
       }
     } else {
       for (int r = tid; r < R; r += T) {
@@ -490,13 +530,15 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_df_kernel(int n, dfl* __r
         pb[k + 1 + (int)blockIdx.x + r * G] = df_mul(ts_df, df_sub(pr[0], df_mul(beta_df, ak1s[r])));
       }
     }
-    // v_k = scale x (v_{k+1} = 1); the reflector store row k, spread over blocks
+    grid_arrive(bar);
+    // while the other blocks finish: v_k = scale x (v_{k+1} = 1) and the
+    // reflector store row k, spread over blocks
     for (int j = k + 1 + tid; j < n; j += T) {
       const dfl v = (j == k + 1) ? dfl{1.0f, 0.0f} : df_mul(VC[j], scale_df);
       VC[j] = v;
       if (j % G == (int)blockIdx.x) Vst[(size_t)k * n + j] = df_to_double(v);
     }
-    if (!grid_barrier(bar, gridDim.x, status)) return;
+    if (!grid_wait(bar, (unsigned)(k + 1) * (unsigned)G, status)) return;
   }
 }
 
@@ -1131,7 +1173,9 @@ int eig_tridiag_weight(int n, int sm_count) {
     const size_t smem = df ? tridiag_smem_df(n, (int)b) : tridiag_smem(n);
     const void* fn = df ? (const void*)tridiag_df_kernel : (const void*)tridiag_kernel;
     if (!tridiag_smem_attribute(smem, df != 0) ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, kTriThreads, smem) != cudaSuccess || p < 1) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, df ? kTriThreadsDf : kTriThreads, smem) !=
+            cudaSuccess ||
+        p < 1) {
       cudaGetLastError();
       p = 1;
     }
@@ -1167,7 +1211,8 @@ int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* 
   void* args_df[] = {&nn, &A, &V, &d, &e, &t, &pb, &bar, &st, &rmax};
   void** args = df ? args_df : args_fp64;
   const void* fn = df ? (const void*)tridiag_df_kernel : (const void*)tridiag_kernel;
-  if (cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kTriThreads), args, smem, s) != cudaSuccess)
+  if (cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(df ? kTriThreadsDf : kTriThreads), args, smem, s) !=
+      cudaSuccess)
     return -2;
   count_launch();
   return 0;
