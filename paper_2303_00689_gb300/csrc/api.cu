@@ -147,6 +147,8 @@ static int build_elem(const double* v, Elem& e) {
   e.G_ss = v[SIM_P_GSS]; e.G_sp = v[SIM_P_GSP]; e.G_pp = v[SIM_P_GPP]; e.G_p2 = v[SIM_P_GP2];
   e.H_sp = v[SIM_P_HSP];
   e.H_pp = 0.5 * (e.G_pp - e.G_p2);
+  for (int k = 0; k < 2; ++k)
+    e.sto_nrm[k] = std::pow(2.0 * e.zeta[k], e.nprin + 0.5) / std::sqrt(e.nprin == 1 ? 2.0 : 24.0);
   const double kHuge = 1e30;  // vanishing two-electron parameters -> integrals -> 0
   e.rho0 = (e.G_ss > 0.0) ? kE2 / (2.0 * e.G_ss) : kHuge;
   if (e.norb == 1) {

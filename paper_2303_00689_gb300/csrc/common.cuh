@@ -57,12 +57,44 @@ struct Elem {
   double G_ss, G_sp, G_pp, G_p2, H_sp, H_pp;
   double D1, D2;        // multipole lengths (Angstrom)
   double rho0, rho1, rho2;  // additive terms (Angstrom)
+  double sto_nrm[2];    // Slater normalisation (2 zeta)^(n + 1/2) / sqrt((2n)!) for zeta_s, zeta_p
   int norb, nprin;
 };
 
 struct ElemTable {
   Elem e[4];  // H, C, N, O
 };
+
+// ---------------------------------------------------------------------------
+// FP64 reciprocal and inverse square root: an FP32 estimate refined by two
+// Newton-Raphson steps (r <- r + r (1 - x r); y <- y + y (1 - x y^2) / 2),
+// each of which squares the relative error (about 2^-22 -> 2^-44 -> below
+// FP64 rounding).  GB300 runs FP64 division and square root as long dependent
+// sequences on its narrow FP64 pipe; these take 4 and 8 FP64 operations.
+// Arguments must be positive and finite in FP32 (x > 2^-126); beyond the FP32
+// maximum the results are 0, the limit the callers need.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double rcp_nr(double x) {
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y = (double)rsqrtf((float)x);
+  double e = fma(-x * y, y, 1.0);
+  y = fma(0.5 * y, e, y);
+  e = fma(-x * y, y, 1.0);
+  return fma(0.5 * y, e, y);
+}
+KX_HOST_DEVICE double kx_rcp(double x) {
+#if defined(__CUDA_ARCH__)
+  return rcp_nr(x);
+#else
+  return 1.0 / x;
+#endif
+}
 
 // ---------------------------------------------------------------------------
 // forward-mode dual number with three derivative directions
@@ -85,13 +117,13 @@ KX_HOST_DEVICE D3 operator*(D3 a, D3 b) {
 KX_HOST_DEVICE D3 operator*(D3 a, double b) { return D3{a.v * b, a.d0 * b, a.d1 * b, a.d2 * b}; }
 KX_HOST_DEVICE D3 operator*(double b, D3 a) { return a * b; }
 KX_HOST_DEVICE D3 operator/(D3 a, D3 b) {
-  double inv = 1.0 / b.v;
+  double inv = kx_rcp(b.v);
   double q = a.v * inv;
   return D3{q, (a.d0 - q * b.d0) * inv, (a.d1 - q * b.d1) * inv, (a.d2 - q * b.d2) * inv};
 }
-KX_HOST_DEVICE D3 operator/(D3 a, double b) { return a * (1.0 / b); }
+KX_HOST_DEVICE D3 operator/(D3 a, double b) { return a * kx_rcp(b); }
 KX_HOST_DEVICE D3 operator/(double a, D3 b) {
-  double inv = 1.0 / b.v;
+  double inv = kx_rcp(b.v);
   double q = a * inv;
   double s = -q * inv;
   return D3{q, s * b.d0, s * b.d1, s * b.d2};
@@ -100,28 +132,66 @@ KX_HOST_DEVICE D3& operator+=(D3& a, D3 b) { a = a + b; return a; }
 KX_HOST_DEVICE D3& operator-=(D3& a, D3 b) { a = a - b; return a; }
 
 __device__ __forceinline__ D3 sq(D3 a) {
-  double s = ::sqrt(a.v);
-  double h = 0.5 / s;
+  double r = rsqrt_nr(a.v);
+  double s = a.v * r;
+  double h = 0.5 * r;
   return D3{s, a.d0 * h, a.d1 * h, a.d2 * h};
 }
-// 1/sqrt(a) with its derivative -a'/(2 a^{3/2})
+// 1/sqrt(a) with its derivative -a'/(2 a^{3/2}) = -a' r^3 / 2
 __device__ __forceinline__ D3 rsqrt_d(D3 a) {
-  double r = 1.0 / ::sqrt(a.v);
-  double h = -0.5 * r / a.v;
+  double r = rsqrt_nr(a.v);
+  double h = -0.5 * r * r * r;
   return D3{r, a.d0 * h, a.d1 * h, a.d2 * h};
 }
-__device__ __forceinline__ double rsqrt_d(double a) { return 1.0 / ::sqrt(a); }
+__device__ __forceinline__ double rsqrt_d(double a) { return rsqrt_nr(a); }
 __device__ __forceinline__ D3 ex(D3 a) {
   double e = ::exp(a.v);
   return D3{e, a.d0 * e, a.d1 * e, a.d2 * e};
 }
 __device__ __forceinline__ double ex(double a) { return ::exp(a); }
-__device__ __forceinline__ double sq(double a) { return ::sqrt(a); }
+__device__ __forceinline__ double sq(double a) { return a * rsqrt_nr(a); }
 __device__ __forceinline__ double val(double a) { return a; }
 __device__ __forceinline__ double val(D3 a) { return a.v; }
+// forward-mode dual number with one derivative direction (d/dR of the
+// quantities that depend on the pair distance R alone)
+struct D1 {
+  double v, d;
+};
+KX_HOST_DEVICE D1 operator+(D1 a, D1 b) { return D1{a.v + b.v, a.d + b.d}; }
+KX_HOST_DEVICE D1 operator-(D1 a, D1 b) { return D1{a.v - b.v, a.d - b.d}; }
+KX_HOST_DEVICE D1 operator-(D1 a) { return D1{-a.v, -a.d}; }
+KX_HOST_DEVICE D1 operator+(D1 a, double b) { return D1{a.v + b, a.d}; }
+KX_HOST_DEVICE D1 operator+(double b, D1 a) { return D1{a.v + b, a.d}; }
+KX_HOST_DEVICE D1 operator-(D1 a, double b) { return D1{a.v - b, a.d}; }
+KX_HOST_DEVICE D1 operator-(double b, D1 a) { return D1{b - a.v, -a.d}; }
+KX_HOST_DEVICE D1 operator*(D1 a, D1 b) { return D1{a.v * b.v, a.d * b.v + a.v * b.d}; }
+KX_HOST_DEVICE D1 operator*(D1 a, double b) { return D1{a.v * b, a.d * b}; }
+KX_HOST_DEVICE D1 operator*(double b, D1 a) { return D1{a.v * b, a.d * b}; }
+KX_HOST_DEVICE D1 operator/(D1 a, D1 b) {
+  double inv = kx_rcp(b.v);
+  double q = a.v * inv;
+  return D1{q, (a.d - q * b.d) * inv};
+}
+KX_HOST_DEVICE D1 operator/(double a, D1 b) {
+  double inv = kx_rcp(b.v);
+  double q = a * inv;
+  return D1{q, -q * inv * b.d};
+}
+KX_HOST_DEVICE D1& operator+=(D1& a, D1 b) { a = a + b; return a; }
+__device__ __forceinline__ D1 rsqrt_d(D1 a) {
+  double r = rsqrt_nr(a.v);
+  return D1{r, -0.5 * r * r * r * a.d};
+}
+__device__ __forceinline__ D1 ex(D1 a) {
+  double e = ::exp(a.v);
+  return D1{e, a.d * e};
+}
+__device__ __forceinline__ double val(D1 a) { return a.v; }
+
 template <typename T> __device__ __forceinline__ T cst(double v);
 template <> __device__ __forceinline__ double cst<double>(double v) { return v; }
 template <> __device__ __forceinline__ D3 cst<D3>(double v) { return mkd(v); }
+template <> __device__ __forceinline__ D1 cst<D1>(double v) { return D1{v, 0.0}; }
 
 // ---------------------------------------------------------------------------
 // reductions

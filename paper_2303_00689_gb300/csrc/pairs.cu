@@ -98,15 +98,24 @@ __device__ void aux_A(T p, T* A) {
   T e = ex(-p);
   T ip = 1.0 / p;
   A[0] = e * ip;
+#pragma unroll
   for (int k = 1; k < 5; ++k) A[k] = (e + (double)k * A[k - 1]) * ip;
 }
-// B_k(q) = int_{-1}^{1} eta^k e^{-q eta}, k = 0..4
+// B_k(q) = int_{-1}^{1} eta^k e^{-q eta}, k = 0..4.  For |q| < 1 the series
+// sum_m (-q)^m / m! int eta^(k+m) (the loops unroll, so the coefficients are
+// compile-time constants); q = 0 (equal exponents) gives int eta^k directly.
 template <typename T>
 __device__ void aux_B(T q, T* B) {
-  if (fabs(val(q)) < 1.0) {
+  if (val(q) == 0.0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) B[k] = (k & 1) ? cst<T>(0.0) : cst<T>(2.0 / (double)(k + 1));
+  } else if (fabs(val(q)) < 1.0) {
+#pragma unroll
     for (int k = 0; k < 5; ++k) B[k] = cst<T>(0.0);
     T term = cst<T>(1.0);
+#pragma unroll
     for (int m = 0; m < 22; ++m) {
+#pragma unroll
       for (int k = 0; k < 5; ++k)
         if (((k + m) & 1) == 0) B[k] += term * (2.0 / (double)(k + m + 1));
       term = term * (-q) * (1.0 / (double)(m + 1));
@@ -115,6 +124,7 @@ __device__ void aux_B(T q, T* B) {
     T ep = ex(q), em = ex(-q);
     T iq = 1.0 / q;
     B[0] = (ep - em) * iq;
+#pragma unroll
     for (int k = 1; k < 5; ++k) {
       T sgn_ep = (k & 1) ? -ep : ep;
       B[k] = (sgn_ep - em + (double)k * B[k - 1]) * iq;
@@ -122,14 +132,9 @@ __device__ void aux_B(T q, T* B) {
   }
 }
 
-__device__ __forceinline__ double sto_norm(int n, double zeta) {
-  double f2n = (n == 1) ? 2.0 : 24.0;  // (2n)!
-  return pow(2.0 * zeta, n + 0.5) / ::sqrt(f2n);
-}
-
 // overlap of normalised Slater orbitals, B at +R z'; kinds 0 s, 1 sigma, 2 pi
 template <typename T>
-__device__ T sto_overlap(T R, int nA, double zA, int kA, int nB, double zB, int kB) {
+__device__ T sto_overlap(T R, int nA, double zA, double nrmA, int kA, int nB, double zB, double nrmB, int kB) {
   T Rb = R * (1.0 / kBohr);
   T p = Rb * (0.5 * (zA + zB));
   T q = Rb * (0.5 * (zA - zB));
@@ -144,8 +149,7 @@ __device__ T sto_overlap(T R, int nA, double zA, int kA, int nB, double zB, int 
     }
   const double cs = 0.28209479177387814;  // 1/sqrt(4 pi)
   const double cp = 0.48860251190291992;  // sqrt(3/(4 pi))
-  double pref = sto_norm(nA, zA) * sto_norm(nB, zB) * (kA == 0 ? cs : cp) * (kB == 0 ? cs : cp) *
-                c_ovl_phi[kA];
+  double pref = nrmA * nrmB * (kA == 0 ? cs : cp) * (kB == 0 ? cs : cp) * c_ovl_phi[kA];
   T half = Rb * 0.5;
   T pw = cst<T>(1.0);
   for (int k = 0; k < nA + nB + 1; ++k) pw = pw * half;
@@ -159,14 +163,47 @@ template <> __device__ __forceinline__ D3 seed<D3>(double v, int k) {
   return D3{v, k == 0 ? 1.0 : 0.0, k == 1 ? 1.0 : 0.0, k == 2 ? 1.0 : 0.0};
 }
 
+// Quantities that depend on the distance R alone (local-frame integrals,
+// local overlaps, core-core energy) are evaluated with one derivative,
+// d/dR, and promoted to the pair-vector derivatives by the chain rule
+// d/dd_k = u_k d/dR (u = d / R): a quarter of the dual-number work.
+template <typename T> struct Radial;
+template <> struct Radial<double> {
+  typedef double type;
+  __device__ static double seed(double R) { return R; }
+  __device__ static double promote(double a, const double*) { return a; }
+};
+template <> struct Radial<D3> {
+  typedef D1 type;
+  __device__ static D1 seed(double R) { return D1{R, 1.0}; }
+  __device__ static D3 promote(D1 a, const double* u) { return D3{a.v, a.d * u[0], a.d * u[1], a.d * u[2]}; }
+};
+
+// mirror image of an orbital product under x <-> y (a reflection that maps
+// the local frame onto itself): sx <-> sy, xx <-> yy, xz <-> yz
+__device__ __forceinline__ int mirror_xy(int p) {
+  switch (p) {
+    case 1: return 2;
+    case 2: return 1;
+    case 4: return 5;
+    case 5: return 4;
+    case 8: return 9;
+    case 9: return 8;
+    default: return p;
+  }
+}
+
 template <typename T>
 __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T* Wout /*100*/,
                            T* Sout /*16*/, T* Eout) {
+  typedef typename Radial<T>::type Tr;
   T d[3];
   for (int k = 0; k < 3; ++k) d[k] = seed<T>(dvec[k], k);
   T R = sq(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
   T iR = 1.0 / R;
   T u[3] = {d[0] * iR, d[1] * iR, d[2] * iR};
+  const double uv[3] = {val(u[0]), val(u[1]), val(u[2])};
+  const Tr Rr = Radial<T>::seed(val(R));
   // reference axis least aligned with u
   int ref = 0;
   double best = fabs(val(u[0]));
@@ -193,16 +230,28 @@ __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T
   const int pa = (ea.norb == 4) ? 10 : 1;
   const int pb = (eb.norb == 4) ? 10 : 1;
 
-  // local integrals
+  // local integrals: the distinct ones (rows ss, sz, xx, zz of the sigma/
+  // delta class, sx and xz of the pi class) from the charge sets, the rest by
+  // the x <-> y mirror and the rotational-invariance relation for (xy|xy)
   T I[10][10];
   for (int p = 0; p < 10; ++p)
-    for (int q = 0; q < 10; ++q) {
-      if (p < pa && q < pb && c_prod_cls[p] == c_prod_cls[q])
-        I[p][q] = local_integral<T>(p, q, ea, eb, R);
-      else
-        I[p][q] = cst<T>(0.0);
+    for (int q = 0; q < 10; ++q) I[p][q] = cst<T>(0.0);
+  for (int p = 0; p < pa; ++p) {
+    if (p == 2 || p == 5 || p == 7 || p == 9) continue;        // mirrored or derived below
+    for (int q = 0; q < pb; ++q) {
+      if (c_prod_cls[p] != c_prod_cls[q]) continue;
+      if (c_prod_cls[p] == 1 && (q == 2 || q == 9)) continue;
+      I[p][q] = Radial<T>::promote(local_integral<Tr>(p, q, ea, eb, Rr), uv);
     }
-  if (pa == 10 && pb == 10) I[7][7] = 0.5 * (I[4][4] - I[4][5]);
+  }
+  if (pa == 10) {
+    for (int q = 0; q < pb; ++q) {
+      const int mq = mirror_xy(q);
+      if (c_prod_cls[q] == 0) I[5][q] = I[4][mq];
+      if (c_prod_cls[q] == 2) { I[2][q] = I[1][mq]; I[9][q] = I[8][mq]; }
+    }
+    if (pb == 10) I[7][7] = 0.5 * (I[4][4] - I[4][5]);
+  }
 
   // product transform C[p][p'] (block diagonal over ss / sp / pp groups)
   T C[10][10];
@@ -232,16 +281,23 @@ __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T
       Wout[p * 10 + q] = acc;
     }
 
-  // overlaps in the local frame, then rotated
+  // overlaps in the local frame (functions of R), then rotated
   T Sl[4][4];
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 4; ++b) Sl[a][b] = cst<T>(0.0);
-  Sl[0][0] = sto_overlap<T>(R, ea.nprin, ea.zeta[0], 0, eb.nprin, eb.zeta[0], 0);
-  if (ea.norb == 4) Sl[3][0] = sto_overlap<T>(R, ea.nprin, ea.zeta[1], 1, eb.nprin, eb.zeta[0], 0);
-  if (eb.norb == 4) Sl[0][3] = sto_overlap<T>(R, ea.nprin, ea.zeta[0], 0, eb.nprin, eb.zeta[1], 1);
+  Sl[0][0] = Radial<T>::promote(
+      sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[0], ea.sto_nrm[0], 0, eb.nprin, eb.zeta[0], eb.sto_nrm[0], 0), uv);
+  if (ea.norb == 4)
+    Sl[3][0] = Radial<T>::promote(
+        sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[1], ea.sto_nrm[1], 1, eb.nprin, eb.zeta[0], eb.sto_nrm[0], 0), uv);
+  if (eb.norb == 4)
+    Sl[0][3] = Radial<T>::promote(
+        sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[0], ea.sto_nrm[0], 0, eb.nprin, eb.zeta[1], eb.sto_nrm[1], 1), uv);
   if (ea.norb == 4 && eb.norb == 4) {
-    Sl[3][3] = sto_overlap<T>(R, ea.nprin, ea.zeta[1], 1, eb.nprin, eb.zeta[1], 1);
-    T spp = sto_overlap<T>(R, ea.nprin, ea.zeta[1], 2, eb.nprin, eb.zeta[1], 2);
+    Sl[3][3] = Radial<T>::promote(
+        sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[1], ea.sto_nrm[1], 1, eb.nprin, eb.zeta[1], eb.sto_nrm[1], 1), uv);
+    T spp = Radial<T>::promote(
+        sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[1], ea.sto_nrm[1], 2, eb.nprin, eb.zeta[1], eb.sto_nrm[1], 2), uv);
     Sl[1][1] = spp;
     Sl[2][2] = spp;
   }
@@ -255,17 +311,17 @@ __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T
       Sout[a * 4 + b] = acc;
     }
 
-  // core-core repulsion
-  T gss = I[0][0];
-  double zz = ea.zcore * eb.zcore;
-  T en = zz * gss * (1.0 + ex(-ea.alpha * R) + ex(-eb.alpha * R));
-  T g = cst<T>(0.0);
+  // core-core repulsion (a function of R)
+  const Tr gss = local_integral<Tr>(0, 0, ea, eb, Rr);
+  const double zz = ea.zcore * eb.zcore;
+  Tr en = zz * gss * (1.0 + ex(-ea.alpha * Rr) + ex(-eb.alpha * Rr));
+  Tr g = cst<Tr>(0.0);
   for (int k = 0; k < 2; ++k) {
-    T ta = R - ea.gc[k];
-    T tb = R - eb.gc[k];
+    Tr ta = Rr - ea.gc[k];
+    Tr tb = Rr - eb.gc[k];
     g += ea.ga[k] * ex(-ea.gb[k] * (ta * ta)) + eb.ga[k] * ex(-eb.gb[k] * (tb * tb));
   }
-  *Eout = en + zz * g * iR;
+  *Eout = Radial<T>::promote(en + zz * g / Rr, uv);
 }
 
 __global__ void pair_values_kernel(int npair, const int* __restrict__ pA, const int* __restrict__ pB,
