@@ -1100,10 +1100,19 @@ __global__ void tfactor_all_kernel(int nref, int kblk, const double* __restrict_
 // number of blocks of kBtBlockTc reflectors (n - 2 reflectors)
 static int tc_blocks(int n) { return n > 2 ? (n - 2 + kBtBlockTc - 1) / kBtBlockTc : 1; }
 
+struct BtScratch;
+static size_t bt_scratch_layout(int n, void* base, BtScratch* out);
+// the inverse-iteration workspace (5 n^2) also serves as back-transformation scratch
+static size_t lu_doubles(int n) {
+  const size_t a = 5 * (size_t)n * n;
+  const size_t b = (bt_scratch_layout(n, nullptr, nullptr) + 7) / 8;
+  return a > b ? a : b;
+}
+
 size_t eig_work_bytes(int n) {
   size_t nn = (size_t)n * n;
   size_t doubles = nn /*A*/ + nn /*Vst*/ + 4 * (size_t)n /*d e e2 tau*/ + 3 * (size_t)n /*pbuf*/ +
-                   5 * nn /*lu*/ + 2 * (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc + 2 * (size_t)kBtBlockTc * n +
+                   lu_doubles(n) + 2 * (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc + 2 * (size_t)kBtBlockTc * n +
                    16;
   return doubles * sizeof(double) + 64 + (size_t)n * sizeof(int) + 256;
 }
@@ -1118,7 +1127,7 @@ void eig_work_bind(EigWork& w, void* base, int n) {
   w.e2 = p; p += n;
   w.tau = p; p += n;
   w.pbuf = p; p += 3 * (size_t)n;
-  w.lu = p; p += 5 * nn;
+  w.lu = p; p += lu_doubles(n);
   w.Tm = p; p += (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc;   // T and Gram of every reflector block
   w.Gm = p; p += (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc;
   w.Wt = p; p += (size_t)kBtBlockTc * n;
@@ -1253,10 +1262,12 @@ void eig_vectors(cudaStream_t s, int n, const double* eps, double* Q, EigWork& w
 
 // tensor-core back-transformation (mixed path), carried out on Z^T so that
 // every large operand is K-major: Z^T <- Z^T (I - V T V^T)^T block by block,
-//   U  = Z^T_sub V      (n x kb)      tensor cores, 4 slices
-//   U2 = U T^T          (n x kb)      FP64
-//   Z^T_sub -= U2 V^T                 tensor cores, 4 slices
-// with the Gram matrix V^T V of the block (for T) also on the tensor cores.
+//   U   = Z^T_sub V_b^T     (n x kb)      tensor cores, 4 slices, split over K
+//   Z^T_sub -= U Y_b        (n x m_b)     tensor cores, 4 slices
+// with Y_b = T_b^T V_b formed for all blocks before the loop (it does not
+// depend on Z).  The Gram matrices V_b V_b^T (for the T factors) and Y_b are
+// double-float products on the FP32 pipe, one launch each for all blocks; the
+// slices of V_b and Y_b^T are cut once, in two launches.
 __global__ void transpose_sq_kernel(int n, const double* __restrict__ A, double* __restrict__ At) {
   __shared__ double tile[32][33];
   int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
@@ -1277,54 +1288,159 @@ static void transpose_sq(cudaStream_t s, int n, const double* A, double* At) {
   count_launch();
 }
 
+// G_b = V_b V_b^T (upper 32 x 32 tiles) for every block b of kBtBlockTc
+// reflectors; V_b = rows k0.. of the reflector store, columns c0 = k0 + 1 ..
+__global__ void __launch_bounds__(256) gram_df_kernel(int n, int nref, const double* __restrict__ Vst,
+                                                      double* __restrict__ Gall) {
+  constexpr int KB = kBtBlockTc, TL = 32, CH = 64;
+  const int b = blockIdx.y;
+  const int k0 = b * KB, kb = min(KB, nref - k0), c0 = k0 + 1, m = n - c0;
+  const int ti = blockIdx.x / (KB / TL), tj = blockIdx.x % (KB / TL);
+  if (ti > tj || ti * TL >= kb || tj * TL >= kb) return;
+  __shared__ dfl sa[TL][CH + 1], sb[TL][CH + 1];
+  const int t = threadIdx.x, ii = t >> 3, jj = (t & 7) * 4;
+  dfl acc[4] = {};
+  for (int l0 = 0; l0 < m; l0 += CH) {
+    for (int e = t; e < TL * CH; e += blockDim.x) {
+      const int r = e / CH, c = e % CH;
+      const int l = l0 + c;
+      const int ra = ti * TL + r, rb = tj * TL + r;
+      sa[r][c] = (ra < kb && l < m) ? df_from_double(Vst[(size_t)(k0 + ra) * n + c0 + l]) : dfl{0.0f, 0.0f};
+      sb[r][c] = (rb < kb && l < m) ? df_from_double(Vst[(size_t)(k0 + rb) * n + c0 + l]) : dfl{0.0f, 0.0f};
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < CH; ++c) {
+      const dfl a = sa[ii][c];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) df_acc_mul(acc[q], a, sb[jj + q][c]);
+    }
+    __syncthreads();
+  }
+  const int i = ti * TL + ii;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = tj * TL + jj + q;
+    if (i < kb && j < kb) Gall[(size_t)b * KB * KB + (size_t)i * KB + j] = df_to_double(df_norm(acc[q]));
+  }
+}
+
+// Y_b^T = V_b^T T_b (m_b x kb, row length KB) for every block b; T_b upper
+// triangular (kb x kb, ld KB); 64 rows of Y_b^T per CTA, T_b and the V_b
+// columns in shared memory as double-float
+constexpr int kYRows = 64;
+constexpr size_t kYSmem = (size_t)(kBtBlockTc * kBtBlockTc + kBtBlockTc * kYRows) * sizeof(dfl);
+__global__ void __launch_bounds__(256) y_df_kernel(int n, int nref, const double* __restrict__ Vst,
+                                                   const double* __restrict__ Tall, double* __restrict__ YT) {
+  constexpr int KB = kBtBlockTc;
+  extern __shared__ dfl ysm[];
+  dfl* sT = ysm;                   // KB x KB
+  dfl* sV = ysm + KB * KB;         // KB (reflector) x kYRows (column)
+  const int b = blockIdx.y;
+  const int k0 = b * KB, kb = min(KB, nref - k0), c0 = k0 + 1, m = n - c0;
+  const int l0 = blockIdx.x * kYRows;
+  if (l0 >= m) return;
+  const double* Tb = Tall + (size_t)b * KB * KB;
+  for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) {
+    const int i = e / KB, j = e % KB;
+    sT[e] = (i < kb && j < kb && i <= j) ? df_from_double(Tb[(size_t)i * KB + j]) : dfl{0.0f, 0.0f};
+  }
+  for (int e = threadIdx.x; e < KB * kYRows; e += blockDim.x) {
+    const int i = e / kYRows, c = e % kYRows;
+    const int l = l0 + c;
+    sV[e] = (i < kb && l < m) ? df_from_double(Vst[(size_t)(k0 + i) * n + c0 + l]) : dfl{0.0f, 0.0f};
+  }
+  __syncthreads();
+  // thread t: row c = t / 4 of the tile, columns j = (t % 4) * 32 .. + 31
+  const int c = threadIdx.x >> 2, jb = (threadIdx.x & 3) * 32;
+  dfl acc[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc[q] = dfl{0.0f, 0.0f};
+  for (int i = 0; i < kb; ++i) {
+    const dfl v = sV[i * kYRows + c];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) df_acc_mul(acc[q], v, sT[i * KB + jb + q]);
+  }
+  const int l = l0 + c;
+  if (l < m) {
+    double* out = YT + (size_t)b * n * KB + (size_t)l * KB;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) out[jb + q] = (jb + q < kb) ? df_to_double(df_norm(acc[q])) : 0.0;
+  }
+}
+
+// back-transformation scratch (in the inverse-iteration workspace, free by then)
+static int bt_blocks(int n) { return n > 2 ? (n - 2 + kBtBlockTc - 1) / kBtBlockTc : 0; }
+constexpr int kBtSplitK = 6;
+struct BtScratch {
+  __nv_bfloat16* vs;   size_t vs_blk, vs_slice;   // V_b slices
+  double* yt;                                     // Y_b^T, FP64
+  __nv_bfloat16* ys;   size_t ys_blk, ys_slice;   // Y_b^T slices
+  double* part;                                   // split-K partial products of U
+};
+static size_t bt_scratch_layout(int n, void* base, BtScratch* out) {
+  const size_t nblk = (size_t)bt_blocks(n), KB = kBtBlockTc;
+  const size_t ldn = (size_t)tc_ld(n > 1 ? n : 1);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+  const size_t vs_slice = KB * ldn, vs_blk = (size_t)kTcMaxSlices * vs_slice;
+  const size_t o_vs = take(nblk * vs_blk * 2);
+  const size_t o_yt = take(nblk * (size_t)n * KB * 8);
+  const size_t ys_slice = (size_t)n * KB, ys_blk = (size_t)kTcMaxSlices * ys_slice;
+  const size_t o_ys = take(nblk * ys_blk * 2);
+  const size_t o_part = take((size_t)(kBtSplitK + 1) * n * KB * 8);
+  if (out) {
+    char* c = (char*)base;
+    out->vs = (__nv_bfloat16*)(c + o_vs); out->vs_blk = vs_blk; out->vs_slice = vs_slice;
+    out->yt = (double*)(c + o_yt);
+    out->ys = (__nv_bfloat16*)(c + o_ys); out->ys_blk = ys_blk; out->ys_slice = ys_slice;
+    out->part = (double*)(c + o_part);
+  }
+  return off;
+}
+
 static void eig_backtransform_tc(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork& tw) {
   static PerDeviceOnce attr;
   once_per_device(attr, [] {
     return cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kBtBlockTc * kBtBlockTc * (int)sizeof(double)) == cudaSuccess &&
            cudaFuncSetAttribute(tfactor_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kBtBlockTc * kBtBlockTc * (int)sizeof(double)) == cudaSuccess;
+                                kBtBlockTc * kBtBlockTc * (int)sizeof(double)) == cudaSuccess &&
+           cudaFuncSetAttribute(y_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSmem) ==
+               cudaSuccess;
   });
   const int nref = n - 2;
-  const int nblk = (nref + kBtBlockTc - 1) / kBtBlockTc;
+  const int nblk = bt_blocks(n);
   const size_t stride = tc_slot_stride(tw);
   int* err = tc_error_flag(tw);
+  BtScratch sc;
+  bt_scratch_layout(n, w.lu, &sc);
   double* Zt = w.A;                      // tridiagonalisation workspace is free now
   transpose_sq(s, n, Q, Zt);
-  // Gram matrices V_b V_b^T and T factors of all blocks first (one launch for the T's)
-  for (int b = 0; b < nblk; ++b) {
-    int k0 = b * kBtBlockTc, k1 = (k0 + kBtBlockTc < nref) ? k0 + kBtBlockTc : nref;
-    int kb = k1 - k0, c0 = k0 + 1, m = n - c0;
-    const double* Vb = w.Vst + (size_t)k0 * n + c0;
-    int ldm = tc_ld(m);
-    __nv_bfloat16* sV = tc_slot_base(tw, kSlotQ);
-    tc_split_rc(s, kb, m, Vb, n, 0, 4, tc_slot_exponents(tw, kSlotQ), sV, ldm, stride);
-    tc_gemm_rc(s, kb, kb, m, sV, ldm, stride, sV, ldm, stride, 10, 1.0,
-               w.Gm + (size_t)b * kBtBlockTc * kBtBlockTc, kBtBlockTc, 0, err);
-  }
-  if (nblk > 0) {
-    tfactor_all_kernel<<<nblk, kBtBlockTc, kBtBlockTc * kBtBlockTc * sizeof(double), s>>>(nref, kBtBlockTc,
-                                                                                          w.tau, w.Gm, w.Tm);
-    count_launch();
-  }
+  // Gram matrices and T factors of all blocks, then Y_b^T = V_b^T T_b, then slices
+  gram_df_kernel<<<dim3((kBtBlockTc / 32) * (kBtBlockTc / 32), nblk), 256, 0, s>>>(n, nref, w.Vst, w.Gm);
+  count_launch();
+  tfactor_all_kernel<<<nblk, kBtBlockTc, kBtBlockTc * kBtBlockTc * sizeof(double), s>>>(nref, kBtBlockTc, w.tau,
+                                                                                      w.Gm, w.Tm);
+  count_launch();
+  y_df_kernel<<<dim3((n + kYRows - 1) / kYRows, nblk), 256, kYSmem, s>>>(n, nref, w.Vst, w.Tm, sc.yt);
+  count_launch();
+  tc_split_blocks(s, 0, n, nref, kBtBlockTc, w.Vst, sc.vs, sc.vs_blk, sc.vs_slice, 4);
+  tc_split_blocks(s, 1, n, nref, kBtBlockTc, sc.yt, sc.ys, sc.ys_blk, sc.ys_slice, 4);
+  __nv_bfloat16* sZ = tc_slot_base(tw, kSlotT0);
+  __nv_bfloat16* sU = tc_slot_base(tw, kSlotT1);
   for (int b = nblk - 1; b >= 0; --b) {
-    int k0 = b * kBtBlockTc, k1 = (k0 + kBtBlockTc < nref) ? k0 + kBtBlockTc : nref;
-    int kb = k1 - k0, c0 = k0 + 1, m = n - c0;
-    const double* Vb = w.Vst + (size_t)k0 * n + c0;      // kb x m, ld n
-    const double* Tb = w.Tm + (size_t)b * kBtBlockTc * kBtBlockTc;
+    const int k0 = b * kBtBlockTc, kb = (k0 + kBtBlockTc < nref) ? kBtBlockTc : nref - k0;
+    const int c0 = k0 + 1, m = n - c0;
+    const int ldm = tc_ld(m);
     double* Zs = Zt + c0;                                // n x m, ld n
-    int ldm = tc_ld(m), ldk = tc_ld(kb);
-    __nv_bfloat16* sV = tc_slot_base(tw, kSlotQ);
-    tc_split_rc(s, kb, m, Vb, n, 0, 4, tc_slot_exponents(tw, kSlotQ), sV, ldm, stride);
-    __nv_bfloat16* sZ = tc_slot_base(tw, kSlotT0);
-    tc_split_rc(s, n, m, Zs, n, 0, 4, tc_slot_exponents(tw, kSlotT0), sZ, ldm, stride);
-    tc_gemm_rc(s, n, kb, m, sZ, ldm, stride, sV, ldm, stride, 10, 1.0, w.Wt, kb, 0, err);      // U
-    dgemm(s, 0, 1, n, kb, kb, 1.0, w.Wt, kb, Tb, kBtBlockTc, 0.0, w.Wt2, kb);                 // U2 = U T^T
-    __nv_bfloat16* sU = tc_slot_base(tw, kSlotT1);
-    tc_split_rc(s, n, kb, w.Wt2, kb, 0, 4, tc_slot_exponents(tw, kSlotT1), sU, ldk, stride);
-    __nv_bfloat16* sVt = tc_slot_base(tw, kSlotQt);
-    tc_split_rc(s, m, kb, Vb, n, 1, 4, tc_slot_exponents(tw, kSlotQt), sVt, ldk, stride);
-    tc_gemm_rc(s, n, m, kb, sU, ldk, stride, sVt, ldk, stride, 10, -1.0, Zs, n, 1, err);      // Zs -= U2 V^T
+    tc_split_rows(s, n, m, Zs, n, 4, sZ, ldm, stride);
+    const int parts = tc_gemm_rc_splitk(s, n, kb, m, sZ, ldm, stride, sc.vs + (size_t)b * sc.vs_blk, ldm,
+                                        sc.vs_slice, 10, 1.0, sc.part, kBtBlockTc, kBtSplitK, err);   // U parts
+    const int ldk = tc_ld(kb);                           // U slices fit the slot: kb <= n
+    tc_reduce_split_rows(s, n, kb, sc.part, parts > 0 ? parts : 0, kBtBlockTc, 4, sU, ldk, stride);
+    tc_gemm_rc(s, n, m, kb, sU, ldk, stride, sc.ys + (size_t)b * sc.ys_blk, kBtBlockTc, sc.ys_slice, 10, -1.0, Zs,
+               n, 1, err);                                                                   // Zs -= U Y_b
   }
   transpose_sq(s, n, Zt, Q);
 }

@@ -170,7 +170,8 @@ __device__ __forceinline__ void twosum_acc(float& hi, float& lo, float b) {
 
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ TcMaps maps, SegTable seg, int M, int N, int K, double alpha,
-                   double* __restrict__ C, int ldc, int sym, int beta, int* err, const int* gate) {
+                   double* __restrict__ C, int ldc, int sym, int beta, int* err, const int* gate, int kt_split,
+                   long long c_zstride) {
   if (gate && *gate == 0) return;      // whole CTA, before any barrier or TMEM use
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (sym && bi > bj) return;
@@ -186,7 +187,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = bi * kBM, n0 = bj * kBN;
-  const int ktiles = (K + kBK - 1) / kBK;
+  // split-K (kt_split > 0): CTA z takes k-tiles [z kt_split, (z + 1) kt_split) and
+  // writes its partial product to C + z c_zstride
+  const int ktiles_all = (K + kBK - 1) / kBK;
+  const int kt0 = (kt_split > 0) ? (int)blockIdx.z * kt_split : 0;
+  int ktiles = (kt_split > 0) ? min(kt_split, ktiles_all - kt0) : ktiles_all;
+  if (ktiles < 0) ktiles = 0;
+  C += (long long)blockIdx.z * c_zstride;
   const int total = seg.nseg * ktiles;
   const int cps = (ktiles + kChunk - 1) / kChunk;   // chunks per segment
   const int nchunks = seg.nseg * cps;
@@ -224,8 +231,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!mbar_wait(&empty[s], ph ^ 1u, err)) { ok = false; break; }
         int sg = it / ktiles, kt = it % ktiles;
         mbar_expect_tx(&full[s], kTileBytesA + kTileBytesB);
-        tma_load_2d(sA + s * kTileBytesA, &maps.a[seg.a[sg]], &full[s], kt * kBK, m0);
-        tma_load_2d(sB + s * kTileBytesB, &maps.b[seg.b[sg]], &full[s], kt * kBK, n0);
+        tma_load_2d(sA + s * kTileBytesA, &maps.a[seg.a[sg]], &full[s], (kt0 + kt) * kBK, m0);
+        tma_load_2d(sB + s * kTileBytesB, &maps.b[seg.b[sg]], &full[s], (kt0 + kt) * kBK, n0);
         issued = it + 1;
       }
       if (!ok) {
@@ -440,6 +447,94 @@ __global__ void split_general_kernel(int rows, int cols, const double* __restric
   slice_value(x, ex[i], slices, base, stride, t);
 }
 
+// Row-wise slicing in one pass per row (a warp per row: the row maximum by
+// shuffles, then the slices); columns cols..ld-1 are written as zeros.  Used
+// by the back-transformation, whose operands change shape block by block.
+// Batched forms: blockIdx.y is a block of reflectors b (kblk of them, rows
+// k = b kblk .. of the reflector store, columns c0 = b kblk + 1 .. n-1).
+struct RowSplit {
+  int rows, cols;          // rows of op(X), K extent
+  const double* X;         // row r at X + r * ldx
+  long long ldx;
+  __nv_bfloat16* base;     // slice a, row r, column k at base + a * stride + r * ld + k
+  int ld;
+  size_t stride;
+};
+
+__device__ __forceinline__ void split_row_warp(const RowSplit& q, int r, int slices, int lane) {
+  const double* x = q.X + (long long)r * q.ldx;
+  unsigned long long m = 0;
+  for (int k = lane; k < q.cols; k += 32) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x[k]) & 0x7FFFFFFFFFFFFFFFULL;
+    m = (b > m) ? b : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (t > m) ? t : m;
+  }
+  const int e = exponent_of_max(m);
+  for (int k = lane; k < q.ld; k += 32)
+    slice_value((k < q.cols) ? x[k] : 0.0, e, slices, q.base, q.stride, (size_t)r * q.ld + k);
+}
+
+__global__ void split_rows_kernel(RowSplit q, int slices) {
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= q.rows) return;
+  split_row_warp(q, r, slices, threadIdx.x & 31);
+}
+
+// mode 0: V_b (kb_b x m_b) from the reflector store;  mode 1: Y_b^T (m_b x kb_b)
+// from YT + b n kblk (row length kblk)
+__global__ void split_blocks_kernel(int mode, int n, int nref, int kblk, const double* __restrict__ src,
+                                    __nv_bfloat16* base, size_t blk_stride, size_t slice_stride, int slices) {
+  const int b = blockIdx.y;
+  const int k0 = b * kblk;
+  const int kb = min(kblk, nref - k0);
+  const int m = n - (k0 + 1);
+  RowSplit q;
+  q.base = base + (size_t)b * blk_stride;
+  q.stride = slice_stride;
+  if (mode == 0) {
+    q.rows = kb; q.cols = m; q.X = src + (size_t)k0 * n + (k0 + 1); q.ldx = n; q.ld = (m + 63) / 64 * 64;
+  } else {
+    q.rows = m; q.cols = kb; q.X = src + (size_t)b * n * kblk; q.ldx = kblk; q.ld = kblk;
+  }
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= q.rows) return;
+  split_row_warp(q, r, slices, threadIdx.x & 31);
+}
+
+// U = sum_z P_z (in order), then its slices (rows x cols, ld ldp; parts at P + z rows ldp)
+__global__ void reduce_split_rows_kernel(int rows, int cols, const double* __restrict__ P, int parts, int ldp,
+                                         int slices, __nv_bfloat16* base, int ld, size_t stride) {
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  constexpr int kMaxPer = 4;                 // cols <= 128
+  double v[kMaxPer];
+  unsigned long long m = 0;
+#pragma unroll
+  for (int c = 0; c < kMaxPer; ++c) {
+    const int k = lane + 32 * c;
+    double a = 0.0;
+    if (k < cols)
+      for (int z = 0; z < parts; ++z) a += P[((size_t)z * rows + r) * ldp + k];
+    v[c] = a;
+    unsigned long long bits = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFULL;
+    m = (bits > m) ? bits : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (t > m) ? t : m;
+  }
+  const int e = exponent_of_max(m);
+#pragma unroll
+  for (int c = 0; c < kMaxPer; ++c) {
+    const int k = lane + 32 * c;
+    if (k < ld) slice_value(v[c], e, slices, base, stride, (size_t)r * ld + k);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -584,7 +679,7 @@ void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, d
     }
   int n = tb->n;
   dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
-  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, 0, tb->err, gate);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, 0, tb->err, gate, 0, 0);
   count_launch();
 }
 
@@ -633,9 +728,68 @@ int tc_gemm_rc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, 
       ++seg.nseg;
     }
   dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
-  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, M, N, K, alpha, C, ldc, 0, beta, err, nullptr);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, M, N, K, alpha, C, ldc, 0, beta, err, nullptr,
+                                                     0, 0);
   count_launch();
   return 0;
+}
+
+// Split-K variant of tc_gemm_rc: the K range is cut into `splits` parts (each a
+// whole number of exact-sum chunks), part z writes alpha * (its partial sum) to
+// P + z * M * ldp (M x N, ld ldp); the caller adds the parts in order.
+int tc_gemm_rc_splitk(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, int lda, size_t astride,
+                      const __nv_bfloat16* Bbase, int ldb, size_t bstride, int terms, double alpha, double* P,
+                      int ldp, int splits, int* err) {
+  set_smem_attribute();
+  int slices = (terms == 10) ? 4 : (terms == 6) ? 3 : (terms == 3) ? 2 : 1;
+  TcMaps maps;
+  for (int a = 0; a < kTcMaxSlices; ++a) {
+    int sa = (a < slices) ? a : 0;
+    if (!make_map_rc(&maps.a[a], (void*)(Abase + sa * astride), M, K, lda)) return -1;
+    if (!make_map_rc(&maps.b[a], (void*)(Bbase + sa * bstride), N, K, ldb)) return -1;
+  }
+  SegTable seg;
+  seg.nseg = 0;
+  for (int d = slices - 1; d >= 0; --d)
+    for (int a = 0; a <= d; ++a) {
+      seg.a[seg.nseg] = a;
+      seg.b[seg.nseg] = d - a;
+      ++seg.nseg;
+    }
+  const int ktiles = (K + kBK - 1) / kBK;
+  int per = (ktiles + splits - 1) / splits;
+  per = ((per + kChunk - 1) / kChunk) * kChunk;          // whole exact-sum chunks
+  const int z = (ktiles + per - 1) / per;
+  dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, z);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, M, N, K, alpha, P, ldp, 0, 0, err, nullptr, per,
+                                                     (long long)M * ldp);
+  count_launch();
+  return z;
+}
+
+void tc_split_rows(cudaStream_t s, int rows, int cols, const double* X, long long ldx, int slices,
+                   __nv_bfloat16* base, int ld, size_t stride) {
+  if (rows <= 0) return;
+  RowSplit q{rows, cols, X, ldx, base, ld, stride};
+  split_rows_kernel<<<(rows + 7) / 8, 256, 0, s>>>(q, slices);
+  count_launch();
+}
+
+void tc_split_blocks(cudaStream_t s, int mode, int n, int nref, int kblk, const double* src, __nv_bfloat16* base,
+                     size_t blk_stride, size_t slice_stride, int slices) {
+  const int nblk = (nref + kblk - 1) / kblk;
+  if (nblk <= 0) return;
+  const int maxrows = (mode == 0) ? kblk : n;
+  split_blocks_kernel<<<dim3((maxrows + 7) / 8, nblk), 256, 0, s>>>(mode, n, nref, kblk, src, base, blk_stride,
+                                                                    slice_stride, slices);
+  count_launch();
+}
+
+void tc_reduce_split_rows(cudaStream_t s, int rows, int cols, const double* P, int parts, int ldp, int slices,
+                          __nv_bfloat16* base, int ld, size_t stride) {
+  if (rows <= 0) return;
+  reduce_split_rows_kernel<<<(rows + 7) / 8, 256, 0, s>>>(rows, cols, P, parts, ldp, slices, base, ld, stride);
+  count_launch();
 }
 
 bool tc_encode_map(CUtensorMap* m, void* ptr, int n, int ld) { return make_map(m, ptr, n, ld); }
@@ -668,7 +822,7 @@ void tc_gemm_on_maps(cudaStream_t s, int n, const CUtensorMap* mapsA, const CUte
       ++seg.nseg;
     }
   dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
-  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, 0, err, nullptr);
+  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, 0, err, nullptr, 0, 0);
   count_launch();
 }
 

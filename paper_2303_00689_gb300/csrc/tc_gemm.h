@@ -44,6 +44,21 @@ void tc_split_rc(cudaStream_t s, int rows, int cols, const double* X, int ldx, i
 int tc_gemm_rc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, int lda, size_t astride,
                const __nv_bfloat16* Bbase, int ldb, size_t bstride, int terms, double alpha, double* C, int ldc,
                int beta, int* err);
+// split-K: returns the number of parts z actually used (partials at P + z M ldp), < 0 on error
+int tc_gemm_rc_splitk(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, int lda, size_t astride,
+                      const __nv_bfloat16* Bbase, int ldb, size_t bstride, int terms, double alpha, double* P,
+                      int ldp, int splits, int* err);
+// one-pass row slicing (row maximum and slices per warp), columns cols..ld-1 zero
+void tc_split_rows(cudaStream_t s, int rows, int cols, const double* X, long long ldx, int slices,
+                   __nv_bfloat16* base, int ld, size_t stride);
+// all reflector blocks at once: mode 0 slices V_b (kb x m_b, rows of the reflector
+// store from column b kblk + 1, row length tc_ld(m_b)), mode 1 slices Y_b^T (m_b x kb,
+// src + b n kblk, row length kblk); block b at base + b blk_stride, slices slice_stride apart
+void tc_split_blocks(cudaStream_t s, int mode, int n, int nref, int kblk, const double* src, __nv_bfloat16* base,
+                     size_t blk_stride, size_t slice_stride, int slices);
+// sum of `parts` partial products (rows x cols <= 128, at P + z rows ldp) and its slices
+void tc_reduce_split_rows(cudaStream_t s, int rows, int cols, const double* P, int parts, int ldp, int slices,
+                          __nv_bfloat16* base, int ld, size_t stride);
 // raw access to a slot's slice buffers (for the back-transformation)
 __nv_bfloat16* tc_slot_base(const TcWork& w, int slot);
 size_t tc_slot_stride(const TcWork& w);
