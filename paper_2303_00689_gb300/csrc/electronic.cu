@@ -19,27 +19,98 @@ __device__ __forceinline__ double fermi_occ(double eps, double mu, double beta) 
 }
 
 // ---- chemical potential and occupations (one block) -------------------------
+// block-wide FP32 sum in a fixed order; every thread gets the total
+__device__ __forceinline__ float block_sum_f(float v, float* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  float t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0f;
+  if (wid == 0)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  const float r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+// mu (eq. 8): bisection on sum_i f_i = N_occ to 1e-15 relative, as before, but
+// (1) a coarse FP32 bisection (eigenvalues staged in shared memory) shrinks the
+// bracket first, and (2) the FP64 sums run over the window of eigenvalues within
+// 40/beta of the bracket only: outside it every f_i is exactly 0 or 1 in FP64,
+// so the window sum plus the count below it is the full sum.  GB300's FP64
+// pipe is narrow; the full FP64 bisection took some fifty passes over n.
+constexpr int kFermiSmemMax = 11264;     // eigenvalues staged in shared memory (larger n: global)
+
+// number of eigenvalues below x (eps ascending); every thread gets it
+__device__ int count_below(int n, const double* __restrict__ eps, double x, double* red) {
+  double c = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) c += (eps[i] < x) ? 1.0 : 0.0;
+  return (int)block_sum(c, red);
+}
+// i0 + sum_{i0 <= i < i1} f_i(mu)
+__device__ double window_sum(const double* __restrict__ eps, int i0, int i1, double mu, double beta, double* red) {
+  double loc = 0.0;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) loc += fermi_occ(eps[i], mu, beta);
+  return (double)i0 + block_sum(loc, red);
+}
+
 __global__ void fermi_kernel(int n, const double* __restrict__ eps, double nocc, double beta,
                              double* __restrict__ f, Scalars* sc) {
   __shared__ double red[32];
-  double lo = eps[0] - 40.0 / beta, hi = eps[n - 1] + 40.0 / beta;
+  __shared__ float redf[32];
+  __shared__ float e32[kFermiSmemMax];
+  const bool staged = n <= kFermiSmemMax;
+  if (staged)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) e32[i] = (float)eps[i];
+  __syncthreads();
+  const double glo = eps[0] - 40.0 / beta, ghi = eps[n - 1] + 40.0 / beta;
+  float lo32 = (float)glo, hi32 = (float)ghi;
+  const float b32 = (float)beta, nocc32 = (float)nocc;
+  for (int it = 0; it < 80; ++it) {
+    const float mid = 0.5f * (lo32 + hi32);
+    if (mid <= lo32 || mid >= hi32) break;
+    float loc = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float ei = staged ? e32[i] : (float)eps[i];
+      loc += 1.0f / (1.0f + __expf(b32 * (ei - mid)));
+    }
+    const float s = block_sum_f(loc, redf);
+    if (s > nocc32) hi32 = mid; else lo32 = mid;
+  }
+  // FP64 bracket around the FP32 one, widened until it brackets the FP64 root
+  double w = 8.0 * ((double)hi32 - (double)lo32) + 1e-12 * fmax(1.0, fabs((double)lo32));
+  double lo = fmax(glo, (double)lo32 - w), hi = fmin(ghi, (double)hi32 + w);
+  int i0 = 0, i1 = n;
+  for (int k = 0; k < 64; ++k) {
+    i0 = count_below(n, eps, lo - 40.0 / beta, red);
+    i1 = count_below(n, eps, hi + 40.0 / beta, red);
+    const bool ok_lo = (lo <= glo) || window_sum(eps, i0, i1, lo, beta, red) <= nocc;
+    const bool ok_hi = (hi >= ghi) || window_sum(eps, i0, i1, hi, beta, red) > nocc;
+    if (ok_lo && ok_hi) break;
+    w *= 4.0;
+    if (!ok_lo) lo = fmax(glo, lo - w);
+    if (!ok_hi) hi = fmin(ghi, hi + w);
+  }
   for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    double loc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) loc += fermi_occ(eps[i], mid, beta);
-    double s = block_sum(loc, red);
-    if (s > nocc) hi = mid; else lo = mid;
+    const double mid = 0.5 * (lo + hi);
+    if (window_sum(eps, i0, i1, mid, beta, red) > nocc) hi = mid; else lo = mid;
     if (hi - lo < 1e-15 * fmax(1.0, fabs(mid))) break;
   }
   double mu = 0.5 * (lo + hi);
   for (int it = 0; it < 3; ++it) {
     double l1 = 0.0, l2 = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       double fi = fermi_occ(eps[i], mu, beta);
       l1 += fi;
       l2 += fi * (1.0 - fi);
     }
-    double s = block_sum(l1, red);
+    double s = (double)i0 + block_sum(l1, red);
     double dn = beta * block_sum(l2, red);
     if (dn < 1e-300) break;
     double step = (nocc - s) / dn;
@@ -48,7 +119,7 @@ __global__ void fermi_kernel(int n, const double* __restrict__ eps, double nocc,
   }
   double ls = 0.0, ll = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double fi = fermi_occ(eps[i], mu, beta);
+    double fi = (i < i0) ? 1.0 : (i >= i1) ? 0.0 : fermi_occ(eps[i], mu, beta);
     f[i] = fi;
     if (fi > 0.0 && fi < 1.0) ls += fi * log(fi) + (1.0 - fi) * log(1.0 - fi);
     ll += -beta * fi * (1.0 - fi);

@@ -150,6 +150,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 16 consecutive TMEM columns of this warp's lane quarter (half the registers
+// of the 32-column load, which keeps the epilogue's accumulators in registers)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 struct TcMaps {
   CUtensorMap a[kTcMaxSlices];
   CUtensorMap b[kTcMaxSlices];
@@ -291,11 +303,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       got = __all_sync(0xffffffffu, got);
       if (!got) { ok = false; break; }
       tc_fence_after();
-      {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kBN + cg * 32), r);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) twosum_acc(hi[j], lo[j], __uint_as_float(r[j]));
+      for (int h = 0; h < 2; ++h) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kBN + cg * 32 + h * 16), r);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) twosum_acc(hi[h * 16 + j], lo[h * 16 + j], __uint_as_float(r[j]));
       }
       tc_fence_before();
       __syncwarp();
@@ -359,12 +372,24 @@ __global__ void row_exponent_kernel(int n, const double* __restrict__ X, int tra
 
 // Balanced base-256 digits of X = round(x 2^(7 + 8(S-1) - e)): slice a is digit
 // a (most significant first) times 2^(e - 7 - 8a).  Digits lie in [-128, 128],
-// so each slice value is exact in BF16.  FP64 work per element: one scaling
-// and one rounding conversion; the digits come from integer arithmetic.
-__device__ __forceinline__ void slice_value(double x, int e, int slices, __nv_bfloat16* out, size_t stride,
-                                            size_t t) {
+// so each slice value is exact in BF16.  X is formed from the bit pattern of x
+// (x = +-M 2^(E - 1075), so X = M 2^sh rounded, sh = E - 1075 + 7 + 8(S-1) - e,
+// ties away from zero) and the digits and their BF16 values by integer and FP32
+// operations: the element needs no FP64 instruction.  |x| < 2^e (e is the
+// exponent of the row maximum), so sh < 0.
+__device__ __forceinline__ void slice_digits(double x, int e, int slices, __nv_bfloat16* v) {
   const int top = 7 + 8 * (slices - 1);
-  long long X = __double2ll_rn(ldexp(x, top - e));
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  unsigned long long M = b & 0xFFFFFFFFFFFFFULL;
+  if (E != 0) M |= 1ULL << 52;
+  const int sh = (E != 0 ? E : 1) - 1075 + top - e;
+  long long X = 0;
+  if (sh >= 0)
+    X = (long long)(M << (sh < 11 ? sh : 11));           // not reached for |x| < 2^e
+  else if (sh > -64)
+    X = (long long)((M + (1ULL << (-sh - 1))) >> (-sh));
+  if (b >> 63) X = -X;
   int dig[kTcMaxSlices];
   for (int a = slices - 1; a > 0; --a) {
     int r = (int)(X & 0xFF);
@@ -374,9 +399,17 @@ __device__ __forceinline__ void slice_value(double x, int e, int slices, __nv_bf
   }
   dig[0] = (int)X;
   for (int a = 0; a < slices; ++a) {
-    float v = ldexpf((float)dig[a], e - 7 - 8 * a);
-    out[a * stride + t] = __float2bfloat16_rn(v);
+    const int k = e - 7 - 8 * a;                           // slice scale 2^k
+    const float p2 = (k >= -126 && k <= 127) ? __int_as_float((k + 127) << 23) : 0.0f;
+    v[a] = __float2bfloat16_rn((float)dig[a] * p2);
   }
+}
+
+__device__ __forceinline__ void slice_value(double x, int e, int slices, __nv_bfloat16* out, size_t stride,
+                                            size_t t) {
+  __nv_bfloat16 v[kTcMaxSlices];
+  slice_digits(x, e, slices, v);
+  for (int a = 0; a < slices; ++a) out[a * stride + t] = v[a];
 }
 
 // FP64 -> fixed-point BF16 slices relative to the row exponent; ld-padded rows
@@ -390,17 +423,9 @@ __global__ void split_bf16_kernel(int n, const double* __restrict__ X, int ld, i
   int i = (int)(t / ld), j = (int)(t % ld);
   double x = 0.0;
   if (j < n) x = transpose ? X[(size_t)j * n + i] : X[(size_t)i * n + j];
-  const int top = 7 + 8 * (slices - 1);
-  long long Xi = __double2ll_rn(ldexp(x, top - ex[i]));
-  int dig[kTcMaxSlices];
-  for (int a = slices - 1; a > 0; --a) {
-    int r = (int)(Xi & 0xFF);
-    if (r >= 128) r -= 256;
-    dig[a] = r;
-    Xi = (Xi - r) >> 8;
-  }
-  dig[0] = (int)Xi;
-  for (int a = 0; a < slices; ++a) P[a][t] = __float2bfloat16_rn(ldexpf((float)dig[a], ex[i] - 7 - 8 * a));
+  __nv_bfloat16 v[kTcMaxSlices];
+  slice_digits(x, ex[i], slices, v);
+  for (int a = 0; a < slices; ++a) P[a][t] = v[a];
 }
 
 // same slicing as split_bf16_kernel, slices at base + a * stride (no pointer table)
