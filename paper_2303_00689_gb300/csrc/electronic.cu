@@ -5,6 +5,8 @@
 //
 // Every reduction runs in a fixed order (per-block tree, then a single block
 // over the partials), so results do not depend on scheduling.
+#include <cstring>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -332,6 +334,122 @@ void launch_energy(cudaStream_t s, int n, int npair, const double* h, const doub
   count_launch();
 }
 
+// ---- fused combination + dot products (one pass over the vectors) -----------------------
+// Per element t: y_i = Y_i[t] (i < ny); val = x[t] - sum_i c_i y_i when combo (c_i = 1
+// when c is null), else x[t]; out[t] = val when out is set; and for each dot j the
+// product of two operands A_j[t] and B_j[t] (a null operand stands for val).
+// Block partials are added in a fixed order by the last block to finish (a
+// counter in Scalars), so each result is deterministic and one launch does it.
+constexpr int kFuseY = 16, kFuseDots = 20;
+struct FuseArgs {
+  const double* x;
+  const double* Y[kFuseY];
+  const double* c;
+  double* out;
+  int ny, combo, nd;
+  const double* A[kFuseDots];
+  const double* B[kFuseDots];
+};
+
+// MY, MD: compile-time bounds on ny and nd (registers); two elements per thread
+// and iteration (16-byte loads; len is even for the n x n matrices used here,
+// an odd tail is handled by the last thread)
+template <int MY, int MD>
+__global__ void __launch_bounds__(kRedThreads) fused_combo_dots_kernel(size_t len, FuseArgs f,
+                                                                       double* __restrict__ partial,
+                                                                       double* __restrict__ dots_out, Scalars* sc,
+                                                                       int gated) {
+  if (gated && !sc->active) return;
+  __shared__ int s_last;
+  __shared__ double sred[MD][kRedThreads / 32];
+  double acc[MD];
+#pragma unroll
+  for (int j = 0; j < MD; ++j) acc[j] = 0.0;
+  double cf[MY];
+#pragma unroll
+  for (int i = 0; i < MY; ++i) cf[i] = (i < f.ny) ? (f.c ? f.c[i] : 1.0) : 0.0;
+  const size_t npair = len >> 1;
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < npair; p += (size_t)gridDim.x * blockDim.x) {
+    double2 yv[MY];
+#pragma unroll
+    for (int i = 0; i < MY; ++i)
+      if (i < f.ny) yv[i] = ((const double2*)f.Y[i])[p];
+    double2 val = ((const double2*)f.x)[p];
+    if (f.combo) {
+#pragma unroll
+      for (int i = 0; i < MY; ++i)
+        if (i < f.ny) { val.x -= cf[i] * yv[i].x; val.y -= cf[i] * yv[i].y; }
+    }
+    if (f.out) ((double2*)f.out)[p] = val;
+#pragma unroll
+    for (int j = 0; j < MD; ++j)
+      if (j < f.nd) {
+        const double2 a = f.A[j] ? ((const double2*)f.A[j])[p] : val;
+        const double2 b = f.B[j] ? ((const double2*)f.B[j])[p] : val;
+        acc[j] += a.x * b.x + a.y * b.y;
+      }
+  }
+  if ((len & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
+    const size_t t = len - 1;
+    double val = f.x[t];
+    if (f.combo)
+#pragma unroll
+      for (int i = 0; i < MY; ++i)
+        if (i < f.ny) val -= cf[i] * f.Y[i][t];
+    if (f.out) f.out[t] = val;
+#pragma unroll
+    for (int j = 0; j < MD; ++j)
+      if (j < f.nd) acc[j] += (f.A[j] ? f.A[j][t] : val) * (f.B[j] ? f.B[j][t] : val);
+  }
+  // all dots reduced together: warp shuffles, one CTA barrier, a fixed order
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < MD; ++j) {
+    if (j < f.nd) {
+      const double v = warp_sum(acc[j]);
+      if (lane == 0) sred[j][wid] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < f.nd) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRedThreads / 32; ++w) t += sred[threadIdx.x][w];
+    partial[threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&sc->red_count, 1u) == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last block: dot j by warp j mod 8, lanes over the block partials
+  for (int j = wid; j < f.nd; j += kRedThreads / 32) {
+    double loc = 0.0;
+    for (int i = lane; i < (int)gridDim.x; i += 32) loc += __ldcg(partial + j * gridDim.x + i);
+    loc = warp_sum(loc);
+    if (lane == 0) dots_out[j] = loc;
+  }
+  if (threadIdx.x == 0) sc->red_count = 0;
+}
+
+static void fused(cudaStream_t s, size_t len, const FuseArgs& f, double* partial, double* dots_out, Scalars* sc,
+                  bool gated) {
+  if (f.ny <= 8 && f.nd <= 8)
+    fused_combo_dots_kernel<8, 8><<<kRedBlocks, kRedThreads, 0, s>>>(len, f, partial, dots_out, sc, gated ? 1 : 0);
+  else
+    fused_combo_dots_kernel<kFuseY, kFuseDots><<<kRedBlocks, kRedThreads, 0, s>>>(len, f, partial, dots_out, sc,
+                                                                                   gated ? 1 : 0);
+  count_launch();
+}
+static FuseArgs fuse_args() {
+  FuseArgs f;
+  memset(&f, 0, sizeof(f));
+  return f;
+}
+
 // ---- Krylov kernel (eqs. 31-34) --------------------------------------------------------
 __global__ void krylov_start_kernel(size_t len, const double* __restrict__ D, const double* __restrict__ X,
                                     double* __restrict__ W0) {
@@ -350,11 +468,12 @@ __global__ void krylov_start_final(const double* n2, Scalars* sc) {
 
 void launch_krylov_start(cudaStream_t s, size_t len, const double* D, const double* X, double* W0,
                          Scalars* sc, double* partial) {
-  krylov_start_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(len, D, X, W0);
-  count_launch();
-  const double* a[1] = {W0};
+  // W0 = D - X and ||W0||^2 in one pass
+  FuseArgs f = fuse_args();
+  f.x = D; f.Y[0] = X; f.ny = 1; f.combo = 1; f.out = W0;
+  f.nd = 1;
   double* tmp = partial + kRedBlocks * kMaxDots;  // small result area after the partials
-  dots(s, len, 1, a, a, tmp, partial);
+  fused(s, len, f, partial, tmp, sc, false);
   krylov_start_final<<<1, 1, 0, s>>>(tmp, sc);
   count_launch();
 }
@@ -393,26 +512,29 @@ __global__ void normalize_kernel(size_t len, double* __restrict__ v, const doubl
   if (t < len) v[t] = v[t] * scale[0];
 }
 
-// k = number of existing vectors V_0..V_{k-1}; src -> v orthonormalised (CGS twice)
+// k = number of existing vectors V_0..V_{k-1}; src -> v orthonormalised (CGS twice).
+// Fused passes: c1 = <V_i, src>; v = src - sum c1_i V_i with c2 = <V_i, v>;
+// v -= sum c2_i V_i with ||v||^2 and ||src||^2; then v *= 1/||v||.
 void launch_krylov_orth(cudaStream_t s, size_t len, int k, double* const* Vs, const double* src, double* v,
                         Scalars* sc, double* partial, double* coef) {
-  PtrList V;
-  for (int i = 0; i < k; ++i) V.p[i] = Vs[i];
   unsigned nb = (unsigned)((len + 255) / 256);
-  const double* cur = src;
-  for (int pass = 0; pass < 2; ++pass) {
-    if (k > 0) {
-      const double* a[16];
-      const double* b[16];
-      for (int i = 0; i < k; ++i) { a[i] = Vs[i]; b[i] = cur; }
-      dots(s, len, k, a, b, coef, partial, &sc->active);
-    }
-    sub_combo_kernel<<<nb, 256, 0, s>>>(len, k, V, coef, cur, v, sc);
-    count_launch();
-    cur = v;
+  FuseArgs f = fuse_args();
+  for (int i = 0; i < k; ++i) f.Y[i] = Vs[i];
+  f.ny = k;
+  if (k > 0) {
+    f.x = src; f.combo = 0; f.out = nullptr; f.nd = k;
+    for (int j = 0; j < k; ++j) f.A[j] = Vs[j];
+    fused(s, len, f, partial, coef, sc, true);                       // c1
+    f.combo = 1; f.c = coef; f.out = v;
+    fused(s, len, f, partial, coef + 20, sc, true);                  // v, c2
+    f.x = v; f.c = coef + 20;
+  } else {
+    f.x = src; f.combo = 0; f.out = v;                               // v = src
   }
-  const double* a2[2] = {v, src};
-  dots(s, len, 2, a2, a2, coef + 16, partial, &sc->active);
+  f.nd = 2;
+  f.A[0] = nullptr; f.B[0] = nullptr;
+  f.A[1] = src; f.B[1] = src;
+  fused(s, len, f, partial, coef + 16, sc, true);                    // v (second pass), norms
   norm_scale_kernel<<<1, 1, 0, s>>>(coef + 16, sc, coef + 18);
   count_launch();
   normalize_kernel<<<nb, 256, 0, s>>>(len, v, coef + 18, sc);
@@ -499,19 +621,17 @@ __global__ void gram_solve_kernel(int k, const double* __restrict__ dv, Scalars*
   if (m >= m_min && fit < tol) sc->active = 0;
 }
 
+// W_k = D1 - v (eq. 31) and its products with W_0..W_k and W0 in one pass
 void launch_krylov_w(cudaStream_t s, size_t len, int k, const double* D1, const double* v, double* Wk,
                      double* const* Ws, const double* W0, Scalars* sc, double* partial, double tol,
                      int m_min) {
-  unsigned nb = (unsigned)((len + 255) / 256);
-  wk_kernel<<<nb, 256, 0, s>>>(len, D1, v, Wk, sc);
-  count_launch();
-  const double* a[18];
-  const double* b[18];
-  for (int j = 0; j <= k; ++j) { a[j] = Wk; b[j] = Ws[j]; }
-  a[k + 1] = Wk;
-  b[k + 1] = W0;
+  FuseArgs f = fuse_args();
+  f.x = D1; f.Y[0] = v; f.ny = 1; f.combo = 1; f.out = Wk;
+  for (int j = 0; j < k; ++j) f.B[j] = Ws[j];                       // <W_k, W_j>, <W_k, W_k>, <W_k, W0>
+  f.B[k + 1] = W0;
+  f.nd = k + 2;
   double* dv = partial + kRedBlocks * kMaxDots + 32;
-  dots(s, len, k + 2, a, b, dv, partial, &sc->active);
+  fused(s, len, f, partial, dv, sc, true);
   gram_solve_kernel<<<1, 1, 0, s>>>(k, dv, sc, tol, m_min);
   count_launch();
 }

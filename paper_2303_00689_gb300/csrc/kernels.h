@@ -89,6 +89,8 @@ struct Scalars {         // device-resident per-evaluation scalars
   double O[16 * 16], b[16], c[16], w0n2;
   int rank, active, status, pad;
   unsigned long long step;   // MD steps taken (counter of the thermostat's random numbers)
+  unsigned red_count;        // blocks done in the current fused reduction (reset by its last block)
+  unsigned red_pad;
 };
 void launch_fermi(cudaStream_t s, int n, const double* eps, double nocc, double beta, double* f,
                   Scalars* sc);
