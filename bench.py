@@ -22,6 +22,7 @@ import argparse
 import json
 import os
 import statistics
+import shutil
 import subprocess
 import sys
 import tempfile
@@ -38,8 +39,13 @@ WORKLOAD = dict(workload="840-atom random carbon packing, 2.2 g/cc, open box (se
                 l2="working set > L2 (no flush needed)")
 METRIC = "atom-steps/s (KSA-XL-BOMD MD step)"
 KERNEL_MODE = [0]      # sim_kernel of the timed runs (--kernel)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk x 2 flop x max clock
-TRIDIAG_TRAFFIC_BYTES = 0.909e9 + 40.228e9       # dram read + write, one launch at n = 3360
+# FP32 instructions per FP64-equivalent multiply-add in the double-float
+# tridiagonalisation: the rank-2 update costs 27 for two, the product term 12 for
+# one (df.cuh), 13 on average over the three multiply-adds of an element
+DF_OPS_PER_FMA = 13.0
+# DRAM bytes (read + write) of one tridiag_df_kernel launch at n = 3360 from one
+# ncu capture of the bench's profile run (dram__bytes_read.sum + dram__bytes_write.sum)
+TRIDIAG_TRAFFIC = {"bytes": None, "source": "not captured for this kernel version"}
 
 
 def _dist():
@@ -64,6 +70,51 @@ def job_throughput(total_ms, steps, natoms_per_rank, world):
     """(ms per step, whole-job atom-steps/s): every rank steps its own replica."""
     ms_per_step = total_ms / steps
     return ms_per_step, world * natoms_per_rank / (ms_per_step / 1e3)
+
+
+class EventClock:
+    """Step marks as CUDA events on the stream the steps are launched on."""
+
+    def __init__(self, stream):
+        import torch
+        self.stream, self.torch, self.ev = stream, torch, []
+
+    def mark(self):
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        self.ev.append(e)
+
+    def laps_ms(self):
+        return [self.ev[k].elapsed_time(self.ev[k + 1]) for k in range(len(self.ev) - 1)]
+
+
+class WallClock:
+    """Step marks from the host clock (CPU replicas)."""
+
+    def __init__(self):
+        self.t = []
+
+    def mark(self):
+        self.t.append(time.perf_counter())
+
+    def laps_ms(self):
+        return [1e3 * (self.t[k + 1] - self.t[k]) for k in range(len(self.t) - 1)]
+
+
+def timed_replica(step, steps, warmup, barrier, clock, world, device):
+    """The rank logic of the bench: `warmup` untimed steps, a barrier, `steps`
+    steps each bracketed by clock marks, a barrier, then the slowest rank's
+    total.  Returns (per-step ms of this rank, max-over-ranks total ms)."""
+    for _ in range(warmup):
+        step()
+    barrier()
+    clock.mark()
+    for _ in range(steps):
+        step()
+        clock.mark()
+    barrier()
+    laps = clock.laps_ms()
+    return laps, max_over_ranks(sum(laps), world, device)
 
 
 def _peaks():
@@ -146,6 +197,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
+    peaks = {"fp64_tflops": kx.sim_measure_peak(0, local), "fp32_tflops": kx.sim_measure_peak(1, local)}
     mol, V, table = _inputs()
     N = mol.natoms
     prec = kx.SIM_PREC_FP64 if args.precision == "fp64" else kx.SIM_PREC_MIXED
@@ -155,7 +207,6 @@ def run_ours(args):
     scf_iters, scf_res = kx.sim_scf_info(h)
     X0 = kx.sim_get_matrix(h, kx.SIM_MAT_X)
     stream = torch.cuda.ExternalStream(kx.sim_stream(h))
-    kx.sim_step(h, args.warmup, records=False)
 
     def barrier():
         torch.cuda.synchronize()
@@ -164,31 +215,26 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     # ---- device-timed steps (state resident in HBM) ---------------------------
+    kx.sim_step(h, args.warmup, records=False)
     kx.sim_profile_enable(h, True)
     clocks = Clocks(local)
     clocks.start()
     launches0 = kx.sim_launch_count()
-    barrier()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    evs[0].record(stream)
-    for k in range(args.steps):
-        kx.sim_step_async(h, 1)
-        evs[k + 1].record(stream)
-    barrier()
+    per_step, total_ms = timed_replica(lambda: kx.sim_step_async(h, 1), args.steps, 0, barrier,
+                                       EventClock(stream), world, "cuda")
     launches = kx.sim_launch_count() - launches0
     clk = clocks.stop()
-    rec = kx.sim_last_result(h)
-    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
+    recs = kx.sim_records(h, args.steps)
     phases = kx.sim_phase_times(h)
     kx.sim_profile_enable(h, False)
-    total_ms = max_over_ranks(total_ms, world, "cuda")
     ms_per_step, value = job_throughput(total_ms, args.steps, N, world)
+    state_dir = None
+    if rank == 0 and not args.no_cpu_baseline:
+        state_dir = _dump_state(kx, h, N)
 
     # ---- end to end through the C ABI with pinned host buffers --------------------
     pin = lambda: torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
     R_h, V_h, R_o, V_o, F_o = pin(), pin(), pin(), pin(), pin()
-    _, _, _, _ = kx.sim_get_state(h, N)
     Rc, Vc, _, _ = kx.sim_get_state(h, N)
     R_h[:] = Rc
     V_h[:] = Vc
@@ -207,7 +253,11 @@ def run_ours(args):
     # ---- dominant phase roofline -----------------------------------------------
     name, ph = max(phases.items(), key=lambda kv: kv[1]["ms"])
     per_launch_s = ph["ms"] / max(1, ph["launches"]) / 1e3
-    roof = _roofline(name, ph, per_launch_s)
+    roof = _roofline(name, ph, per_launch_s, peaks, prec == kx.SIM_PREC_MIXED)
+
+    def stats(key):
+        v = np.array([r[key] for r in recs], dtype=float)
+        return {"min": float(v.min()), "median": float(np.median(v)), "max": float(v.max())}
 
     out = {
         "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
@@ -222,40 +272,75 @@ def run_ours(args):
                 "d2h_bytes_per_step": 3 * N * 3 * 8 + 64},
         "gpu_launches": int(launches),
         "roofline": roof,
+        "measured_peaks": peaks,
         "phases_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in phases.items()},
-        "last_step": {k: rec[k] for k in ("E_tot", "res_norm", "fit_err", "rank", "gap")},
+        "timed_steps": {"res_norm": stats("res_norm"), "fit_err": stats("fit_err"), "rank": stats("rank"),
+                        "E_tot": stats("E_tot")},
         "setup_s": round(setup_s, 2),
         "scf": {"method": "low-rank Krylov, rank 6", "iterations": scf_iters, "max_abs_residual": scf_res},
         "clocks": clk,
     }
     if rank == 0 and not args.no_fp64_context and prec == kx.SIM_PREC_MIXED:
         out["fp64_path"] = _fp64_context(kx, mol, V, table, X0)
+    if rank == 0 and not args.no_extras:
+        out["serving"] = _serving_record(kx, args)
+        out["batch"] = _batch_record(kx, args)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = _cpu_baseline(args)
+        cb = _cpu_baseline(args, state_dir)
+        if "accuracy" in cb:
+            out["accuracy"] = cb.pop("accuracy")
+        out["cpu_baseline"] = cb
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def _roofline(name, ph, per_launch_s):
-    peaks = _peaks()
+def _dump_state(kx, h, N):
+    """The state after the timed steps, for the oracle's accuracy check."""
+    d = tempfile.mkdtemp(prefix="ksaxl_state_")
+    R, V, F, D0 = kx.sim_get_state(h, N)
+    np.save(os.path.join(d, "R.npy"), R)
+    np.save(os.path.join(d, "V.npy"), V)
+    np.save(os.path.join(d, "F.npy"), F)
+    np.save(os.path.join(d, "D0.npy"), D0)
+    np.save(os.path.join(d, "K.npy"), kx.sim_get_matrix(h, kx.SIM_MAT_KERNEL))
+    np.save(os.path.join(d, "Xh.npy"), np.stack([kx.sim_get_matrix(h, kx.SIM_MAT_XHIST + k) for k in range(7)]))
+    with open(os.path.join(d, "rec.json"), "w") as f:
+        json.dump({k: v for k, v in kx.sim_last_result(h).items()}, f)
+    return d
+
+
+def _roofline(name, ph, per_launch_s, peaks, mixed):
+    """Roofline entry of the dominant phase; peaks measured in this run."""
+    meas = _peaks()
     work = ph["work"]
-    if name in ("eig_tridiag", "eig_backtransform", "density_gemm") or (name == "krylov_dmpt_gemm" and False):
+    if name == "eig_tridiag" and mixed:
+        # FP64-equivalent algorithmic flops (4/3 n^3) run as double-float on the
+        # FP32 pipe: the arithmetic peak is the measured FP32 FMA rate divided by
+        # the FP32 instructions one FP64-equivalent multiply-add costs
         achieved = work / per_launch_s / 1e12
-        # DRAM bytes of one tridiag_kernel launch from the ncu capture summarised in
-        # profiles/tridiag_kernel_c840_n3360.md (same kernel and workload)
-        traffic = TRIDIAG_TRAFFIC_BYTES if name == "eig_tridiag" else None
-        return {"kernel_phase": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "derived FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"}
+        peak = peaks["fp32_tflops"] / DF_OPS_PER_FMA
+        return {"kernel_phase": name, "kernel": "tridiag_df_kernel", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TRIDIAG_TRAFFIC["bytes"], "traffic_source": TRIDIAG_TRAFFIC["source"],
+                "peak_source": f"measured FP32 FMA rate {peaks['fp32_tflops']:.1f} TFLOP/s / {DF_OPS_PER_FMA:g} "
+                               "FP32 instructions per double-float multiply-add",
+                "fp64_frac": achieved / peaks["fp64_tflops"],
+                "fp64_note": "the same algorithmic flops against the measured FP64 FMA rate "
+                             f"{peaks['fp64_tflops']:.2f} TFLOP/s"}
+    if name in ("eig_tridiag", "eig_backtransform", "density_gemm"):
+        achieved = work / per_launch_s / 1e12
+        peak = peaks["fp64_tflops"]
+        return {"kernel_phase": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": "measured FP64 FMA rate"}
     if name == "krylov_dmpt_gemm":
         achieved = work / per_launch_s / 1e12
-        peak = peaks.get("bf16_tflops_sustained", 1715.0)
+        peak = meas.get("bf16_tflops_sustained", 1715.0)
         return {"kernel_phase": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "peak_source": "measured bf16 sustained"}
     achieved = work / per_launch_s / 1e9
-    peak = peaks.get("hbm_gbs", 6792.1)
+    peak = meas.get("hbm_gbs", 6792.1)
     return {"kernel_phase": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else 0.0, "traffic": None, "peak_source": "measured HBM copy"}
 
@@ -274,35 +359,69 @@ def _fp64_context(kx, mol, V, table, X0, steps=2):
     return {"value": mol.natoms / s, "unit": "atom-steps/s", "ms_per_step": 1e3 * s, "steps": steps}
 
 
-def _cpu_baseline(args):
-    """Times the oracle in a fresh (spawned) interpreter on a bounded sample."""
+def _cpu_baseline(args, state_dir=None):
+    """Times the oracle in a fresh (spawned) interpreter on a bounded sample;
+    with a state from the GPU run it also reports the GPU's errors there."""
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample"]
+    if state_dir:
+        cmd += ["--state", state_dir]
     try:
         r = subprocess.run(cmd, capture_output=True, text=True, timeout=args.cpu_timeout)
         return json.loads(r.stdout.strip().splitlines()[-1])
     except Exception as e:  # noqa: BLE001
         return {"value": None, "unit": "atom-steps/s", "kind": "oracle", "error": str(e)[:200]}
+    finally:
+        if state_dir:
+            shutil.rmtree(state_dir, ignore_errors=True)
 
 
-def oracle_sample():
-    """One full oracle MD step of the 840-atom workload (bounded sample)."""
+def oracle_sample(state_dir=None):
+    """One full oracle MD step of the 840-atom workload (bounded sample).
+
+    Without a state: from the diagonal guess X (no SCF).  With the GPU's state
+    after its timed steps (R, V, X(t - k dt)): the oracle's evaluation there
+    (untimed) gives the GPU path's errors in D0, forces, U and the Krylov
+    kernel K; then one oracle step from that state is timed."""
     import synth
     from oracle import dynamics as dyn, hamiltonian as ham
     mol, V, _ = _inputs()
     sysm = ham.System(mol.Z, synth.synthetic_table(1))
     cfg = dyn.Config(Te=WORKLOAD["Te_K"], dt=WORKLOAD["dt_fs"], m=6)
-    X = dyn.initial_guess(sysm)
-    t = time.perf_counter()
-    st = dyn.State(sysm, mol.R, V, cfg, X0=X)     # evaluation at t0 (not timed below)
-    t_eval = time.perf_counter() - t
+    acc = None
+    if state_dir:
+        ld = lambda k: np.load(os.path.join(state_dir, k + ".npy"))
+        R, Vg, Xh = ld("R"), ld("V"), ld("Xh")
+        t = time.perf_counter()
+        st = dyn.State(sysm, R, Vg, cfg, X0=Xh[0])       # evaluation at the GPU's (R, X(t)), not timed
+        t_eval = time.perf_counter() - t
+        st.X = [x.copy() for x in Xh]                    # the GPU's X history (eq. 29)
+        with open(os.path.join(state_dir, "rec.json")) as f:
+            rec = json.load(f)
+        ev = st.ev
+        acc = {"max_abs_dD0": float(np.abs(ld("D0") - ev["D"]).max()),
+               "max_abs_dF_eV_per_A": float(np.abs(ld("F") - ev["forces"]).max()),
+               "abs_dU_eV": float(abs(rec["U"] - ev["U"])),
+               "rel_max_dK": float(np.abs(ld("K") - ev["K"]).max() / np.abs(ev["K"]).max()),
+               "where": "state after the timed steps; oracle evaluation at the same R and X(t)",
+               "bars": {"D0": 1e-6, "F_eV_per_A": 1e-4}}
+        sample = ("one full oracle MD step of the 840-atom workload from the GPU's state after its timed steps "
+                  f"(R, V, X history); the evaluation there ({t_eval:.1f} s) untimed")
+    else:
+        X = dyn.initial_guess(sysm)
+        t = time.perf_counter()
+        st = dyn.State(sysm, mol.R, V, cfg, X0=X)     # evaluation at t0 (not timed below)
+        t_eval = time.perf_counter() - t
+        sample = ("one full oracle MD step (teacher-forced from the diagonal guess X, no SCF) of the "
+                  f"840-atom workload; first evaluation {t_eval:.1f} s untimed")
     t = time.perf_counter()
     st.step()
     s = time.perf_counter() - t
     cores = len(os.sched_getaffinity(0))
-    return {"value": mol.natoms / s, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
-            "sample": "one full oracle MD step (teacher-forced from the diagonal guess X, no SCF) of the "
-                      f"840-atom workload; first evaluation {t_eval:.1f} s untimed",
-            "seconds_per_step": s}
+    out = {"value": mol.natoms / s, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+           "sample": sample, "seconds_per_step": s}
+    if acc is not None:
+        out["accuracy"] = acc
+    return out
 
 
 def profile_run(args):
@@ -343,36 +462,29 @@ def _batch_handles(kx, mols, table, graphs):
     return hs
 
 
-def run_batch(args):
+def measure_batch(kx, molecules, steps, warmup):
     """Molecule batch: every molecule its own trajectory, all stepped together
-    (sim_batch_create/run: one CUDA graph per batch step, one branch per molecule)."""
+    (sim_batch_create/run: one CUDA graph per batch step, one branch per
+    molecule).  Returns the measurement as a dict."""
     import torch
     import synth
-    import paper_2303_00689_gb300 as kx
-    from paper_2303_00689_gb300 import build
-    torch.cuda.set_device(0)
-    build.build()
-    mols = synth.molecule_batch(seed=3, count=BATCH["molecules"])
+    mols = synth.molecule_batch(seed=3, count=molecules)
     table = synth.table_to_array(synth.synthetic_table(1))
     atoms = sum(m.natoms for m in mols)
     t = time.time()
     hs = _batch_handles(kx, mols, table, graphs=False)
     batch = kx.sim_batch_create(hs)              # one CUDA graph per batch step
     setup = time.time() - t
-    kx.sim_batch_run(batch, args.warmup)
-    clocks = Clocks(0)
-    clocks.start()
+    kx.sim_batch_run(batch, warmup)
     l0 = kx.sim_launch_count()
     torch.cuda.synchronize()
     t = time.perf_counter()
-    kx.sim_batch_run(batch, args.steps)
+    kx.sim_batch_run(batch, steps)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
     launches = kx.sim_launch_count() - l0
-    clk = clocks.stop()
-    value = atoms * args.steps / dt
     # the same handles stepped one molecule after the other (no overlap)
-    k_seq = max(1, min(args.steps, 3))
+    k_seq = max(1, min(steps, 3))
     torch.cuda.synchronize()
     t = time.perf_counter()
     for h in hs:
@@ -381,38 +493,56 @@ def run_batch(args):
     kx.sim_batch_destroy(batch)
     for h in hs:
         kx.sim_destroy(h)
-    out = {"metric": "atom-steps/s (128-molecule batch, KSA-XL-BOMD)", "value": value, "unit": "atom-steps/s",
-           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16-slices",
-           "data": "synthetic", "config": dict(BATCH, atoms=atoms, l2="per-molecule working sets are small; "
-                                                                    "timed region is many consecutive steps"),
-           "sequential_value": seq, "gpu_launches": int(launches), "graph_launches_per_step": 1,
-           "setup_s": round(setup, 1), "clocks": clk}
-    print(json.dumps(out), flush=True)
+    return {"workload": f"{molecules} organic molecules, 12-200 atoms (C/N/O/H, seed 3)", "atoms": atoms,
+            "value": atoms * steps / dt, "unit": "atom-steps/s", "ms_per_batch_step": 1e3 * dt / steps,
+            "steps": steps, "sequential_value": seq, "gpu_launches_per_step": launches / steps,
+            "graph_launches_per_step": 1, "setup_s": round(setup, 1), "Te_K": BATCH["Te_K"], "krylov_rank": 4,
+            "precision": "mixed"}
 
 
-def run_serve(args):
-    """Serving: Poisson arrivals of MD requests (20-600 atoms, 10-100 steps)
-    at 0.8x the measured capacity, continuous batching under an HBM budget."""
+def _batch_record(kx, args):
+    try:
+        return measure_batch(kx, args.extra_batch_molecules, 5, 3)
+    except Exception as e:  # noqa: BLE001
+        return {"error": str(e)[:200]}
+
+
+def run_batch(args):
     import torch
-    import synth
     import paper_2303_00689_gb300 as kx
     from paper_2303_00689_gb300 import build
     torch.cuda.set_device(0)
     build.build()
+    clocks = Clocks(0)
+    clocks.start()
+    m = measure_batch(kx, BATCH["molecules"], args.steps, args.warmup)
+    clk = clocks.stop()
+    out = {"metric": "atom-steps/s (128-molecule batch, KSA-XL-BOMD)", "value": m["value"], "unit": "atom-steps/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_batch_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16-slices",
+           "data": "synthetic", "config": dict(BATCH, atoms=m["atoms"], l2="per-molecule working sets are small; "
+                                                                         "timed region is many consecutive steps"),
+           "sequential_value": m["sequential_value"], "gpu_launches": int(m["gpu_launches_per_step"] * args.steps),
+           "graph_launches_per_step": 1, "setup_s": m["setup_s"], "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
+def measure_serving(kx, count, nmax, use_graphs=True, admit=4, timeout_s=900.0):
+    """Serving: Poisson arrivals of MD requests (C60 cages, 60..nmax atoms,
+    10-100 steps) at 0.8x the measured closed-loop capacity, continuous
+    batching under an HBM budget.  Returns the measurement as a dict."""
+    import synth
     table = kx.param_table(synth.table_to_array(synth.synthetic_table(1)))
     cfg = kx.sim_config_default(Te=1000.0, dt=0.5, m_max=4, m_min=4, precision=kx.SIM_PREC_MIXED,
                                 scf_tol=1e-7, scf_max=40, scf_krylov=1, scf_accept=1)
-    count = args.serve_requests
     # C60 cages: random organic trees heat up and fly apart within a few fs under
     # the synthetic parameter table, which would make long trajectories meaningless
-    reqs = synth.serving_requests(seed=4, count=count, rate_per_s=1.0, nmax=args.serve_nmax, kind="fullerene")
+    reqs = synth.serving_requests(seed=4, count=count, rate_per_s=1.0, nmax=nmax, kind="fullerene")
     work = sum(m.natoms * st for _, m, st in reqs)
 
     def replay(rate_scale):
         """rate_scale None: all requests at t = 0 (closed loop, capacity)."""
-        with kx.Server(max_active=64, use_graphs=bool(args.serve_graphs),
-                       admission_threads=args.serve_admit) as srv:
+        with kx.Server(max_active=64, use_graphs=use_graphs, admission_threads=admit) as srv:
             t0 = time.perf_counter()
             tickets = []
             for (ta, m, st) in reqs:
@@ -422,26 +552,13 @@ def run_serve(args):
                         time.sleep(wait)
                 V = synth.maxwell_boltzmann(m.Z, 300.0, seed=int(ta * 1e3) % 100000)
                 tickets.append(srv.submit(cfg, table, m.Z, m.R, V=V, charge=m.charge, nsteps=st, records=False))
-            while True:                      # progress to stderr while draining
+            while True:
                 st = srv.stats()
-                print(f"serve t={time.perf_counter() - t0:7.1f}s done={st['completed']}+{st['failed']} "
-                      f"live={st['active']} queued={st['queued']} atom_steps={st['atom_steps']}",
-                      file=sys.stderr, flush=True)
                 if st["completed"] + st["failed"] == len(reqs):
                     break
-                if time.perf_counter() - t0 > args.serve_timeout:
-                    # leave without joining the server's threads
-                    fails = []
-                    for i, t in enumerate(tickets):
-                        r = srv.poll(t)
-                        if r is not None and r["status"] != kx.SIM_OK:
-                            fails.append((i, reqs[i][1].natoms, r["status"], r["error"]))
-                    print(json.dumps({"error": "serving run exceeded --serve-timeout", "stats": st,
-                                      "failed": fails,
-                                      "sizes": [(i, m.natoms, n) for i, (_, m, n) in enumerate(reqs)]}),
-                          file=sys.stderr, flush=True)
-                    os._exit(3)
-                time.sleep(2.0)
+                if time.perf_counter() - t0 > timeout_s:
+                    raise RuntimeError(f"serving run exceeded {timeout_s} s: {st}")
+                time.sleep(0.5)
             wall = time.perf_counter() - t0
             res = [srv.poll(t) for t in tickets]
             st = srv.stats()
@@ -456,16 +573,37 @@ def run_serve(args):
     span = reqs[-1][0]
     target_wall = work / (0.8 * cap["atom_steps_per_s"])
     served = replay(target_wall / span)
-    out = {"metric": "atom-steps/s served (Poisson arrivals at 0.8x capacity)",
-           "value": served["atom_steps_per_s"], "unit": "atom-steps/s", "n_gpus": 1, "steps": count,
-           "warmup": 0, "ms_per_step": served["step_p50_ms"], "higher_is_better": True, "scaling": "weak",
+    return {"workload": f"{count} requests of 1-{nmax // 60} C60 cages (60-{nmax} atoms), 10-100 steps (seed 4)",
+            "value": served["atom_steps_per_s"], "unit": "atom-steps/s",
+            "latency_ms": {"p50": served["step_p50_ms"], "p99": served["step_p99_ms"]},
+            "queue_ms": {"p50": served["queue_p50_ms"], "p99": served["queue_p99_ms"]},
+            "offered_load": "0.8 x closed-loop capacity", "Te_K": 1000.0, "krylov_rank": 4, "precision": "mixed",
+            "capacity": cap, "served": served}
+
+
+def _serving_record(kx, args):
+    try:
+        return measure_serving(kx, args.extra_serve_requests, args.extra_serve_nmax, timeout_s=300.0)
+    except Exception as e:  # noqa: BLE001
+        return {"error": str(e)[:200]}
+
+
+def run_serve(args):
+    import torch
+    import paper_2303_00689_gb300 as kx
+    from paper_2303_00689_gb300 import build
+    torch.cuda.set_device(0)
+    build.build()
+    m = measure_serving(kx, args.serve_requests, args.serve_nmax, bool(args.serve_graphs), args.serve_admit,
+                        args.serve_timeout)
+    out = {"metric": "atom-steps/s served (Poisson arrivals at 0.8x capacity)", "value": m["value"],
+           "unit": "atom-steps/s", "n_gpus": 1, "steps": args.serve_requests, "warmup": 0,
+           "ms_per_step": m["latency_ms"]["p50"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64+bf16-slices", "data": "synthetic",
-           "config": {"workload": f"{count} requests of 1-{args.serve_nmax // 60} C60 cages (60-{args.serve_nmax} "
-                                  f"atoms), 10-100 steps (seed 4)", "Te_K": 1000.0,
-                      "krylov_rank": 4, "precision": "mixed", "offered_load": "0.8 x closed-loop capacity"},
-           "latency_ms": {"p50": served["step_p50_ms"], "p99": served["step_p99_ms"]},
-           "queue_ms": {"p50": served["queue_p50_ms"], "p99": served["queue_p99_ms"]},
-           "capacity": cap, "served": served}
+           "config": {"workload": m["workload"], "Te_K": 1000.0, "krylov_rank": 4, "precision": "mixed",
+                      "offered_load": m["offered_load"]},
+           "latency_ms": m["latency_ms"], "queue_ms": m["queue_ms"], "capacity": m["capacity"],
+           "served": m["served"]}
     print(json.dumps(out), flush=True)
 
 
@@ -536,6 +674,11 @@ def main():
     p.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     p.add_argument("--no-fp64-context", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the short serving and batch records")
+    p.add_argument("--extra-serve-requests", type=int, default=12)
+    p.add_argument("--extra-serve-nmax", type=int, default=300)
+    p.add_argument("--extra-batch-molecules", type=int, default=32)
+    p.add_argument("--state", default=None, help=argparse.SUPPRESS)
     p.add_argument("--cpu-timeout", type=float, default=600.0)
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--workload", choices=("md840", "batch", "serve", "drift"), default="md840",
@@ -552,7 +695,7 @@ def main():
                    help="short run for ncu (no SCF, no baselines); prints launch counts")
     args = p.parse_args()
     if args.oracle_sample:
-        print(json.dumps(oracle_sample()), flush=True)
+        print(json.dumps(oracle_sample(args.state)), flush=True)
         return
     if args.profile_run:
         profile_run(args)

@@ -210,7 +210,10 @@ int sim_records(sim_handle* h, sim_step_result* out, int count);
 
 /* sim_wait -- synchronise the handle's stream and return the first error a
  * kernel reported since the last check (SIM_ETIMEOUT for an expired bounded
- * wait, SIM_ENUMERIC for NaN/Inf), else SIM_OK. */
+ * wait, SIM_ENUMERIC for NaN/Inf), else SIM_OK.  Every device-reported error
+ * (here and in the step calls) is reported once and then cleared; after a
+ * failed step the handle holds a partial step, so re-establish the state
+ * with sim_set_state or sim_load before stepping on. */
 int sim_wait(sim_handle* h);
 
 /* sim_enable_graphs -- enable != 0 captures one MD step into CUDA graphs
@@ -411,6 +414,24 @@ int sim_tc_gemm_noalloc(int n, const double* A, const double* B, int terms, int 
  * (use only when A B^T is symmetric).  Allocates and frees its own device
  * memory; synchronous. */
 int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sym, double* C);
+
+/* sim_measure_peak -- FMA throughput of `device` in TFLOP/s (2 flops per FMA),
+ * kind 0: FP64, kind 1: FP32; 8 independent chains per thread on 8 blocks of
+ * 256 threads per SM, timed with CUDA events after a warm-up launch.  The
+ * denominators of the arithmetic-bound roofline fractions (no counterpart in
+ * the paper).  Allocates 16 bytes; synchronous. */
+int sim_measure_peak(int device, int kind, double* tflops);
+
+/* Failure-path test hooks (no counterpart in the paper).
+ * sim_debug_barrier_limit -- wall-time limit, ns, of the eigensolver's grid
+ *   barriers on `device` (default 2e9).  A limit of 0 makes the next step's
+ *   barrier waits expire: the kernel records the timeout and returns, and the
+ *   step reports SIM_ETIMEOUT.  Restore the default afterwards.
+ * sim_debug_wait_expiry -- one bounded mbarrier wait (the wait primitive of
+ *   the tensor-core pipeline) on a barrier that nothing arrives at, `tries`
+ *   polls; returns SIM_ETIMEOUT when the wait expired as it must. */
+int sim_debug_barrier_limit(int device, unsigned long long ns);
+int sim_debug_wait_expiry(int device, long long tries);
 
 /* Thread-local message of the last error (never NULL). */
 const char* sim_last_error(void);

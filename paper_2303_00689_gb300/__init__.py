@@ -30,7 +30,7 @@ EXPORTED = (
     "sim_tc_gemm_noalloc", "sim_records", "sim_wait", "sim_enable_graphs", "sim_batch_step",
     "sim_estimate_bytes", "sim_server_create", "sim_submit", "sim_poll", "sim_server_stats_get",
     "sim_server_drain", "sim_server_destroy", "sim_save", "sim_load", "sim_batch_create", "sim_batch_run",
-    "sim_batch_destroy",
+    "sim_batch_destroy", "sim_measure_peak", "sim_debug_barrier_limit", "sim_debug_wait_expiry",
 )
 
 
@@ -128,6 +128,9 @@ def lib():
         L.sim_tc_gemm_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                           C.c_void_p]
         L.sim_records.argtypes = [C.c_void_p, P(sim_step_result), C.c_int]
+        L.sim_measure_peak.argtypes = [C.c_int, C.c_int, dp]
+        L.sim_debug_barrier_limit.argtypes = [C.c_int, C.c_ulonglong]
+        L.sim_debug_wait_expiry.argtypes = [C.c_int, C.c_longlong]
         L.sim_save.argtypes = [C.c_void_p, C.c_char_p]
         L.sim_batch_create.argtypes = [P(C.c_void_p), C.c_int, P(C.c_void_p)]
         L.sim_batch_run.argtypes = [C.c_void_p, C.c_int]
@@ -430,6 +433,23 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def sim_measure_peak(kind, device=0):
+    """FMA throughput in TFLOP/s: kind 0 FP64, kind 1 FP32."""
+    out = C.c_double(0.0)
+    _check(lib().sim_measure_peak(int(device), int(kind), C.byref(out)))
+    return out.value
+
+
+def sim_debug_barrier_limit(ns, device=0):
+    """Wall-time limit (ns) of the eigensolver's grid barriers (test hook)."""
+    _check(lib().sim_debug_barrier_limit(int(device), int(ns)))
+
+
+def sim_debug_wait_expiry(tries, device=0):
+    """Raw status of one bounded mbarrier wait that nothing satisfies (test hook)."""
+    return lib().sim_debug_wait_expiry(int(device), int(tries))
 
 
 def sim_last_error():

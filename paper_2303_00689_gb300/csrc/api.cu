@@ -538,6 +538,12 @@ static int check_status(sim_handle* h) {
   if (mixed(h)) CUDA_TRY(cudaMemcpyAsync(&tce, tc_error_flag(h->tw), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   CUDA_TRY(cudaGetLastError());
+  if (st || tce) {
+    // an error is reported once: the device words are cleared for the next call
+    CUDA_TRY(cudaMemsetAsync(&h->sc->status, 0, sizeof(int), h->stream));
+    if (mixed(h)) CUDA_TRY(cudaMemsetAsync(tc_error_flag(h->tw), 0, sizeof(int), h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+  }
   if (tce) return fail(SIM_ETIMEOUT, "a bounded tensor-core pipeline wait expired");
   if (st & kStatusTimeout) return fail(SIM_ETIMEOUT, "a bounded device-side wait expired");
   if (st & kStatusNumeric) return fail(SIM_ENUMERIC, "NaN or Inf in forces or kernel result");

@@ -52,6 +52,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // (cooperative launch; callers that run several such grids concurrently keep
 // their total within what the device holds at one time, eig_tridiag_weight).
 constexpr unsigned long long kBarrierNs = 2000000000ull;   // 2 s
+// the wall-time limit the barriers use (per device; tests set it through
+// eig_set_barrier_limit; 0 makes every wait expire at once, even one that
+// would be satisfied, so a test can force the expiry path of a real step)
+__device__ unsigned long long g_barrier_ns = kBarrierNs;
 
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
   __shared__ int s_ok;
@@ -61,7 +65,9 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
     unsigned g = *vgen;
     __threadfence();
     unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == nblocks - 1) {
+    if (g_barrier_ns == 0) {
+      atomicOr(status, (int)kStatusTimeout);
+    } else if (arrived == nblocks - 1) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
@@ -71,7 +77,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
       while (*vgen == g) {
         ++it;
         if ((it & 63) == 0 &&
-            (global_ns() - t0 > kBarrierNs || it > (1LL << 27) ||
+            (global_ns() - t0 > g_barrier_ns || it > (1LL << 27) ||
              ((*(volatile int*)status) & kStatusTimeout))) {
           atomicOr(status, (int)kStatusTimeout);
           break;
@@ -101,12 +107,13 @@ __device__ bool grid_wait(const unsigned* cnt, unsigned target, int* status) {
   if (threadIdx.x == 0) {
     const unsigned long long t0 = global_ns();
     long long it = 0;
-    for (;;) {
+    if (g_barrier_ns == 0) atomicOr(status, (int)kStatusTimeout);
+    for (; g_barrier_ns != 0;) {
       unsigned v;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
       if ((int)(v - target) >= 0) break;
       ++it;
-      if ((it & 63) == 0 && (global_ns() - t0 > kBarrierNs || it > (1LL << 27) ||
+      if ((it & 63) == 0 && (global_ns() - t0 > g_barrier_ns || it > (1LL << 27) ||
                              ((*(volatile int*)status) & kStatusTimeout))) {
         atomicOr(status, (int)kStatusTimeout);
         break;
@@ -1173,6 +1180,10 @@ static bool tridiag_smem_attribute(size_t smem, bool df) {
 }
 
 // (the larger share of the FP64 and the double-float kernel)
+int eig_set_barrier_limit(unsigned long long ns) {
+  return cudaMemcpyToSymbol(g_barrier_ns, &ns, sizeof(ns)) == cudaSuccess ? 0 : -1;
+}
+
 int eig_tridiag_weight(int n, int sm_count) {
   if (n <= 0) return 0;
   int weight = 0;

@@ -71,6 +71,8 @@ int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* 
 // tridiagonalisation grid of size n occupies while resident (blocks divided by
 // blocks per SM).  Grids that run concurrently must sum to <= 1000 x SMs.
 int eig_tridiag_weight(int n, int sm_count);
+// wall-time limit of the eigensolver's grid barriers on the current device (default 2 s)
+int eig_set_barrier_limit(unsigned long long ns);
 // rel_tol: eigenvalues to rel_tol x max(1, ||T||) (1e-12 FP64 path, 1e-9 mixed path)
 // eigenvalues to rel_tol x ||T||; df_path: double-float multisection (mixed path), else FP64 bisection
 void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w, double rel_tol, bool df_path);

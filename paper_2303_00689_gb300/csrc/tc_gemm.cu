@@ -87,8 +87,8 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // bounded wait; returns false on timeout or when another thread flagged an error
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, long long limit = kWaitLimit) {
+  for (long long it = 0; it < limit; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 1023) == 1023 && *(volatile int*)err) return false;
   }
@@ -560,6 +560,16 @@ __global__ void reduce_split_rows_kernel(int rows, int cols, const double* __res
   }
 }
 
+// Test of the bounded wait itself: one thread waits on an mbarrier that no one
+// arrives at (no copy, no tensor-core work in flight), with `limit` tries.
+__global__ void mbar_expiry_kernel(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_fence_init();
+  mbar_wait(&bar, 0, err, limit);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -814,6 +824,11 @@ void tc_reduce_split_rows(cudaStream_t s, int rows, int cols, const double* P, i
                           __nv_bfloat16* base, int ld, size_t stride) {
   if (rows <= 0) return;
   reduce_split_rows_kernel<<<(rows + 7) / 8, 256, 0, s>>>(rows, cols, P, parts, ldp, slices, base, ld, stride);
+  count_launch();
+}
+
+void tc_mbar_expiry(cudaStream_t s, int* err, long long limit) {
+  mbar_expiry_kernel<<<1, 32, 0, s>>>(err, limit);
   count_launch();
 }
 

@@ -59,6 +59,8 @@ void tc_split_blocks(cudaStream_t s, int mode, int n, int nref, int kblk, const 
 // sum of `parts` partial products (rows x cols <= 128, at P + z rows ldp) and its slices
 void tc_reduce_split_rows(cudaStream_t s, int rows, int cols, const double* P, int parts, int ldp, int slices,
                           __nv_bfloat16* base, int ld, size_t stride);
+// test of the pipeline's bounded mbarrier wait: sets *err when `limit` tries expire
+void tc_mbar_expiry(cudaStream_t s, int* err, long long limit);
 // raw access to a slot's slice buffers (for the back-transformation)
 __nv_bfloat16* tc_slot_base(const TcWork& w, int slot);
 size_t tc_slot_stride(const TcWork& w);
