@@ -44,8 +44,11 @@ KERNEL_MODE = [0]      # sim_kernel of the timed runs (--kernel)
 # one (df.cuh), 13 on average over the three multiply-adds of an element
 DF_OPS_PER_FMA = 13.0
 # DRAM bytes (read + write) of one tridiag_df_kernel launch at n = 3360 from one
-# ncu capture of the bench's profile run (dram__bytes_read.sum + dram__bytes_write.sum)
-TRIDIAG_TRAFFIC = {"bytes": None, "source": "not captured for this kernel version"}
+# ncu capture of the bench's profile run (dram__bytes_read.sum 1.018e9 +
+# dram__bytes_write.sum 3.868e10; a one-pass metric set, kernel unchanged since)
+TRIDIAG_TRAFFIC = {"bytes": 1017753856 + 38678435584,
+                   "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one tridiag_df_kernel launch "
+                             "of bench.py --profile-run at n = 3360"}
 
 
 def _dist():
@@ -167,9 +170,9 @@ class Clocks:
         return out
 
 
-def _inputs():
+def _inputs(natoms=None):
     import synth
-    mol = synth.carbon_packing(seed=2, natoms=WORKLOAD["natoms"])
+    mol = synth.carbon_packing(seed=2, natoms=natoms or WORKLOAD["natoms"])
     V = synth.maxwell_boltzmann(mol.Z, 300.0, seed=2)
     table = synth.table_to_array(synth.synthetic_table(1))
     return mol, V, table
@@ -430,7 +433,7 @@ def profile_run(args):
     import paper_2303_00689_gb300 as kx
     from paper_2303_00689_gb300 import build
     build.build()
-    mol, V, table = _inputs()
+    mol, V, table = _inputs(args.profile_natoms)
     X0 = 0.5 * np.eye(mol.norb)      # all-carbon: 4 valence electrons over 4 orbitals, per spin
     prec = kx.SIM_PREC_FP64 if args.precision == "fp64" else kx.SIM_PREC_MIXED
     c0 = kx.sim_launch_count()
@@ -607,37 +610,61 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
+def _fit_slope(t, y):
+    """Least-squares slope of y(t) and its standard error."""
+    A = np.vstack([t, np.ones_like(t)]).T
+    coef, res, _, _ = np.linalg.lstsq(A, y, rcond=None)
+    r = y - A @ coef
+    dof = max(len(t) - 2, 1)
+    se = np.sqrt((r @ r) / dof / ((t - t.mean()) @ (t - t.mean())))
+    return float(coef[0]), float(se)
+
+
 def run_drift(args):
-    """Energy conservation of the shadow dynamics (eq. 26) on six neutral C60
-    cages (360 atoms) at T_e = 5000 K, mixed precision, 200 steps of 0.5 fs:
-    adaptive-rank and fixed-rank Krylov kernels against the XL-BOMD kernel -cI."""
+    """Energy conservation of the shadow dynamics (eq. 26): neutral C60 cages
+    (synthetic table, C-C 1.60 A) at T_e = 5000 K, mixed precision, 0.5 fs.
+    The cages are first thermalised by Langevin dynamics at 300 K (the
+    paper's drifts are for equilibrated systems), then each kernel of eq. 25
+    runs `steps` NVE steps (default 2000 = 1 ps) from the same R, V and
+    density: adaptive- and fixed-rank Krylov against the XL-BOMD kernel -cI.
+    The slope of E_tot(t) per atom is fitted with its standard error."""
     import collections
     import synth
     import paper_2303_00689_gb300 as kx
     from paper_2303_00689_gb300 import build
     build.build()
-    mol = synth.fullerene_c60(copies=6, bond=1.60)
+    mol = synth.fullerene_c60(copies=args.drift_copies, bond=1.60)
     table = kx.param_table(synth.table_to_array(synth.synthetic_table(1)))
-    V = synth.maxwell_boltzmann(mol.Z, 300.0, seed=5)
+    V0 = synth.maxwell_boltzmann(mol.Z, 300.0, seed=5)
+    base = dict(Te=5000.0, dt=0.5, precision=kx.SIM_PREC_MIXED, scf_tol=1e-7, scf_max=300, scf_accept=1)
+    cfg = kx.sim_config_default(m_max=4, m_min=4, langevin_gamma=0.02, langevin_T=300.0, langevin_seed=11,
+                                **base)
+    h = kx.sim_create(cfg, table, mol.Z, mol.R, V=V0)
+    kx.sim_step(h, args.drift_equil, records=False)
+    R, V, _, D = kx.sim_get_state(h, mol.natoms)
+    kx.sim_destroy(h)
     modes = [("krylov adaptive m 4-12, tol 1e-3", dict(m_max=12, m_min=4, krylov_tol=1e-3)),
              ("krylov m 4", dict(m_max=4, m_min=4)),
              ("xl -cI, c = 1", dict(kernel=kx.SIM_KERNEL_XL, xl_c=1.0)),
              ("xl -cI, c = 0.9", dict(kernel=kx.SIM_KERNEL_XL, xl_c=0.9))]
-    nst = args.steps if args.steps > 10 else 200
+    nst = args.steps if args.steps > 10 else 2000
     runs = []
     for name, kw in modes:
-        cfg = kx.sim_config_default(Te=5000.0, dt=0.5, precision=kx.SIM_PREC_MIXED, scf_tol=1e-7, scf_max=300,
-                                    scf_accept=1, **kw)
-        h = kx.sim_create(cfg, table, mol.Z, mol.R, V=V)
+        cfg = kx.sim_config_default(**base, **kw)
+        h = kx.sim_create(cfg, table, mol.Z, R, V=V, P0=D)
         it, res = kx.sim_scf_info(h)
         t = time.perf_counter()
         recs = kx.sim_step(h, nst)
         dt_s = time.perf_counter() - t
         kx.sim_destroy(h)
         E = np.array([r["E_tot"] for r in recs])
-        slope = np.polyfit(np.arange(len(E)) * 0.5e-3, E, 1)[0] / mol.natoms
-        runs.append({"kernel": name, "ms_per_step": 1e3 * dt_s / nst, "drift_eV_per_ps_atom": slope,
+        Ek = np.array([r["E_kin"] for r in recs])
+        t_ps = np.arange(len(E)) * 0.5e-3
+        slope, se = _fit_slope(t_ps, E)
+        runs.append({"kernel": name, "ms_per_step": 1e3 * dt_s / nst,
+                     "drift_eV_per_ps_atom": slope / mol.natoms, "stderr_eV_per_ps_atom": se / mol.natoms,
                      "E_tot_std_eV": float(E.std()), "E_tot_ptp_eV": float(np.ptp(E)),
+                     "E_kin_ptp_eV": float(np.ptp(Ek)), "finite": bool(np.all(np.isfinite(E))),
                      "max_residual": max(r["res_norm"] for r in recs),
                      "ranks": dict(sorted(collections.Counter(r["rank"] for r in recs).items())),
                      "scf": {"iterations": it, "residual": res}})
@@ -645,7 +672,9 @@ def run_drift(args):
            "unit": "eV/ps/atom", "n_gpus": 1, "steps": nst, "warmup": 0,
            "ms_per_step": runs[0]["ms_per_step"], "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64+bf16-slices", "data": "synthetic",
-           "config": {"workload": "6 C60 cages, 360 atoms, n = 1440, C-C 1.60 A", "Te_K": 5000.0, "dt_fs": 0.5},
+           "config": {"workload": f"{args.drift_copies} C60 cages, {mol.natoms} atoms, n = {mol.norb}, C-C 1.60 A",
+                      "Te_K": 5000.0, "dt_fs": 0.5,
+                      "equilibration": f"{args.drift_equil} Langevin steps at 300 K, gamma 0.02/fs, Krylov m 4"},
            "runs": runs}
     print(json.dumps(out), flush=True)
 
@@ -693,6 +722,10 @@ def main():
     p.add_argument("--serve-admit", type=int, default=4, help="server admission threads")
     p.add_argument("--profile-run", action="store_true",
                    help="short run for ncu (no SCF, no baselines); prints launch counts")
+    p.add_argument("--drift-copies", type=int, default=2, help="C60 cages in the drift workload")
+    p.add_argument("--drift-equil", type=int, default=400, help="Langevin steps before the NVE drift runs")
+    p.add_argument("--profile-natoms", type=int, default=None,
+                   help="atoms of the carbon packing in --profile-run (default: the headline 840)")
     args = p.parse_args()
     if args.oracle_sample:
         print(json.dumps(oracle_sample(args.state)), flush=True)

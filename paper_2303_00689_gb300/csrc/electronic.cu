@@ -12,7 +12,6 @@
 
 namespace kx {
 
-constexpr int kRedBlocks = 264;     // partial sums per reduction (multiple of SM pairs)
 constexpr int kRedThreads = 256;
 constexpr int kMaxDots = 24;
 
@@ -336,8 +335,9 @@ void launch_energy(cudaStream_t s, int n, int npair, const double* h, const doub
 
 // ---- fused combination + dot products (one pass over the vectors) -----------------------
 // Per element t: y_i = Y_i[t] (i < ny); val = x[t] - sum_i c_i y_i when combo (c_i = 1
-// when c is null), else x[t]; out[t] = val when out is set; and for each dot j the
-// product of two operands A_j[t] and B_j[t] (a null operand stands for val).
+// when c is null), else x[t]; out[t] = val when out is set; and dot j sums
+// val[t] times its operand: Z_j[t] when Z_j is set, else y_j when dots_on_y (the
+// loaded value is reused), else val[t] itself.
 // Block partials are added in a fixed order by the last block to finish (a
 // counter in Scalars), so each result is deterministic and one launch does it.
 constexpr int kFuseY = 16, kFuseDots = 20;
@@ -346,19 +346,59 @@ struct FuseArgs {
   const double* Y[kFuseY];
   const double* c;
   double* out;
-  int ny, combo, nd;
-  const double* A[kFuseDots];
-  const double* B[kFuseDots];
+  int ny, combo, nd, dots_on_y;
+  const double* Z[kFuseDots];
 };
 
-// MY, MD: compile-time bounds on ny and nd (registers); two elements per thread
-// and iteration (16-byte loads; len is even for the n x n matrices used here,
-// an odd tail is handled by the last thread)
-template <int MY, int MD>
-__global__ void __launch_bounds__(kRedThreads) fused_combo_dots_kernel(size_t len, FuseArgs f,
-                                                                       double* __restrict__ partial,
-                                                                       double* __restrict__ dots_out, Scalars* sc,
-                                                                       int gated) {
+// MY, MD: compile-time bounds on ny and nd (registers).  Each thread handles
+// pairs of elements (16-byte loads; len is even for the n x n matrices used
+// here, an odd tail is handled by the last thread) and issues the loads of U
+// pairs, one grid stride apart, before any arithmetic or store, so a thread
+// keeps U x (loads per element) 16-byte requests in flight.  Storing out
+// after all loads of the batch is safe when out aliases x: each element is
+// read and written by the same thread in the same batch.
+template <int MY, int MD, int U>
+__device__ __forceinline__ void fused_batch(const FuseArgs& f, const double (&cf)[MY], size_t p0, size_t stride,
+                                            int cnt, double (&acc)[MD]) {
+  double2 yv[U][MY], xv[U], zv[U][MD];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (u < cnt) {
+      const size_t p = p0 + (size_t)u * stride;
+      xv[u] = ((const double2*)f.x)[p];
+#pragma unroll
+      for (int i = 0; i < MY; ++i)
+        if (i < f.ny) yv[u][i] = ((const double2*)f.Y[i])[p];
+#pragma unroll
+      for (int j = 0; j < MD; ++j)
+        if (j < f.nd && f.Z[j]) zv[u][j] = ((const double2*)f.Z[j])[p];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (u < cnt) {
+      double2 val = xv[u];
+      if (f.combo) {
+#pragma unroll
+        for (int i = 0; i < MY; ++i)
+          if (i < f.ny) { val.x -= cf[i] * yv[u][i].x; val.y -= cf[i] * yv[u][i].y; }
+      }
+      if (f.out) ((double2*)f.out)[p0 + (size_t)u * stride] = val;
+#pragma unroll
+      for (int j = 0; j < MD; ++j)
+        if (j < f.nd) {
+          double2 b = val;
+          if (f.Z[j]) b = zv[u][j];
+          else if (j < MY && f.dots_on_y && j < f.ny) b = yv[u][j];
+          acc[j] += val.x * b.x + val.y * b.y;
+        }
+    }
+  }
+}
+
+template <int MY, int MD, int U>
+__global__ void __launch_bounds__(kRedThreads, (MY <= 2 ? 4 : (MY <= 8 ? 2 : 1))) fused_combo_dots_kernel(
+    size_t len, FuseArgs f, double* __restrict__ partial, double* __restrict__ dots_out, Scalars* sc, int gated) {
   if (gated && !sc->active) return;
   __shared__ int s_last;
   __shared__ double sred[MD][kRedThreads / 32];
@@ -369,25 +409,13 @@ __global__ void __launch_bounds__(kRedThreads) fused_combo_dots_kernel(size_t le
 #pragma unroll
   for (int i = 0; i < MY; ++i) cf[i] = (i < f.ny) ? (f.c ? f.c[i] : 1.0) : 0.0;
   const size_t npair = len >> 1;
-  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < npair; p += (size_t)gridDim.x * blockDim.x) {
-    double2 yv[MY];
-#pragma unroll
-    for (int i = 0; i < MY; ++i)
-      if (i < f.ny) yv[i] = ((const double2*)f.Y[i])[p];
-    double2 val = ((const double2*)f.x)[p];
-    if (f.combo) {
-#pragma unroll
-      for (int i = 0; i < MY; ++i)
-        if (i < f.ny) { val.x -= cf[i] * yv[i].x; val.y -= cf[i] * yv[i].y; }
-    }
-    if (f.out) ((double2*)f.out)[p] = val;
-#pragma unroll
-    for (int j = 0; j < MD; ++j)
-      if (j < f.nd) {
-        const double2 a = f.A[j] ? ((const double2*)f.A[j])[p] : val;
-        const double2 b = f.B[j] ? ((const double2*)f.B[j])[p] : val;
-        acc[j] += a.x * b.x + a.y * b.y;
-      }
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; p + (size_t)(U - 1) * stride < npair; p += (size_t)U * stride)
+    fused_batch<MY, MD, U>(f, cf, p, stride, U, acc);
+  if (p < npair) {
+    const int rem = (int)((npair - 1 - p) / stride) + 1;     // < U
+    fused_batch<MY, MD, U>(f, cf, p, stride, rem, acc);
   }
   if ((len & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
     const size_t t = len - 1;
@@ -399,7 +427,7 @@ __global__ void __launch_bounds__(kRedThreads) fused_combo_dots_kernel(size_t le
     if (f.out) f.out[t] = val;
 #pragma unroll
     for (int j = 0; j < MD; ++j)
-      if (j < f.nd) acc[j] += (f.A[j] ? f.A[j][t] : val) * (f.B[j] ? f.B[j][t] : val);
+      if (j < f.nd) acc[j] += val * (f.Z[j] ? f.Z[j][t] : ((f.dots_on_y && j < f.ny) ? f.Y[j][t] : val));
   }
   // all dots reduced together: warp shuffles, one CTA barrier, a fixed order
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -435,13 +463,21 @@ __global__ void __launch_bounds__(kRedThreads) fused_combo_dots_kernel(size_t le
   if (threadIdx.x == 0) sc->red_count = 0;
 }
 
+// the smallest instantiation that holds ny and nd; a fixed grid of kRedBlocks
+// (four blocks per SM of a 152-SM GB300) keeps the reduction order, and so
+// the results, independent of the instantiation's occupancy
 static void fused(cudaStream_t s, size_t len, const FuseArgs& f, double* partial, double* dots_out, Scalars* sc,
                   bool gated) {
-  if (f.ny <= 8 && f.nd <= 8)
-    fused_combo_dots_kernel<8, 8><<<kRedBlocks, kRedThreads, 0, s>>>(len, f, partial, dots_out, sc, gated ? 1 : 0);
+  const int g = gated ? 1 : 0;
+  if (f.ny <= 1 && f.nd <= 2)
+    fused_combo_dots_kernel<1, 2, 2><<<kRedBlocks, kRedThreads, 0, s>>>(len, f, partial, dots_out, sc, g);
+  else if (f.ny <= 4 && f.nd <= 4)
+    fused_combo_dots_kernel<4, 4, 2><<<kRedBlocks, kRedThreads, 0, s>>>(len, f, partial, dots_out, sc, g);
+  else if (f.ny <= 8 && f.nd <= 8)
+    fused_combo_dots_kernel<8, 8, 1><<<kRedBlocks, kRedThreads, 0, s>>>(len, f, partial, dots_out, sc, g);
   else
-    fused_combo_dots_kernel<kFuseY, kFuseDots><<<kRedBlocks, kRedThreads, 0, s>>>(len, f, partial, dots_out, sc,
-                                                                                   gated ? 1 : 0);
+    fused_combo_dots_kernel<kFuseY, kFuseDots, 1><<<kRedBlocks, kRedThreads, 0, s>>>(len, f, partial, dots_out,
+                                                                                      sc, g);
   count_launch();
 }
 static FuseArgs fuse_args() {
@@ -493,11 +529,12 @@ __global__ void sub_combo_kernel(size_t len, int k, PtrList V, const double* __r
   v[t] = x;
 }
 
-// scale[0] = 1 / ||v|| from nrm[0] = ||v||^2, nrm[1] = ||src||^2; breakdown
+// scale[0] = 1 / ||v|| from nv2 = ||v||^2, ns2 = ||src||^2; breakdown
 // (invariant subspace) when orthogonalisation left < 1e-10 of the norm
-__global__ void norm_scale_kernel(const double* __restrict__ nrm, Scalars* sc, double* __restrict__ scale) {
+__global__ void norm_scale_kernel(const double* __restrict__ nv2, const double* __restrict__ ns2, Scalars* sc,
+                                  double* __restrict__ scale) {
   if (!sc->active) return;
-  double nv = ::sqrt(nrm[0]), ns = ::sqrt(nrm[1]);
+  double nv = ::sqrt(nv2[0]), ns = ::sqrt(ns2[0]);
   if (nv < 1e-10 * ns || nv == 0.0) {
     sc->active = 0;
     return;
@@ -513,29 +550,31 @@ __global__ void normalize_kernel(size_t len, double* __restrict__ v, const doubl
 }
 
 // k = number of existing vectors V_0..V_{k-1}; src -> v orthonormalised (CGS twice).
-// Fused passes: c1 = <V_i, src>; v = src - sum c1_i V_i with c2 = <V_i, v>;
-// v -= sum c2_i V_i with ||v||^2 and ||src||^2; then v *= 1/||v||.
+// Fused passes: c1 = <V_i, src> with ||src||^2; v = src - sum c1_i V_i with
+// c2 = <V_i, v>; v -= sum c2_i V_i with ||v||^2; then v *= 1/||v||.
 void launch_krylov_orth(cudaStream_t s, size_t len, int k, double* const* Vs, const double* src, double* v,
                         Scalars* sc, double* partial, double* coef) {
   unsigned nb = (unsigned)((len + 255) / 256);
   FuseArgs f = fuse_args();
-  for (int i = 0; i < k; ++i) f.Y[i] = Vs[i];
-  f.ny = k;
+  const double* ns2 = coef + 16;
   if (k > 0) {
-    f.x = src; f.combo = 0; f.out = nullptr; f.nd = k;
-    for (int j = 0; j < k; ++j) f.A[j] = Vs[j];
-    fused(s, len, f, partial, coef, sc, true);                       // c1
+    f.x = src; f.combo = 0; f.out = nullptr; f.ny = 0; f.nd = k + 1;
+    for (int j = 0; j < k; ++j) f.Z[j] = Vs[j];                      // dot k: ||src||^2
+    fused(s, len, f, partial, coef, sc, true);                       // c1 in coef[0..k-1]
+    ns2 = coef + k;
+    for (int i = 0; i < k; ++i) { f.Y[i] = Vs[i]; f.Z[i] = nullptr; }
+    f.ny = k; f.nd = k; f.dots_on_y = 1;
     f.combo = 1; f.c = coef; f.out = v;
     fused(s, len, f, partial, coef + 20, sc, true);                  // v, c2
     f.x = v; f.c = coef + 20;
   } else {
     f.x = src; f.combo = 0; f.out = v;                               // v = src
   }
-  f.nd = 2;
-  f.A[0] = nullptr; f.B[0] = nullptr;
-  f.A[1] = src; f.B[1] = src;
-  fused(s, len, f, partial, coef + 16, sc, true);                    // v (second pass), norms
-  norm_scale_kernel<<<1, 1, 0, s>>>(coef + 16, sc, coef + 18);
+  f.nd = 1;
+  f.dots_on_y = 0;
+  f.Z[0] = nullptr;
+  fused(s, len, f, partial, coef + 16, sc, true);                    // v (second pass), ||v||^2
+  norm_scale_kernel<<<1, 1, 0, s>>>(coef + 16, ns2, sc, coef + 18);
   count_launch();
   normalize_kernel<<<nb, 256, 0, s>>>(len, v, coef + 18, sc);
   count_launch();
@@ -627,8 +666,8 @@ void launch_krylov_w(cudaStream_t s, size_t len, int k, const double* D1, const 
                      int m_min) {
   FuseArgs f = fuse_args();
   f.x = D1; f.Y[0] = v; f.ny = 1; f.combo = 1; f.out = Wk;
-  for (int j = 0; j < k; ++j) f.B[j] = Ws[j];                       // <W_k, W_j>, <W_k, W_k>, <W_k, W0>
-  f.B[k + 1] = W0;
+  for (int j = 0; j < k; ++j) f.Z[j] = Ws[j];                       // <W_k, W_j>, <W_k, W_k>, <W_k, W0>
+  f.Z[k + 1] = W0;
   f.nd = k + 2;
   double* dv = partial + kRedBlocks * kMaxDots + 32;
   fused(s, len, f, partial, dv, sc, true);

@@ -108,8 +108,11 @@ void launch_dmpt_y(cudaStream_t s, int n, const double* F1p, const double* Lam, 
 // U = 2 Tr[h D] + Tr[(2D - X)(F - h)] and V_nn = sum E_pair
 void launch_energy(cudaStream_t s, int n, int npair, const double* h, const double* D,
                    const double* X, const double* F, const double* E, Scalars* sc, double* partial);
-// size in doubles of the reduction workspace ("partial") the launchers above expect
-constexpr size_t kReduceWorkDoubles = 264 * 24 + 128;
+// blocks of the grid-wide reductions (partial sums per reduction: four per SM
+// of a 152-SM GB300) and the size in doubles of the reduction workspace
+// ("partial") the launchers above expect
+constexpr int kRedBlocks = 608;
+constexpr size_t kReduceWorkDoubles = (size_t)kRedBlocks * 24 + 128;
 // out[k] = <A_k, B_k> over n*n elements for k < cnt (deterministic)
 void launch_dots(cudaStream_t s, size_t len, int cnt, const double* const* A, const double* const* B,
                  double* out, double* partial);

@@ -502,6 +502,46 @@ __device__ __forceinline__ void split_row_warp(const RowSplit& q, int r, int sli
     slice_value((k < q.cols) ? x[k] : 0.0, e, slices, q.base, q.stride, (size_t)r * q.ld + k);
 }
 
+// One pass per row of a square n x n operand (a warp per row): the row
+// maximum, then the slices of four consecutive columns per lane, stored as
+// 8-byte groups per slice (ld is a multiple of 64, so every group is aligned);
+// columns n..ld-1 are zeros.  The second sweep of the row re-reads it from
+// L1/L2, so X leaves HBM once.
+__global__ void split_rows_sq_kernel(int n, const double* __restrict__ X, int ld, int slices,
+                                     int* __restrict__ ex, __nv_bfloat16* __restrict__ base, size_t stride,
+                                     const int* gate) {
+  if (gate && *gate == 0) return;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const double* x = X + (size_t)r * n;
+  unsigned long long m = 0;
+  for (int k = lane; k < n; k += 32) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x[k]) & 0x7FFFFFFFFFFFFFFFULL;
+    m = (b > m) ? b : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (t > m) ? t : m;
+  }
+  const int e = exponent_of_max(m);
+  if (lane == 0) ex[r] = e;
+  for (int k0 = 4 * lane; k0 < ld; k0 += 128) {
+    __nv_bfloat16 v[4][kTcMaxSlices];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) slice_digits((k0 + c < n) ? x[k0 + c] : 0.0, e, slices, v[c]);
+    for (int a = 0; a < slices; ++a) {
+      __nv_bfloat162 lo2, hi2;
+      lo2.x = v[0][a]; lo2.y = v[1][a];
+      hi2.x = v[2][a]; hi2.y = v[3][a];
+      uint2 w;
+      w.x = *(const uint32_t*)&lo2;
+      w.y = *(const uint32_t*)&hi2;
+      *(uint2*)(base + a * stride + (size_t)r * ld + k0) = w;
+    }
+  }
+}
+
 __global__ void split_rows_kernel(RowSplit q, int slices) {
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (r >= q.rows) return;
@@ -685,6 +725,12 @@ void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int sl
   TcBuffers* tb = (TcBuffers*)w.base;
   int n = tb->n;
   int* ex = tb->ex + (size_t)slot * n;
+  if (!transpose) {
+    split_rows_sq_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, X, tb->ld, slices, ex, tb->piece[slot][0],
+                                                              (size_t)(tb->piece[0][1] - tb->piece[0][0]), gate);
+    count_launch();
+    return;
+  }
   row_exponent_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, X, transpose, ex, gate);
   count_launch();
   size_t tot = (size_t)n * tb->ld;

@@ -1,8 +1,14 @@
-"""Energy conservation of the GPU shadow dynamics (eq. 26) with the adaptive
-Krylov kernel, mixed precision: two neutral C60 cages at T_e = 5000 K, 120
-steps of 0.5 fs.  The shadow energy E_tot = kinetic + U(R, X) must not drift
-beyond its fluctuation, and the residual D0 - X must stay small (no runaway of
-the extended electronic degrees of freedom)."""
+"""Energy conservation of the GPU shadow dynamics (eq. 26), mixed precision:
+two neutral C60 cages at T_e = 5000 K, thermalised by 400 Langevin steps at
+300 K, then 2000 NVE steps of 0.5 fs (1 ps) with the adaptive Krylov kernel
+and with the XL-BOMD kernel -cI from the same R, V and density.
+
+The slope of E_tot(t) per atom is held to a bound about four times the
+measured value (adaptive Krylov 2.7e-6 +- 1.0e-6 eV/ps/atom, XL -cI
+-1.7e-5 +- 1.7e-6 on GB300), so a drift ten times larger fails; E_tot
+fluctuates by about a thousandth of the kinetic energy's swing, and the
+residual D0 - X stays small (no runaway of the extended electronic degrees
+of freedom)."""
 import numpy as np
 import pytest
 
@@ -12,6 +18,9 @@ from tests.gpu_helpers import table
 
 pytestmark = pytest.mark.gpu
 
+STEPS = 2000
+BOUND = {"krylov-adaptive": 1.2e-5, "xl": 7e-5}   # eV/ps/atom
+
 
 @pytest.fixture(scope="module", autouse=True)
 def built():
@@ -19,28 +28,42 @@ def built():
     build.build()
 
 
-@pytest.mark.parametrize("kernel", ["krylov-adaptive", "xl"])
-def test_shadow_energy_is_conserved(kernel):
+@pytest.fixture(scope="module")
+def thermalised():
     mol = synth.fullerene_c60(copies=2, bond=1.60)
-    kw = dict(m_max=12, m_min=4, krylov_tol=1e-3) if kernel != "xl" else dict(kernel=kx.SIM_KERNEL_XL, xl_c=1.0)
+    tab = kx.param_table(synth.table_to_array(table()))
     cfg = kx.sim_config_default(Te=5000.0, dt=0.5, precision=kx.SIM_PREC_MIXED, scf_tol=1e-7, scf_max=300,
-                                scf_accept=1, **kw)
-    h = kx.sim_create(cfg, kx.param_table(synth.table_to_array(table())), mol.Z, mol.R,
-                      V=synth.maxwell_boltzmann(mol.Z, 300.0, seed=5))
+                                scf_accept=1, m_max=4, m_min=4, langevin_gamma=0.02, langevin_T=300.0,
+                                langevin_seed=11)
+    h = kx.sim_create(cfg, tab, mol.Z, mol.R, V=synth.maxwell_boltzmann(mol.Z, 300.0, seed=5))
     try:
-        recs = kx.sim_step(h, 120)
+        kx.sim_step(h, 400, records=False)
+        R, V, _, D = kx.sim_get_state(h, mol.natoms)
+    finally:
+        kx.sim_destroy(h)
+    return mol, tab, R, V, D
+
+
+@pytest.mark.parametrize("kernel", ["krylov-adaptive", "xl"])
+def test_shadow_energy_is_conserved(thermalised, kernel):
+    mol, tab, R, V, D = thermalised
+    kw = dict(m_max=12, m_min=4, krylov_tol=1e-3) if kernel != "xl" else dict(kernel=kx.SIM_KERNEL_XL, xl_c=1.0)
+    cfg = kx.sim_config_default(Te=5000.0, dt=0.5, precision=kx.SIM_PREC_MIXED, **kw)
+    h = kx.sim_create(cfg, tab, mol.Z, R, V=V, P0=D)
+    try:
+        recs = kx.sim_step(h, STEPS)
     finally:
         kx.sim_destroy(h)
     E = np.array([r["E_tot"] for r in recs])
     Ekin = np.array([r["E_kin"] for r in recs])
     assert np.all(np.isfinite(E))
     t_ps = np.arange(len(E)) * 0.5e-3
-    slope = np.polyfit(t_ps, E, 1)[0]
-    # kinetic energy swings by eV while E_tot stays within a small fraction of that
-    assert np.ptp(Ekin) > 10 * E.std()
-    # no systematic drift beyond the fluctuation over the 60 fs window
-    assert abs(slope) * t_ps[-1] < 3 * E.std() + 1e-3
-    assert max(r["res_norm"] for r in recs) < 0.2
+    slope = np.polyfit(t_ps, E, 1)[0] / mol.natoms
+    print(f"\n{kernel}: drift {slope:.3e} eV/ps/atom, std E_tot {E.std():.2e} eV, "
+          f"ptp E_kin {np.ptp(Ekin):.3f} eV, max ||D0 - X|| {max(r['res_norm'] for r in recs):.3e}")
+    assert abs(slope) < BOUND[kernel]
+    assert E.std() < 5e-3 * np.ptp(Ekin)
+    assert max(r["res_norm"] for r in recs) < 0.1
     if kernel != "xl":
         assert all(4 <= r["rank"] <= 12 for r in recs)
     else:
