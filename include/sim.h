@@ -415,6 +415,14 @@ int sim_tc_gemm_noalloc(int n, const double* A, const double* B, int terms, int 
  * memory; synchronous. */
 int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sym, double* C);
 
+/* sim_debug_tc_gemm_grouped -- the same 3-slice product (terms = 6) computed
+ * the way the mixed path's DMPT products of eq. 36 are: all slices of a
+ * 64-deep k-tile staged together, the weight-1 slice product summed exactly
+ * per 512-K chunk and the lower-weight ones in FP32, so C is within ~2^-26 of
+ * sum_k |A_ik||B_jk| of the exact 6-term slice product (not bitwise equal).
+ * Arguments, memory and errors as sim_debug_tc_gemm. */
+int sim_debug_tc_gemm_grouped(int n, const double* A, const double* B, int sym, double* C);
+
 /* sim_measure_peak -- FMA throughput of `device` in TFLOP/s (2 flops per FMA),
  * kind 0: FP64, kind 1: FP32; 8 independent chains per thread on 8 blocks of
  * 256 threads per SM, timed with CUDA events after a warm-up launch.  The

@@ -27,6 +27,7 @@ EXPORTED = (
     "sim_last_result", "sim_get_state", "sim_set_state", "sim_get_matrix", "sim_get_vector",
     "sim_profile_enable", "sim_phase_count", "sim_phase_name", "sim_phase_times",
     "sim_launch_count", "sim_stream", "sim_destroy", "sim_last_error", "sim_debug_tc_gemm",
+    "sim_debug_tc_gemm_grouped",
     "sim_tc_gemm_noalloc", "sim_records", "sim_wait", "sim_enable_graphs", "sim_batch_step",
     "sim_estimate_bytes", "sim_server_create", "sim_submit", "sim_poll", "sim_server_stats_get",
     "sim_server_drain", "sim_server_destroy", "sim_save", "sim_load", "sim_batch_create", "sim_batch_run",
@@ -125,6 +126,7 @@ def lib():
         L.sim_destroy.argtypes = [C.c_void_p]
         L.sim_destroy.restype = None
         L.sim_debug_tc_gemm.argtypes = [C.c_int, dp, dp, C.c_int, C.c_int, dp]
+        L.sim_debug_tc_gemm_grouped.argtypes = [C.c_int, dp, dp, C.c_int, dp]
         L.sim_tc_gemm_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                           C.c_void_p]
         L.sim_records.argtypes = [C.c_void_p, P(sim_step_result), C.c_int]
@@ -314,6 +316,15 @@ def sim_debug_tc_gemm(A, B, terms=1, sym=False):
     n = A.shape[0]
     out = np.empty((n, n))
     _check(lib().sim_debug_tc_gemm(n, _dptr(A), _dptr(B), int(terms), 1 if sym else 0, _dptr(out)))
+    return out
+
+
+def sim_debug_tc_gemm_grouped(A, B, sym=False):
+    A = _f64(A)
+    B = _f64(B)
+    n = A.shape[0]
+    out = np.empty((n, n))
+    _check(lib().sim_debug_tc_gemm_grouped(n, _dptr(A), _dptr(B), 1 if sym else 0, _dptr(out)))
     return out
 
 

@@ -252,17 +252,18 @@ static void dmpt(sim_handle* h, const double* F1, double* D1) {
   int n = h->n;
   const int* g = &h->sc->active;
   if (mixed(h)) {
-    // three fixed-point BF16 slices per operand, six slice products (24 bits per row scale)
+    // three fixed-point BF16 slices per operand, six slice products (24 bits per row
+    // scale), all slices of a k-tile staged together (tc_gemm_grouped)
     tc_split(s, h->tw, kSlotT0, F1, 3, 0, g);
-    tc_gemm(s, h->tw, kSlotQt, kSlotT0, 6, 1.0, h->T1, 0, g);      // T1 = Q^T F1
+    tc_gemm_grouped(s, h->tw, kSlotQt, kSlotT0, 1.0, h->T1, 0, g);      // T1 = Q^T F1
     tc_split(s, h->tw, kSlotT1, h->T1, 3, 0, g);
-    tc_gemm(s, h->tw, kSlotT1, kSlotQt, 6, 1.0, h->T2, 1, g);      // T2 = (Q^T F1) Q
+    tc_gemm_grouped(s, h->tw, kSlotT1, kSlotQt, 1.0, h->T2, 1, g);      // T2 = (Q^T F1) Q
     launch_dmu(s, n, h->T2, h->eps, h->f, h->beta, h->sc);
     launch_dmpt_y(s, n, h->T2, h->K, h->sc, h->Y);     // h->K holds Lambda until the final combine
     tc_split(s, h->tw, kSlotT0, h->Y, 3, 0, g);
-    tc_gemm(s, h->tw, kSlotQ, kSlotT0, 6, 1.0, h->T1, 0, g);       // T1 = Q Y
+    tc_gemm_grouped(s, h->tw, kSlotQ, kSlotT0, 1.0, h->T1, 0, g);       // T1 = Q Y
     tc_split(s, h->tw, kSlotT1, h->T1, 3, 0, g);
-    tc_gemm(s, h->tw, kSlotT1, kSlotQ, 6, 1.0, D1, 1, g);          // D1 = (Q Y) Q^T
+    tc_gemm_grouped(s, h->tw, kSlotT1, kSlotQ, 1.0, D1, 1, g);          // D1 = (Q Y) Q^T
     return;
   }
   dgemm(s, 0, 0, n, n, n, 1.0, F1, n, h->Q, n, 0.0, h->T1, n, 0, g);         // T1 = F1 Q
@@ -1366,8 +1367,9 @@ int sim_phase_times(sim_handle* h, double* ms, long long* launches, double* work
   return SIM_OK;
 }
 
-// Test hook: C = sum of BF16-piece products of A and B^T on the tensor cores.
-int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sym, double* C) {
+// Test hooks: C = sum of BF16-piece products of A and B^T on the tensor cores
+// (terms 1, 3, 6, 10: the exact per-segment kernel; grouped: the DMPT's 3-slice kernel).
+static int debug_tc_gemm(int n, const double* A, const double* B, int terms, int sym, bool grouped, double* C) {
   if (n < 1 || !A || !B || !C || (terms != 1 && terms != 3 && terms != 6 && terms != 10))
     return fail(SIM_EINVAL, "bad argument");
   if (!tc_available()) return fail(SIM_EINVAL, "tensor-map entry point unavailable");
@@ -1392,7 +1394,10 @@ int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sy
     cudaMemset(dC, 0, nn * sizeof(double));
     tc_split(s, w, kSlotT0, dA, pieces, 0);
     tc_split(s, w, kSlotT1, dB, pieces, 0);
-    tc_gemm(s, w, kSlotT0, kSlotT1, terms, 1.0, dC, sym);
+    if (grouped)
+      tc_gemm_grouped(s, w, kSlotT0, kSlotT1, 1.0, dC, sym);
+    else
+      tc_gemm(s, w, kSlotT0, kSlotT1, terms, 1.0, dC, sym);
     int err = 0;
     cudaError_t ce = cudaDeviceSynchronize();
     cudaMemcpy(&err, tc_error_flag(w), sizeof(int), cudaMemcpyDeviceToHost);
@@ -1403,6 +1408,14 @@ int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sy
   tc_work_release(w);
   cudaFree(arena);
   return rc;
+}
+
+int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sym, double* C) {
+  return debug_tc_gemm(n, A, B, terms, sym, false, C);
+}
+
+int sim_debug_tc_gemm_grouped(int n, const double* A, const double* B, int sym, double* C) {
+  return debug_tc_gemm(n, A, B, 6, sym, true, C);
 }
 
 void sim_destroy(sim_handle* h) {

@@ -162,6 +162,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 8 consecutive TMEM columns (the grouped kernel's epilogue folds two
+// accumulators per chunk and keeps its double-float registers without spills)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 struct TcMaps {
   CUtensorMap a[kTcMaxSlices];
   CUtensorMap b[kTcMaxSlices];
@@ -334,6 +343,196 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kBN) : "memory");
+  }
+}
+
+// Slice-grouped product of two 3-slice operands (the DMPT products of eq. 36).
+// Same tile, warps and bounded waits as tc_gemm_kernel, but one pipeline stage
+// holds all three slices of A and of B for one 64-deep k-tile (96 KB), and
+// the six kept slice products of that k-tile are issued from it: every byte
+// brought into shared memory feeds twice the tensor-core work of the
+// per-segment kernel.  Two accumulators per TMEM buffer:
+//   acc0  : A0 B0, summed exactly over a 512-K chunk (as in tc_gemm_kernel);
+//   acc12 : A0 B1 + A1 B0 + A0 B2 + A1 B1 + A2 B0, weights 2^-8 and 2^-16 of
+//           acc0's, summed in FP32 over the chunk.
+// Both are folded into the double-float registers after every chunk.  The
+// FP32 rounding of acc12 is at most ~2^-26 of sum |a||b| per entry, below the
+// 2^-20 truncation of three slices, so the result is the 3-slice product to
+// within that bound rather than bitwise the sum of its slice products.
+// TMEM: 4 x 128 columns (acc0 and acc12, double-buffered).
+constexpr int kGSlices = 3;
+constexpr int kGStages = 2;
+constexpr int kGStageBytes = 2 * kGSlices * kTileBytesA;                 // 96 KB
+constexpr int kGSmemBytes = kGStages * kGStageBytes + 1024 + 256;
+static_assert(kBM * (kBN + 1) * (int)sizeof(double) <= kGStages * kGStageBytes, "output tile fits the stages");
+
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_grouped_kernel(const __grid_constant__ TcMaps maps, int n, double alpha, double* __restrict__ C,
+                           int ldc, int sym, int* err, const int* gate) {
+  if (gate && *gate == 0) return;      // whole CTA, before any barrier or TMEM use
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (sym && bi > bj) return;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(base + kGStages * kGStageBytes);
+  uint64_t* empty = full + kGStages;
+  uint64_t* acc_full = empty + kGStages;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = bi * kBM, n0 = bj * kBN;
+  const int ktiles = (n + kBK - 1) / kBK;
+  const int nchunks = (ktiles + kChunk - 1) / kChunk;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kGStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kEpiWarps);
+    }
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(4 * kBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer: the three slices of A and of B of k-tile `it` into one stage
+      int issued = 0;
+      bool ok = true;
+      for (int it = 0; it < ktiles && ok; ++it) {
+        const int st = it % kGStages;
+        const uint32_t ph = (uint32_t)(it / kGStages) & 1u;
+        if (!mbar_wait(&empty[st], ph ^ 1u, err)) { ok = false; break; }
+        uint8_t* sbase = base + st * kGStageBytes;
+        mbar_expect_tx(&full[st], kGStageBytes);
+#pragma unroll
+        for (int a = 0; a < kGSlices; ++a) {
+          tma_load_2d(sbase + a * kTileBytesA, &maps.a[a], &full[st], it * kBK, m0);
+          tma_load_2d(sbase + (kGSlices + a) * kTileBytesA, &maps.b[a], &full[st], it * kBK, n0);
+        }
+        issued = it + 1;
+      }
+      if (!ok) {
+        for (int it = (issued > kGStages ? issued - kGStages : 0); it < issued; ++it) {
+          const int st = it % kGStages;
+          const uint32_t ph = (uint32_t)(it / kGStages) & 1u;
+          for (long long w = 0; w < kWaitLimit && !mbar_try(&full[st], ph); ++w) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc();
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int b = c & 1;
+        if (!mbar_wait(&acc_empty[b], ((uint32_t)(c >> 1) & 1u) ^ 1u, err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d0 = tmem + (uint32_t)(b * kBN);
+        const uint32_t d12 = tmem + (uint32_t)((2 + b) * kBN);
+        const int it0 = c * kChunk;
+        const int it1 = (it0 + kChunk < ktiles) ? it0 + kChunk : ktiles;
+        for (int it = it0; it < it1; ++it) {
+          const int st = it % kGStages;
+          const uint32_t ph = (uint32_t)(it / kGStages) & 1u;
+          if (!mbar_wait(&full[st], ph, err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(base + st * kGStageBytes);
+          const uint32_t sb = sa + kGSlices * kTileBytesA;
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) {
+            const uint32_t first = (it > it0 || k > 0) ? 1u : 0u;
+            // weight 1: A0 B0
+            umma_bf16(d0, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, first);
+            // weights 2^-16 then 2^-8 (smallest first)
+            umma_bf16(d12, smem_desc(sa + 2 * kTileBytesA + k * 32), smem_desc(sb + k * 32), idesc, first);
+            umma_bf16(d12, smem_desc(sa + kTileBytesA + k * 32), smem_desc(sb + kTileBytesA + k * 32), idesc, 1u);
+            umma_bf16(d12, smem_desc(sa + k * 32), smem_desc(sb + 2 * kTileBytesA + k * 32), idesc, 1u);
+            umma_bf16(d12, smem_desc(sa + kTileBytesA + k * 32), smem_desc(sb + k * 32), idesc, 1u);
+            umma_bf16(d12, smem_desc(sa + k * 32), smem_desc(sb + kTileBytesA + k * 32), idesc, 1u);
+          }
+          umma_commit(&empty[st]);
+        }
+        if (ok) umma_commit(&acc_full[b]);
+      }
+    }
+  } else {
+    // epilogue warps: fold both accumulators of each chunk into double-float registers
+    const int quarter = warp & 3;
+    const int cg = (warp - 2) >> 2;
+    float hi[32], lo[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) { hi[j] = 0.0f; lo[j] = 0.0f; }
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1;
+      bool got = mbar_wait(&acc_full[b], (uint32_t)(c >> 1) & 1u, err);
+      got = __all_sync(0xffffffffu, got);
+      if (!got) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        uint32_t r[8];
+        tmem_ld8(tmem + lane_base + (uint32_t)(b * kBN + cg * 32 + h * 8), r);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) twosum_acc(hi[h * 8 + j], lo[h * 8 + j], __uint_as_float(r[j]));
+        tmem_ld8(tmem + lane_base + (uint32_t)((2 + b) * kBN + cg * 32 + h * 8), r);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) twosum_acc(hi[h * 8 + j], lo[h * 8 + j], __uint_as_float(r[j]));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+    }
+    // The tile goes through shared memory (the pipeline stages are idle once
+    // the last chunk has been read): the thread's 32 values at constant
+    // offsets, then row-contiguous stores of the tile and, for a symmetric
+    // result, of its transpose.  Every epilogue warp reaches the named
+    // barrier; the global stores run only when no wait of any CTA expired.
+    constexpr int kLdT = kBN + 1;                      // padded row: conflict-free transposed reads
+    double* tile = (double*)base;
+    if (ok) {
+      const int rl = quarter * 32 + lane;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tile[rl * kLdT + cg * 32 + j] = alpha * ((double)hi[j] + (double)lo[j]);
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");
+    if (ktiles > 0 && *(volatile int*)err == 0) {
+      const int t = threadIdx.x - 64;
+      for (int idx = t; idx < kBM * kBN; idx += kEpiWarps * 32) {
+        const int rr = idx / kBN, cc = idx - rr * kBN;
+        const int row = m0 + rr, col = n0 + cc;
+        if (row < n && col < n && !(sym && row > col)) C[(size_t)row * ldc + col] = tile[rr * kLdT + cc];
+      }
+      if (sym) {
+        // C[col][row] for row < col: rows of the output are columns of the tile
+        for (int idx = t; idx < kBM * kBN; idx += kEpiWarps * 32) {
+          const int cr = idx / kBM, rc = idx - cr * kBM;   // output row n0 + cr, column m0 + rc
+          const int row = m0 + rc, col = n0 + cr;
+          if (row < n && col < n && row < col) C[(size_t)col * ldc + row] = tile[rc * kLdT + cr];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * kBN) : "memory");
   }
 }
 
@@ -761,6 +960,25 @@ void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, d
   int n = tb->n;
   dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
   tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, seg, n, n, n, alpha, C, n, sym, 0, tb->err, gate, 0, 0);
+  count_launch();
+}
+
+void tc_gemm_grouped(cudaStream_t s, const TcWork& w, int slotA, int slotB, double alpha, double* C, int sym,
+                     const int* gate) {
+  TcBuffers* tb = (TcBuffers*)w.base;
+  static PerDeviceOnce flag;
+  once_per_device(flag, [] {
+    return cudaFuncSetAttribute(tc_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemBytes) ==
+           cudaSuccess;
+  });
+  TcMaps maps;
+  for (int k = 0; k < kTcMaxSlices; ++k) {
+    maps.a[k] = tb->map[slotA][k];
+    maps.b[k] = tb->map[slotB][k];
+  }
+  const int n = tb->n;
+  dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
+  tc_gemm_grouped_kernel<<<grid, kThreads, kGSmemBytes, s>>>(maps, n, alpha, C, n, sym, tb->err, gate);
   count_launch();
 }
 

@@ -29,6 +29,12 @@ void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int sl
 void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, double alpha, double* C,
              int sym, const int* gate = nullptr);
 
+// The DMPT's 3-slice product (terms 6) with all slices of a k-tile staged together:
+// the weight-1 slice product summed exactly per 512-K chunk, the lower-weight ones
+// in FP32; within 2^-26 of sum |a||b| of the exact 6-term slice product
+void tc_gemm_grouped(cudaStream_t s, const TcWork& w, int slotA, int slotB, double alpha, double* C, int sym,
+                     const int* gate = nullptr);
+
 // Building blocks on caller-provided buffers (used by the allocation-free entry point)
 int tc_ld(int n);                                                   // padded slice row length
 bool tc_encode_map(CUtensorMap* m, void* ptr, int n, int ld);       // BF16 slice tensor map

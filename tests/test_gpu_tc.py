@@ -78,3 +78,26 @@ def test_tc_gemm_symmetric_output(n):
     exact = A @ A.T
     scale = np.abs(A) @ np.abs(A).T
     assert np.max(np.abs(C - exact) / scale) < 2.0 ** -26
+
+
+@pytest.mark.parametrize("n", [64, 128, 200, 333, 700, 1100])
+@pytest.mark.parametrize("sym", [False, True])
+def test_grouped_product_is_the_three_slice_product(n, sym):
+    """The DMPT's slice-grouped kernel: the weight-1 slice product is summed
+    exactly per chunk, the lower-weight ones in FP32, so the result is the
+    exact 6-term slice product to within 2^-24 of sum |a||b| (the bound the
+    kernel's FP32 accumulation of weights 2^-8 and 2^-16 gives, with margin)
+    and the FP64 product to within the 3-slice truncation 2^-20."""
+    rng = np.random.default_rng(n + 7 * sym)
+    A = rng.normal(size=(n, n)) * np.exp(rng.normal(size=(n, 1)))
+    B = A if sym else rng.normal(size=(n, n))
+    C = kx.sim_debug_tc_gemm_grouped(A, B, sym=sym)
+    pa, pb = slices(A, 3), slices(B, 3)
+    ref = sum(pa[i] @ pb[j].T for i, j in kept_pairs(3))
+    scale = np.abs(A) @ np.abs(B).T
+    err_slices = np.max(np.abs(C - ref) / scale)
+    err_exact = np.max(np.abs(C - A @ B.T) / scale)
+    assert err_slices < 2.0 ** -24, err_slices
+    assert err_exact < 2.0 ** -20, err_exact
+    if sym:
+        assert np.array_equal(C, C.T)
