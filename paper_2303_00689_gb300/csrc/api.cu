@@ -83,6 +83,7 @@ struct sim_handle {
   int *elem = nullptr, *off = nullptr, *pA = nullptr, *pB = nullptr;
   double *R = nullptr, *V = nullptr, *F = nullptr, *mass = nullptr, *g = nullptr;
   double *W = nullptr, *S = nullptr, *E = nullptr, *dW = nullptr, *dS = nullptr, *dE = nullptr;
+  double* cw = nullptr;
   double *h = nullptr, *Fock = nullptr, *D = nullptr, *K = nullptr, *Q = nullptr, *Qs = nullptr;
   double *eps = nullptr, *f = nullptr, *Dd = nullptr, *Pd = nullptr, *Vd = nullptr;
   double *T1 = nullptr, *T2 = nullptr, *F1 = nullptr, *Y = nullptr, *D1 = nullptr, *W0 = nullptr;
@@ -218,7 +219,7 @@ static void collect_events(sim_handle* h) {
 // device orchestration
 // ---------------------------------------------------------------------------
 static MolDev mol(const sim_handle* h) { return MolDev{h->N, h->n, h->npair, h->elem, h->off, h->pA, h->pB}; }
-static PairDev pairs(const sim_handle* h) { return PairDev{h->W, h->S, h->E, h->dW, h->dS, h->dE}; }
+static PairDev pairs(const sim_handle* h) { return PairDev{h->W, h->S, h->E, h->dW, h->dS, h->dE, h->cw}; }
 static double* xslot(sim_handle* h, int k) { return h->X[(h->xhead + k) % 8]; }
 
 static bool mixed(const sim_handle* h) { return h->cfg.precision == SIM_PREC_MIXED; }
@@ -584,6 +585,7 @@ static void layout(sim_handle* h, Arena& a) {
   h->dW = a.take<double>(300 * np);
   h->dS = a.take<double>(48 * np);
   h->dE = a.take<double>(3 * np);
+  h->cw = a.take<double>(10 * (size_t)h->N * h->N);
   h->h = a.take<double>(nn);
   h->Fock = a.take<double>(nn);
   h->D = a.take<double>(nn);

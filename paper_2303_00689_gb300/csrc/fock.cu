@@ -11,9 +11,13 @@
 //     2 Tr[h D] + Tr[(2D - P) G(P)] + V_nn at fixed D, P contracted with the
 //     stored dW, dS, dE blocks; F_A += g, F_B -= g with g = dE/dd, d = R_B - R_A.
 //
-// Diagonal blocks are gathered per atom by one block (deterministic order, no
-// atomics); off-diagonal blocks are written by one thread per pair into the
-// upper triangle and mirrored by a tiled transpose.
+// h: diagonal blocks are gathered per atom by one block (deterministic order,
+// no atomics); off-diagonal blocks by one thread per pair.
+// F = h + G(P): one thread per pair reads its 100 integrals once, writes both
+// off-diagonal blocks (exchange) and the pair's Coulomb contributions to the
+// diagonal blocks of both atoms into cw[X][Y][10] (X the receiving atom);
+// one warp per atom then sums its row of cw in a fixed order and adds the
+// one-centre terms.  No atomics: the result does not depend on scheduling.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -138,136 +142,218 @@ __global__ void h_offdiag_kernel(MolDev m, PairDev pd, ElemTable tab, double* __
     }
 }
 
-__global__ void __launch_bounds__(kDiagThreads)
-    fock_diag_kernel(MolDev m, PairDev pd, ElemTable tab, const double* __restrict__ P,
-                     const double* __restrict__ Pd, const double* __restrict__ h, double* __restrict__ out,
-                     const int* gate) {
+// Orbital products on one atom: ss, sx, sy, sz, xx, yy, zz, xy, xz, yz.
+// pair_cnt(p) ordered orbital pairs (mu, nu) make up product p; the i-th is
+// (pair_mu(p, i), pair_nu(p, i)).  Written as constexpr functions so that in
+// the fully unrolled loops below every index is a compile-time constant.
+__host__ __device__ constexpr int pair_cnt(int p) { return (p == 0 || (p >= 4 && p <= 6)) ? 1 : 2; }
+__host__ __device__ constexpr int pair_mu(int p, int i) {
+  return p == 0 ? 0
+       : p < 4  ? (i == 0 ? 0 : p)
+       : p < 7  ? p - 3
+       : p == 7 ? (i == 0 ? 1 : 2)
+       : p == 8 ? (i == 0 ? 1 : 3)
+                : (i == 0 ? 2 : 3);
+}
+__host__ __device__ constexpr int pair_nu(int p, int i) {
+  return p == 0 ? 0
+       : p < 4  ? (i == 0 ? p : 0)
+       : p < 7  ? p - 3
+       : p == 7 ? (i == 0 ? 2 : 1)
+       : p == 8 ? (i == 0 ? 3 : 1)
+                : (i == 0 ? 3 : 2);
+}
+__host__ __device__ constexpr double pair_mult(int p) { return (double)pair_cnt(p); }
+
+// one thread per pair (A < B): exchange blocks F_AB, F_BA = F_AB^T (plus h) and
+// the Coulomb contributions cw[A][B][P] = sum_q m_q Pd_B[q] W[P][q],
+// cw[B][A][q] = sum_P m_P Pd_A[P] W[P][q] (m = product multiplicity)
+__global__ void __launch_bounds__(128) fock_pair_kernel(MolDev m, PairDev pd, ElemTable tab,
+                                                       const double* __restrict__ P,
+                                                       const double* __restrict__ Pd, const double* __restrict__ h,
+                                                       double* __restrict__ out, const int* gate) {
   if (gate && *gate == 0) return;
-  int A = blockIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m.npair) return;
+  const int A = m.pA[t], B = m.pB[t];
+  const int na = tab.e[m.elem[A]].norb, nb = tab.e[m.elem[B]].norb;
+  const int oa = m.off[A], ob = m.off[B];
+  const size_t np = (size_t)m.npair;
+  const size_t n = (size_t)m.n;
+  double pab[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) pab[a][b] = (a < na && b < nb) ? P[(oa + a) * n + ob + b] : 0.0;
+  double da[10], db[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    da[k] = pair_mult(k) * Pd[(size_t)A * 10 + k];
+    db[k] = pair_mult(k) * Pd[(size_t)B * 10 + k];
+  }
+  double g[4][4], ca[10], cb[10];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) g[a][b] = 0.0;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) { ca[k] = 0.0; cb[k] = 0.0; }
+  const int qa = (na == 4) ? 10 : 1, qb = (nb == 4) ? 10 : 1;
+#pragma unroll
+  for (int pp = 0; pp < 10; ++pp) {
+#pragma unroll
+    for (int qq = 0; qq < 10; ++qq) {
+      if (pp < qa && qq < qb) {
+        const double w = pd.W[(size_t)(pp * 10 + qq) * np + t];
+        ca[pp] += db[qq] * w;
+        cb[qq] += da[pp] * w;
+        // exchange: g[mu][la] -= P[nu][si] (mu nu | la si) over the orbital pairs of pp, qq
+#pragma unroll
+        for (int i = 0; i < pair_cnt(pp); ++i)
+#pragma unroll
+          for (int j = 0; j < pair_cnt(qq); ++j)
+            g[pair_mu(pp, i)][pair_mu(qq, j)] -= pab[pair_nu(pp, i)][pair_nu(qq, j)] * w;
+      }
+    }
+  }
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+    for (int la = 0; la < 4; ++la) {
+      if (mu < na && la < nb) {
+        const size_t ix = (oa + mu) * n + ob + la, jx = (ob + la) * n + oa + mu;
+        const double v = (h ? h[ix] : 0.0) + g[mu][la];
+        out[ix] = v;
+        out[jx] = v;
+      }
+    }
+  double* cA = pd.cw + ((size_t)A * m.N + B) * 10;
+  double* cB = pd.cw + ((size_t)B * m.N + A) * 10;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) { cA[k] = ca[k]; cB[k] = cb[k]; }
+}
+
+// one warp per atom: Coulomb sums over partners (lanes over partners, fixed
+// order), then the diagonal block with the one-centre terms (eq. 3)
+__global__ void fock_atom_kernel(MolDev m, PairDev pd, ElemTable tab, const double* __restrict__ Pd,
+                                 const double* __restrict__ h, double* __restrict__ out, const int* gate) {
+  if (gate && *gate == 0) return;
+  const int A = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (A >= m.N) return;
   double acc[10];
-  gather_diag(A, m, pd, tab, Pd, 0, acc);
-  if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+  const double* row = pd.cw + (size_t)A * m.N * 10;
+  for (int Y = lane; Y < m.N; Y += 32) {
+    if (Y == A) continue;
+    const double* c = row + (size_t)Y * 10;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] += c[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 10; ++k) acc[k] = warp_sum(acc[k]);
+  if (lane != 0) return;
   const Elem& e = tab.e[m.elem[A]];
-  int o = m.off[A], no = m.off[A + 1] - o;
+  const int o = m.off[A], no = m.off[A + 1] - o;
   const double* pa = Pd + (size_t)A * 10;
   for (int mu = 0; mu < no; ++mu)
     for (int nu = 0; nu < no; ++nu) {
       double g = 2.0 * acc[c_pidx[mu][nu]];
       for (int la = 0; la < no; ++la)
         for (int si = 0; si < no; ++si) {
-          double p = pa[c_pidx[la][si]];
+          const double p = pa[c_pidx[la][si]];
           g += p * (2.0 * onec(e, mu, nu, la, si) - onec(e, mu, la, nu, si));
         }
-      size_t ix = (size_t)(o + mu) * m.n + o + nu;
+      const size_t ix = (size_t)(o + mu) * m.n + o + nu;
       out[ix] = (h ? h[ix] : 0.0) + g;
     }
 }
 
-__global__ void fock_offdiag_kernel(MolDev m, PairDev pd, ElemTable tab, const double* __restrict__ P,
-                                    const double* __restrict__ h, double* __restrict__ out, const int* gate) {
-  if (gate && *gate == 0) return;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+// dU/dd for one pair (d = R_B - R_A), d = x, y, z: every term of eq. 37 is a
+// stored derivative block contracted with density factors that do not depend
+// on the direction, so the factor z[P][Q] of each integral derivative
+// dW[P][Q] (Coulomb, exchange and electron-core parts together) is formed
+// once and used for all three directions.
+__global__ void __launch_bounds__(128) force_pair_kernel(MolDev m, PairDev pd, ElemTable tab,
+                                                        const double* __restrict__ D, const double* __restrict__ P,
+                                                        const double* __restrict__ Dd, const double* __restrict__ Pd,
+                                                        double* __restrict__ g) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= m.npair) return;
-  int A = m.pA[t], B = m.pB[t];
-  int na = tab.e[m.elem[A]].norb, nb = tab.e[m.elem[B]].norb;
-  int oa = m.off[A], ob = m.off[B];
-  size_t np = (size_t)m.npair;
-  double pab[4][4];
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b)
-      pab[a][b] = (a < na && b < nb) ? P[(size_t)(oa + a) * m.n + ob + b] : 0.0;
-  for (int mu = 0; mu < na; ++mu)
-    for (int la = 0; la < nb; ++la) {
-      double g = 0.0;
-      for (int nu = 0; nu < na; ++nu)
-        for (int si = 0; si < nb; ++si)
-          g -= pab[nu][si] * pd.W[(size_t)(c_pidx[mu][nu] * 10 + c_pidx[la][si]) * np + t];
-      size_t ix = (size_t)(oa + mu) * m.n + ob + la;
-      out[ix] = (h ? h[ix] : 0.0) + g;
-    }
-}
-
-// copy the strict upper triangle onto the lower one (32 x 32 tiles)
-__global__ void mirror_upper_kernel(int n, double* __restrict__ a, const int* gate) {
-  if (gate && *gate == 0) return;
-  __shared__ double tile[32][33];
-  int bi = blockIdx.y, bj = blockIdx.x;
-  if (bi > bj) return;
-  int i0 = bi * 32, j0 = bj * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    int i = i0 + r, j = j0 + threadIdx.x;
-    tile[r][threadIdx.x] = (i < n && j < n) ? a[(size_t)i * n + j] : 0.0;
-  }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    int j = j0 + r, i = i0 + threadIdx.x;  // write a[j][i] = a[i][j] for i < j
-    if (i < n && j < n && i < j) a[(size_t)j * n + i] = tile[threadIdx.x][r];
-  }
-}
-
-__global__ void force_pair_kernel(MolDev m, PairDev pd, ElemTable tab, const double* __restrict__ D,
-                                  const double* __restrict__ P, const double* __restrict__ Dd,
-                                  const double* __restrict__ Pd, double* __restrict__ g) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= m.npair) return;
-  int A = m.pA[t], B = m.pB[t];
+  const int A = m.pA[t], B = m.pB[t];
   const Elem& ea = tab.e[m.elem[A]];
   const Elem& eb = tab.e[m.elem[B]];
-  int na = ea.norb, nb = eb.norb;
-  int oa = m.off[A], ob = m.off[B];
-  size_t np = (size_t)m.npair;
-  double dab[4][4], pab[4][4];
+  const int na = ea.norb, nb = eb.norb;
+  const int oa = m.off[A], ob = m.off[B];
+  const size_t np = (size_t)m.npair;
+  const size_t n = (size_t)m.n;
+  double xab[4][4], pab[4][4];                 // xab = 2 D - P on the block
+#pragma unroll
   for (int a = 0; a < 4; ++a)
+#pragma unroll
     for (int b = 0; b < 4; ++b) {
-      bool ok = (a < na && b < nb);
-      dab[a][b] = ok ? D[(size_t)(oa + a) * m.n + ob + b] : 0.0;
-      pab[a][b] = ok ? P[(size_t)(oa + a) * m.n + ob + b] : 0.0;
+      const bool ok = (a < na && b < nb);
+      const double dv = ok ? D[(oa + a) * n + ob + b] : 0.0;
+      pab[a][b] = ok ? P[(oa + a) * n + ob + b] : 0.0;
+      xab[a][b] = 2.0 * dv - pab[a][b];
     }
+  // packed diagonal-block factors with the product multiplicities m_k
+  double xa[10], pa[10], xb[10], pb[10];
   const double* DA = Dd + (size_t)A * 10;
   const double* DB = Dd + (size_t)B * 10;
-  const double* PA = Pd + (size_t)A * 10;
-  const double* PB = Pd + (size_t)B * 10;
-  int qa = (na == 4) ? 10 : 1, qb = (nb == 4) ? 10 : 1;
-  for (int k = 0; k < 3; ++k) {
-    const double* dW = pd.dW + (size_t)k * 100 * np;
-    const double* dS = pd.dS + (size_t)k * 16 * np;
-    double s = pd.dE[(size_t)k * np + t];
-    // electron-core attraction on both diagonal blocks
-    double ec = 0.0;
-    for (int p = 0; p < qa; ++p) ec -= eb.zcore * c_mult[p] * DA[p] * dW[(size_t)(p * 10) * np + t];
-    for (int q = 0; q < qb; ++q) ec -= ea.zcore * c_mult[q] * DB[q] * dW[(size_t)q * np + t];
-    s += 2.0 * ec;
-    // resonance (off-diagonal blocks appear twice in the trace)
-    double rs = 0.0;
-    for (int mu = 0; mu < na; ++mu)
-      for (int la = 0; la < nb; ++la)
-        rs += 0.5 * (ea.beta[mu ? 1 : 0] + eb.beta[la ? 1 : 0]) * dS[(size_t)(mu * 4 + la) * np + t] *
-              dab[mu][la];
-    s += 4.0 * rs;
-    // two-centre Coulomb: Tr[(2D - P) G_R]
-    double cb = 0.0;
-    for (int p = 0; p < qa; ++p) {
-      double aA = c_mult[p] * (2.0 * DA[p] - PA[p]);
-      double pA = c_mult[p] * PA[p];
-      for (int q = 0; q < qb; ++q) {
-        double w = dW[(size_t)(p * 10 + q) * np + t];
-        cb += w * (aA * c_mult[q] * PB[q] + pA * c_mult[q] * (2.0 * DB[q] - PB[q]));
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    const double mk = pair_mult(k);
+    const double PA = Pd[(size_t)A * 10 + k], PB = Pd[(size_t)B * 10 + k];
+    xa[k] = mk * (2.0 * DA[k] - PA);
+    pa[k] = mk * PA;
+    xb[k] = mk * (2.0 * DB[k] - PB);
+    pb[k] = mk * PB;
+  }
+  double s0 = pd.dE[t], s1 = pd.dE[np + t], s2 = pd.dE[2 * np + t];
+  const int qa = (na == 4) ? 10 : 1, qb = (nb == 4) ? 10 : 1;
+#pragma unroll
+  for (int pp = 0; pp < 10; ++pp) {
+#pragma unroll
+    for (int qq = 0; qq < 10; ++qq) {
+      if (pp < qa && qq < qb) {
+        // two-centre Coulomb, 2 Tr[(2D - P) G_R] part
+        double z = 2.0 * (xa[pp] * pb[qq] + pa[pp] * xb[qq]);
+        // two-centre exchange
+        double ex = 0.0;
+#pragma unroll
+        for (int i = 0; i < pair_cnt(pp); ++i)
+#pragma unroll
+          for (int j = 0; j < pair_cnt(qq); ++j)
+            ex += xab[pair_mu(pp, i)][pair_mu(qq, j)] * pab[pair_nu(pp, i)][pair_nu(qq, j)];
+        z -= 2.0 * ex;
+        // electron-core attraction on both diagonal blocks (2 Tr[h D])
+        if (qq == 0) z -= 2.0 * eb.zcore * pair_mult(pp) * DA[pp];
+        if (pp == 0) z -= 2.0 * ea.zcore * pair_mult(qq) * DB[qq];
+        const size_t ix = (size_t)(pp * 10 + qq) * np + t;
+        s0 += z * pd.dW[ix];
+        s1 += z * pd.dW[100 * np + ix];
+        s2 += z * pd.dW[200 * np + ix];
       }
     }
-    s += 2.0 * cb;
-    // two-centre exchange
-    double ex = 0.0;
-    for (int mu = 0; mu < na; ++mu)
-      for (int nu = 0; nu < na; ++nu)
-        for (int la = 0; la < nb; ++la)
-          for (int si = 0; si < nb; ++si) {
-            double w = dW[(size_t)(c_pidx[mu][nu] * 10 + c_pidx[la][si]) * np + t];
-            ex += w * (2.0 * dab[mu][la] - pab[mu][la]) * pab[nu][si];
-          }
-    s -= 2.0 * ex;
-    g[(size_t)k * np + t] = s;
   }
+  // resonance: off-diagonal blocks appear twice in 2 Tr[h D]
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+    for (int la = 0; la < 4; ++la) {
+      if (mu < na && la < nb) {
+        const double r = 2.0 * (ea.beta[mu ? 1 : 0] + eb.beta[la ? 1 : 0]) * D[(oa + mu) * n + ob + la];
+        const size_t ix = (size_t)(mu * 4 + la) * np + t;
+        s0 += r * pd.dS[ix];
+        s1 += r * pd.dS[16 * np + ix];
+        s2 += r * pd.dS[32 * np + ix];
+      }
+    }
+  g[t] = s0;
+  g[np + t] = s1;
+  g[2 * np + t] = s2;
 }
 
 // forces_I = sum_{B > I} g(I, B) - sum_{A < I} g(A, I); one warp per atom
@@ -295,12 +381,6 @@ void launch_pack_diag(cudaStream_t s, const MolDev& m, const double* M, double* 
   count_launch();
 }
 
-static void mirror(cudaStream_t s, int n, double* a, const int* gate) {
-  int t = (n + 31) / 32;
-  mirror_upper_kernel<<<dim3(t, t), dim3(32, 8), 0, s>>>(n, a, gate);
-  count_launch();
-}
-
 void launch_build_h(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,
                     double* h) {
   h_diag_kernel<<<m.N, kDiagThreads, 0, s>>>(m, pd, tab, h);
@@ -313,13 +393,12 @@ void launch_build_h(cudaStream_t s, const MolDev& m, const PairDev& pd, const El
 
 void launch_build_fock(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,
                        const double* P, const double* Pd, const double* h, double* out, const int* gate) {
-  fock_diag_kernel<<<m.N, kDiagThreads, 0, s>>>(m, pd, tab, P, Pd, h, out, gate);
-  count_launch();
   if (m.npair > 0) {
-    fock_offdiag_kernel<<<blocks_for(m.npair, 128), 128, 0, s>>>(m, pd, tab, P, h, out, gate);
+    fock_pair_kernel<<<blocks_for(m.npair, 128), 128, 0, s>>>(m, pd, tab, P, Pd, h, out, gate);
     count_launch();
   }
-  mirror(s, m.n, out, gate);
+  fock_atom_kernel<<<blocks_for((long long)m.N * 32, 256), 256, 0, s>>>(m, pd, tab, Pd, h, out, gate);
+  count_launch();
 }
 
 void launch_forces(cudaStream_t s, const MolDev& m, const PairDev& pd, const ElemTable& tab,

@@ -23,6 +23,7 @@ struct MolDev {          // read-only molecule description on the device
 };
 struct PairDev {         // pair blocks (SoA, stride npair)
   const double *W, *S, *E, *dW, *dS, *dE;
+  double* cw;            // Fock scratch: Coulomb contribution of partner Y to atom X, [X][Y][10]
 };
 
 // out[N][10]: diagonal 4x4 block of M per atom, packed by orbital product

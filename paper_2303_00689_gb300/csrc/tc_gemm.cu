@@ -572,23 +572,42 @@ __global__ void row_exponent_kernel(int n, const double* __restrict__ X, int tra
 // Balanced base-256 digits of X = round(x 2^(7 + 8(S-1) - e)): slice a is digit
 // a (most significant first) times 2^(e - 7 - 8a).  Digits lie in [-128, 128],
 // so each slice value is exact in BF16.  X is formed from the bit pattern of x
-// (x = +-M 2^(E - 1075), so X = M 2^sh rounded, sh = E - 1075 + 7 + 8(S-1) - e,
-// ties away from zero) and the digits and their BF16 values by integer and FP32
-// operations: the element needs no FP64 instruction.  |x| < 2^e (e is the
-// exponent of the row maximum), so sh < 0.
+// (x = +-M 2^(E - 1075), so |X| = M 2^-s0 rounded half up, s0 = 1075 - E - top
+// + e) by 32-bit integer operations: when the row maximum is a normal number
+// (e >= -1021) and top = 7 + 8(S-1) <= 31, s0 >= 22, so only the top 32 bits
+// q = M >> 21 of the significand can reach X or its rounding bit, and
+// |X| = (q >> s) + bit (s - 1) of q with s = s0 - 21 >= 1 (the same rounding
+// as (M + 2^(s0-1)) >> s0: the dropped 21 bits cannot carry past a multiple of
+// 2^s0).  Rows with a subnormal maximum and non-finite x take the 64-bit form.
+// The element needs no FP64 instruction.
 __device__ __forceinline__ void slice_digits(double x, int e, int slices, __nv_bfloat16* v) {
   const int top = 7 + 8 * (slices - 1);
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int E = (int)((b >> 52) & 0x7FF);
-  unsigned long long M = b & 0xFFFFFFFFFFFFFULL;
-  if (E != 0) M |= 1ULL << 52;
-  const int sh = (E != 0 ? E : 1) - 1075 + top - e;
-  long long X = 0;
-  if (sh >= 0)
-    X = (long long)(M << (sh < 11 ? sh : 11));           // not reached for |x| < 2^e
-  else if (sh > -64)
-    X = (long long)((M + (1ULL << (-sh - 1))) >> (-sh));
-  if (b >> 63) X = -X;
+  const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+  const int E = (int)((bh >> 20) & 0x7FF);
+  const unsigned q = (((bh & 0xFFFFFu) | (E != 0 ? 0x100000u : 0u)) << 11) | (bl >> 21);
+  const int s0 = 1075 - (E != 0 ? E : 1) - top + e;
+  long long X;
+  if (s0 >= 22) {
+    const int s = s0 - 21;
+    unsigned mag = 0;
+    if (s < 32)
+      mag = (q >> s) + ((q >> (s - 1)) & 1u);
+    else if (s == 32)
+      mag = q >> 31;
+    X = (long long)mag;
+  } else {
+    // a row whose maximum is subnormal (e <= -1022), or a non-finite x: 64-bit path
+    unsigned long long M = b & 0xFFFFFFFFFFFFFULL;
+    if (E != 0) M |= 1ULL << 52;
+    const int sh = -s0;
+    X = 0;
+    if (sh >= 0)
+      X = (long long)(M << (sh < 11 ? sh : 11));
+    else if (sh > -64)
+      X = (long long)((M + (1ULL << (-sh - 1))) >> (-sh));
+  }
+  if (bh >> 31) X = -X;
   int dig[kTcMaxSlices];
   for (int a = slices - 1; a > 0; --a) {
     int r = (int)(X & 0xFF);
@@ -701,21 +720,23 @@ __device__ __forceinline__ void split_row_warp(const RowSplit& q, int r, int sli
     slice_value((k < q.cols) ? x[k] : 0.0, e, slices, q.base, q.stride, (size_t)r * q.ld + k);
 }
 
-// One pass per row of a square n x n operand (a warp per row): the row
-// maximum, then the slices of four consecutive columns per lane, stored as
-// 8-byte groups per slice (ld is a multiple of 64, so every group is aligned);
-// columns n..ld-1 are zeros.  The second sweep of the row re-reads it from
-// L1/L2, so X leaves HBM once.
-__global__ void split_rows_sq_kernel(int n, const double* __restrict__ X, int ld, int slices,
-                                     int* __restrict__ ex, __nv_bfloat16* __restrict__ base, size_t stride,
-                                     const int* gate) {
+// One pass per row of a square n x n operand, one block of kSqThreads per row:
+// the row maximum (block reduction), then the slices of four consecutive
+// columns per thread, stored as 8-byte groups per slice (ld is a multiple of
+// 64, so every group is aligned); columns n..ld-1 are zeros.  The second sweep
+// re-reads the row from L1/L2, so X leaves HBM once.
+constexpr int kSqThreads = 128;
+__global__ void __launch_bounds__(kSqThreads) split_rows_sq_kernel(int n, const double* __restrict__ X, int ld,
+                                                                 int slices, int* __restrict__ ex,
+                                                                 __nv_bfloat16* __restrict__ base, size_t stride,
+                                                                 const int* gate) {
   if (gate && *gate == 0) return;
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (r >= n) return;
+  __shared__ unsigned long long s_max[kSqThreads / 32];
+  const int r = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const double* x = X + (size_t)r * n;
   unsigned long long m = 0;
-  for (int k = lane; k < n; k += 32) {
+  for (int k = tid; k < n; k += kSqThreads) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x[k]) & 0x7FFFFFFFFFFFFFFFULL;
     m = (b > m) ? b : m;
   }
@@ -723,9 +744,13 @@ __global__ void split_rows_sq_kernel(int n, const double* __restrict__ X, int ld
     const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
     m = (t > m) ? t : m;
   }
+  if (lane == 0) s_max[wid] = m;
+  __syncthreads();
+#pragma unroll
+  for (int w = 0; w < kSqThreads / 32; ++w) m = (s_max[w] > m) ? s_max[w] : m;
   const int e = exponent_of_max(m);
-  if (lane == 0) ex[r] = e;
-  for (int k0 = 4 * lane; k0 < ld; k0 += 128) {
+  if (tid == 0) ex[r] = e;
+  for (int k0 = 4 * tid; k0 < ld; k0 += 4 * kSqThreads) {
     __nv_bfloat16 v[4][kTcMaxSlices];
 #pragma unroll
     for (int c = 0; c < 4; ++c) slice_digits((k0 + c < n) ? x[k0 + c] : 0.0, e, slices, v[c]);
@@ -925,8 +950,8 @@ void tc_split(cudaStream_t s, const TcWork& w, int slot, const double* X, int sl
   int n = tb->n;
   int* ex = tb->ex + (size_t)slot * n;
   if (!transpose) {
-    split_rows_sq_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, X, tb->ld, slices, ex, tb->piece[slot][0],
-                                                              (size_t)(tb->piece[0][1] - tb->piece[0][0]), gate);
+    split_rows_sq_kernel<<<n, kSqThreads, 0, s>>>(n, X, tb->ld, slices, ex, tb->piece[slot][0],
+                                                  (size_t)(tb->piece[0][1] - tb->piece[0][0]), gate);
     count_launch();
     return;
   }
