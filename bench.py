@@ -18,6 +18,7 @@ replicas: a single system has no natural partition, so there is no data-path
 collective) and rank 0 prints the job total.  ``--impl reference`` times the
 CPU oracle (tests' FP64 numpy implementation) on one bounded sample step.
 """
+import ctypes
 import argparse
 import json
 import os
@@ -272,7 +273,7 @@ def run_ours(args):
                        "per_step": [round(x, 3) for x in per_step]},
         "e2e": {"value": world * N / e2e_s, "unit": "atom-steps/s",
                 "h2d_bytes_per_step": 2 * N * 3 * 8,
-                "d2h_bytes_per_step": 3 * N * 3 * 8 + 64},
+                "d2h_bytes_per_step": 3 * N * 3 * 8 + ctypes.sizeof(kx.sim_step_result)},
         "gpu_launches": int(launches),
         "roofline": roof,
         "measured_peaks": peaks,

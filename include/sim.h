@@ -152,6 +152,11 @@ typedef struct sim_step_result {
   double fit_err;   /* relative Krylov fit error of the last rank used         */
   int rank;         /* Krylov rank used                                        */
   int pad;
+  double dipole[3]; /* dipole moment of the cores and D0 (the observable of the
+                       paper's IR spectrum, Results), e Angstrom:
+                       sum_A (Z'_A - 2 N_A) R_A - 4 sum_A D1_A D_{s,p_k}(A),
+                       N_A = trace of atom A's block of the per-spin D0; the
+                       on-site position operator of the NDDO basis       */
 } sim_step_result;
 
 typedef struct sim_handle sim_handle;

@@ -14,6 +14,18 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   dU/dR_I = 2 Tr[h_R D] + Tr[(2D - P) G_R(P)] + dV_nn/dR_I at fixed P,
   F_I = -dU/dR_I (eq. 9 sign; eq. 24 is printed without it).
 
+* dipole moment (Results: the methanol IR spectrum comes from the dipole's
+  autocorrelation; the paper does not print its formula).  Reading: the
+  NDDO dipole of the point nuclear cores and the valence density with the
+  on-site position operator of the zero-differential-overlap basis,
+  <mu_A| r |nu_A> = R_A delta_mu,nu plus D1_A for s_A and p_k,A (D1 = <s|z|p_z>),
+  so mu = sum_A Z'_A R_A - sum_mu,nu P_mu,nu <mu| r |nu> with P = 2D:
+  mu = sum_A (Z'_A - 2 sum_{mu in A} D_mu,mu) R_A - 4 sum_A D1_A (D_s,px, D_s,py, D_s,pz)_A
+  in e Angstrom.  Pins: Hellmann-Feynman, mu = -dOmega/dE_field of the SCF
+  free energy with the field term added to h, by central differences; a
+  neutral molecule's dipole does not depend on the origin, an ion's moves by
+  its charge times the shift (tests/test_oracle_dipole.py).
+
 Everything is held in a padded layout with four orbital slots per atom
 (hydrogen uses only slot 0); ``orb`` maps the compact n orbitals to slots.
 Pins: tests/test_oracle_hamiltonian.py (textbook NDDO Fock form, G = 0,
@@ -236,3 +248,27 @@ def forces(sysm, R, D, P, pairs=None):
 def electronic_energy_terms(h, G, D, P):
     """2 Tr[h D] + Tr[(2D - P) G(P)] (eq. 13 without entropy and V_nn)."""
     return 2.0 * np.sum(h * D) + np.sum((2.0 * D - P) * G)
+
+
+def dipole_operator(sysm, R):
+    """On-site position operator of the NDDO basis, (3, n, n), Angstrom:
+    R_A,k on every orbital of atom A and D1_A between s_A and p_k,A."""
+    N = sysm.N
+    R = np.asarray(R, dtype=np.float64)
+    M = np.zeros((3, N, 4, N, 4))
+    for A in range(N):
+        for k in range(3):
+            M[k, A, :, A, :] = np.diag(R[A, k] * sysm.mask[A])
+            if sysm.norb_atom[A] == 4:
+                M[k, A, 0, A, 1 + k] = sysm.elem["D1"][A]
+                M[k, A, 1 + k, A, 0] = sysm.elem["D1"][A]
+    return np.stack([sysm.unpad(M[k]) for k in range(3)])
+
+
+def dipole(sysm, R, D):
+    """Dipole moment (e Angstrom) of the cores and the per-spin density D."""
+    M = dipole_operator(sysm, R)
+    R = np.asarray(R, dtype=np.float64)
+    nuc = (sysm.elem["zcore"][:, None] * R).sum(axis=0)
+    return nuc - 2.0 * np.einsum("kij,ij->k", M, D)
+

@@ -57,7 +57,13 @@ class sim_param_table(C.Structure):
 class sim_step_result(C.Structure):
     _fields_ = [("E_kin", C.c_double), ("U", C.c_double), ("E_tot", C.c_double), ("mu", C.c_double),
                 ("gap", C.c_double), ("res_norm", C.c_double), ("fit_err", C.c_double),
-                ("rank", C.c_int), ("pad", C.c_int)]
+                ("rank", C.c_int), ("pad", C.c_int), ("dipole", C.c_double * 3)]
+
+
+def _record_dict(r):
+    d = {f: getattr(r, f) for f, _ in sim_step_result._fields_}
+    d["dipole"] = tuple(r.dipole)
+    return d
 
 
 class sim_server_config(C.Structure):
@@ -230,7 +236,7 @@ def sim_step(h, nsteps, records=True):
     _check(lib().sim_step(h, int(nsteps), out))
     if not records:
         return None
-    return [{f: getattr(r, f) for f, _ in sim_step_result._fields_} for r in out[:nsteps]]
+    return [_record_dict(r) for r in out[:nsteps]]
 
 
 def sim_step_async(h, nsteps):
@@ -246,7 +252,7 @@ def sim_step_host(h, R_in, V_in, R_out, V_out, F_out, record=None):
 def sim_last_result(h):
     r = sim_step_result()
     _check(lib().sim_last_result(h, C.byref(r)))
-    return {f: getattr(r, f) for f, _ in sim_step_result._fields_}
+    return _record_dict(r)
 
 
 def sim_get_state(h, natoms):
@@ -337,7 +343,7 @@ def sim_tc_gemm_noalloc(n, A_dev, B_dev, terms, sym, C_dev, stream=None):
 def sim_records(h, count):
     out = (sim_step_result * max(1, count))()
     _check(lib().sim_records(h, out, int(count)))
-    return [{f: getattr(r, f) for f, _ in sim_step_result._fields_} for r in out[:count]]
+    return [_record_dict(r) for r in out[:count]]
 
 
 def sim_save(h, path):
@@ -419,7 +425,7 @@ class Server:
         outs = self._keep.pop(ticket)
         recs = None
         if outs["rec"] is not None:
-            recs = [{f: getattr(r, f) for f, _ in sim_step_result._fields_} for r in outs["rec"][:res.steps_done]]
+            recs = [_record_dict(r) for r in outs["rec"][:res.steps_done]]
         return dict(status=res.status, steps_done=res.steps_done, queue_ms=res.queue_ms,
                     create_ms=res.create_ms, run_ms=res.run_ms, error=res.error.decode(),
                     R=outs["R"], V=outs["V"], F=outs["F"], records=recs)

@@ -287,8 +287,9 @@ static int eig(sim_handle* h) {
   eig_vectors(h->stream, h->n, h->eps, h->Q, h->ew, mixed(h));
   phase_end(h);
   phase_begin(h, PH_BACKTR);
-  eig_backtransform(h->stream, h->n, h->Q, h->ew, mixed(h) ? &h->tw : nullptr);
+  const int bt = eig_backtransform(h->stream, h->n, h->Q, h->ew, mixed(h) ? &h->tw : nullptr);
   phase_end(h);
+  if (bt != 0) return fail(SIM_EINTERNAL, "back-transformation: tensor map encoding failed");
   return SIM_OK;
 }
 
@@ -341,7 +342,7 @@ static int evaluate(sim_handle* h, bool krylov = true, bool pairs_ready = false)
   if (!pairs_ready) {
     phase_begin(h, PH_PAIRS);
     launch_pair_derivs(s, h->npair, h->pA, h->pB, h->elem, h->R, h->tab, h->W, h->S, h->E, h->dW, h->dS,
-                       h->dE);
+                       h->dE, mixed(h));
     phase_end(h);
   }
   phase_begin(h, PH_FOCK);
@@ -359,6 +360,7 @@ static int evaluate(sim_handle* h, bool krylov = true, bool pairs_ready = false)
   launch_energy(s, n, h->npair, h->h, h->D, X, h->Fock, h->E, h->sc, h->red);
   launch_pack_diag(s, m, h->D, h->Dd);
   launch_forces(s, m, pd, h->tab, h->D, X, h->Dd, h->Pd, h->g, h->F);
+  launch_dipole(s, m, h->tab, h->R, h->Dd, h->sc);
   phase_end(h);
   if (!krylov) return SIM_OK;
   if (h->cfg.kernel == SIM_KERNEL_XL) {
@@ -389,6 +391,7 @@ __global__ void record_kernel(const Scalars* sc, double Te, sim_step_result* bas
   r.fit_err = sc->fit;
   r.rank = sc->rank;
   r.pad = sc->status;
+  for (int k = 0; k < 3; ++k) r.dipole[k] = sc->dipole[k];
   *out = r;
 }
 
@@ -428,7 +431,8 @@ static int bomd_step(sim_handle* h) {
   launch_drift(s, h->N, h->R, h->V, dt);                  // eq. 28
   phase_end(h);
   phase_begin(h, PH_PAIRS);
-  launch_pair_derivs(s, h->npair, h->pA, h->pB, h->elem, h->R, h->tab, h->W, h->S, h->E, h->dW, h->dS, h->dE);
+  launch_pair_derivs(s, h->npair, h->pA, h->pB, h->elem, h->R, h->tab, h->W, h->S, h->E, h->dW, h->dS, h->dE,
+                     mixed(h));
   launch_build_h(s, mol(h), pairs(h), h->tab, h->h);
   phase_end(h);
   int it = 0;
@@ -852,7 +856,8 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
     cudaMemcpyAsync(h->mass, h->mass_h.data(), natoms * sizeof(double), cudaMemcpyHostToDevice, s);
     launch_fill(s, (size_t)h->n * h->n, h->K, 0.0);
     // pair blocks and h at R0
-    launch_pair_derivs(s, h->npair, h->pA, h->pB, h->elem, h->R, h->tab, h->W, h->S, h->E, h->dW, h->dS, h->dE);
+    launch_pair_derivs(s, h->npair, h->pA, h->pB, h->elem, h->R, h->tab, h->W, h->S, h->E, h->dW, h->dS, h->dE,
+                     mixed(h));
     launch_build_h(s, mol(h), pairs(h), h->tab, h->h);
     size_t nn = (size_t)h->n * h->n;
     if (P0) {

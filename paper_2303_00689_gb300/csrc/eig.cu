@@ -909,11 +909,18 @@ __global__ void invit_kernel(int n, const double* __restrict__ d, const double* 
 // separation use the double-float unit 2^-46 |T| instead of the FP64 epsilon.
 __device__ __forceinline__ float df_abs_hi(dfl a) { return fabsf(a.hi); }
 
-__global__ void invit_df_kernel(int n, const dfl* __restrict__ d, const double* __restrict__ e,
-                                const double* __restrict__ ev, const double* __restrict__ scal,
-                                const int* __restrict__ clus, dfl* __restrict__ lu,
-                                double* __restrict__ Zout) {
-  int L = blockIdx.x * blockDim.x + threadIdx.x;
+// Each cluster leader runs its recurrences alone, so the kernel is bound by
+// their latency: kIvLanes active lanes per 32-thread block spread the n
+// chains over n / kIvLanes warps (about 5 per SM at n = 3360 instead of
+// one), so each SM interleaves several independent chains; four lanes keep
+// every access a whole 32-byte sector and limit divergence at the pivots.
+constexpr int kIvLanes = 4;
+__global__ void __launch_bounds__(32) invit_df_kernel(int n, const dfl* __restrict__ d, const double* __restrict__ e,
+                                                    const double* __restrict__ ev, const double* __restrict__ scal,
+                                                    const int* __restrict__ clus, dfl* __restrict__ lu,
+                                                    double* __restrict__ Zout) {
+  if (threadIdx.x >= kIvLanes) return;
+  int L = blockIdx.x * kIvLanes + threadIdx.x;
   if (L >= n || !clus[L]) return;
   int end = L + 1;
   while (end < n && !clus[end]) ++end;
@@ -1116,33 +1123,46 @@ static size_t lu_doubles(int n) {
   return a > b ? a : b;
 }
 
-size_t eig_work_bytes(int n) {
-  size_t nn = (size_t)n * n;
-  size_t doubles = nn /*A*/ + nn /*Vst*/ + 4 * (size_t)n /*d e e2 tau*/ + 3 * (size_t)n /*pbuf*/ +
-                   lu_doubles(n) + 2 * (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc + 2 * (size_t)kBtBlockTc * n +
-                   16;
-  return doubles * sizeof(double) + 64 + (size_t)n * sizeof(int) + 256;
+// One layout for sizing and binding.  Every buffer starts on a 256-byte
+// boundary: the back-transformation cuts BF16 slices into the lu region and
+// hands them to TMA, whose tensor maps need 16-byte aligned bases (with odd n
+// an unpadded layout would leave the region 8 bytes off).
+static size_t eig_layout(int n, void* base, EigWork* w) {
+  const size_t nn = (size_t)n * n;
+  size_t off = 0;
+  auto take = [&](size_t doubles) {
+    double* q = base ? (double*)base + off : nullptr;
+    off += (doubles + 31) & ~(size_t)31;
+    return q;
+  };
+  double* A = take(nn);
+  double* Vst = take(nn);
+  double* d = take(n);
+  double* e = take(n);
+  double* e2 = take(n);
+  double* tau = take(n);
+  double* pbuf = take(3 * (size_t)n);
+  double* lu = take(lu_doubles(n));
+  double* Tm = take((size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc);   // T and Gram of every reflector block
+  double* Gm = take((size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc);
+  double* Wt = take((size_t)kBtBlockTc * n);
+  double* Wt2 = take((size_t)kBtBlockTc * n);
+  double* scal = take(16);
+  double* bar = take(8);
+  double* clus = take(((size_t)n * sizeof(int) + 7) / 8);
+  if (w) {
+    w->A = A; w->Vst = Vst; w->d = d; w->e = e; w->e2 = e2; w->tau = tau; w->pbuf = pbuf; w->lu = lu;
+    w->Tm = Tm; w->Gm = Gm; w->Wt = Wt; w->Wt2 = Wt2; w->scal = scal;
+    w->bar = (unsigned*)bar;
+    w->clus = (int*)clus;
+  }
+  return off * sizeof(double) + 256;
 }
 
-void eig_work_bind(EigWork& w, void* base, int n) {
-  size_t nn = (size_t)n * n;
-  double* p = (double*)base;
-  w.A = p; p += nn;
-  w.Vst = p; p += nn;
-  w.d = p; p += n;
-  w.e = p; p += n;
-  w.e2 = p; p += n;
-  w.tau = p; p += n;
-  w.pbuf = p; p += 3 * (size_t)n;
-  w.lu = p; p += lu_doubles(n);
-  w.Tm = p; p += (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc;   // T and Gram of every reflector block
-  w.Gm = p; p += (size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc;
-  w.Wt = p; p += (size_t)kBtBlockTc * n;
-  w.Wt2 = p; p += (size_t)kBtBlockTc * n;
-  w.scal = p; p += 16;
-  w.bar = (unsigned*)p; p += 8;
-  w.clus = (int*)p;
-}
+size_t eig_work_bytes(int n) { return eig_layout(n, nullptr, nullptr); }
+
+// base must be 256-byte aligned (arena allocations are)
+void eig_work_bind(EigWork& w, void* base, int n) { eig_layout(n, base, &w); }
 
 // About 64K (FP64 kernel) or 32K (double-float kernel, whose columns cost
 // less arithmetic and more latency) elements of the initial matrix per block,
@@ -1264,7 +1284,7 @@ void eig_vectors(cudaStream_t s, int n, const double* eps, double* Q, EigWork& w
   count_launch();
   if (df_path) {
     const dfl* d_dfl = (const dfl*)(w.pbuf + n);     // written by eig_bisect
-    invit_df_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, d_dfl, w.e, eps, w.scal, w.clus, (dfl*)w.lu, Q);
+    invit_df_kernel<<<(n + kIvLanes - 1) / kIvLanes, 32, 0, s>>>(n, d_dfl, w.e, eps, w.scal, w.clus, (dfl*)w.lu, Q);
   } else {
     invit_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e, eps, w.scal, w.clus, w.lu, Q);
   }
@@ -1410,7 +1430,7 @@ static size_t bt_scratch_layout(int n, void* base, BtScratch* out) {
   return off;
 }
 
-static void eig_backtransform_tc(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork& tw) {
+static int eig_backtransform_tc(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork& tw) {
   static PerDeviceOnce attr;
   once_per_device(attr, [] {
     return cudaFuncSetAttribute(tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1448,19 +1468,19 @@ static void eig_backtransform_tc(cudaStream_t s, int n, double* Q, EigWork& w, c
     tc_split_rows(s, n, m, Zs, n, 4, sZ, ldm, stride);
     const int parts = tc_gemm_rc_splitk(s, n, kb, m, sZ, ldm, stride, sc.vs + (size_t)b * sc.vs_blk, ldm,
                                         sc.vs_slice, 10, 1.0, sc.part, kBtBlockTc, kBtSplitK, err);   // U parts
+    if (parts <= 0) return -1;
     const int ldk = tc_ld(kb);                           // U slices fit the slot: kb <= n
-    tc_reduce_split_rows(s, n, kb, sc.part, parts > 0 ? parts : 0, kBtBlockTc, 4, sU, ldk, stride);
-    tc_gemm_rc(s, n, m, kb, sU, ldk, stride, sc.ys + (size_t)b * sc.ys_blk, kBtBlockTc, sc.ys_slice, 10, -1.0, Zs,
-               n, 1, err);                                                                   // Zs -= U Y_b
+    tc_reduce_split_rows(s, n, kb, sc.part, parts, kBtBlockTc, 4, sU, ldk, stride);
+    if (tc_gemm_rc(s, n, m, kb, sU, ldk, stride, sc.ys + (size_t)b * sc.ys_blk, kBtBlockTc, sc.ys_slice, 10, -1.0,
+                   Zs, n, 1, err) != 0)                                                      // Zs -= U Y_b
+      return -1;
   }
   transpose_sq(s, n, Zt, Q);
+  return 0;
 }
 
-void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork* tw) {
-  if (tw && n > 2) {
-    eig_backtransform_tc(s, n, Q, w, *tw);
-    return;
-  }
+int eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork* tw) {
+  if (tw && n > 2) return eig_backtransform_tc(s, n, Q, w, *tw);
   // 4. back-transformation, last block of reflectors first
   int nref = n - 2;
   if (nref > 0) {
@@ -1477,6 +1497,7 @@ void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w, const TcWor
       dgemm(s, 1, 0, m, n, kb, -1.0, Vb, n, w.Wt2, n, 1.0, Q + (size_t)c0 * n, n);
     }
   }
+  return 0;
 }
 
 int symmetric_eig(cudaStream_t s, int n, const double* F, double* eps, double* Q, EigWork& w,

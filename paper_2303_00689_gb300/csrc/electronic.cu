@@ -325,6 +325,37 @@ __global__ void energy_final_kernel(int nparts, const double* __restrict__ parti
   if (threadIdx.x == 0) { sc->e_elec = a; sc->vnn = b; }
 }
 
+// Dipole moment (the observable of the paper's IR spectrum, Results): the
+// cores Z'_A at R_A and the valence density through the on-site position
+// operator of the zero-differential-overlap basis, <mu_A| r |nu_A> = R_A
+// delta_mu,nu and D1_A between s_A and p_k,A.  With the total density 2 D:
+// mu = sum_A (Z'_A - 2 N_A) R_A - 4 sum_A D1_A (D_s,px, D_s,py, D_s,pz)_A,
+// N_A the trace of A's diagonal block of D.  One block, fixed-order sums.
+__global__ void dipole_kernel(MolDev m, ElemTable tab, const double* __restrict__ R, const double* __restrict__ Dd,
+                              Scalars* sc) {
+  __shared__ double red[32];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int A = threadIdx.x; A < m.N; A += blockDim.x) {
+    const Elem& e = tab.e[m.elem[A]];
+    const double* d = Dd + (size_t)A * 10;
+    const double nA = d[0] + d[4] + d[5] + d[6];        // products ss, xx, yy, zz
+    const double q = e.zcore - 2.0 * nA;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[k] += q * R[3 * A + k] - 4.0 * e.D1 * d[1 + k];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double t = block_sum(acc[k], red);
+    if (threadIdx.x == 0) sc->dipole[k] = t;
+  }
+}
+
+void launch_dipole(cudaStream_t s, const MolDev& m, const ElemTable& tab, const double* R, const double* Dd,
+                   Scalars* sc) {
+  dipole_kernel<<<1, 256, 0, s>>>(m, tab, R, Dd, sc);
+  count_launch();
+}
+
 void launch_energy(cudaStream_t s, int n, int npair, const double* h, const double* D, const double* X,
                    const double* F, const double* E, Scalars* sc, double* part) {
   energy_partial_kernel<<<kRedBlocks, kRedThreads, 0, s>>>((size_t)n * n, npair, h, D, X, F, E, part);

@@ -9,9 +9,11 @@ namespace kx {
 bool upload_overlap_tables();
 void launch_pair_values(cudaStream_t s, int npair, const int* pA, const int* pB, const int* elem,
                         const double* R, const ElemTable& tab, double* W, double* S, double* E);
+// df_rotation: the molecular-frame rotation of the integral blocks in
+// double-float on the FP32 pipe (mixed path) instead of FP64
 void launch_pair_derivs(cudaStream_t s, int npair, const int* pA, const int* pB, const int* elem,
                         const double* R, const ElemTable& tab, double* W, double* S, double* E,
-                        double* dW, double* dS, double* dE);
+                        double* dW, double* dS, double* dE, bool df_rotation);
 
 // ---- fock.cu ----------------------------------------------------------------
 struct MolDev {          // read-only molecule description on the device
@@ -81,7 +83,8 @@ void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w, double rel_tol, 
 void eig_vectors(cudaStream_t s, int n, const double* eps, double* Q, EigWork& w, bool df_path);
 struct TcWork;
 // tw != nullptr: the large products run on the tensor cores (mixed path)
-void eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork* tw);
+// returns nonzero when the tensor-core path could not encode its tensor maps
+int eig_backtransform(cudaStream_t s, int n, double* Q, EigWork& w, const TcWork* tw);
 int symmetric_eig(cudaStream_t s, int n, const double* F, double* eps, double* Q, EigWork& w,
                   int* status, int sm_count);
 
@@ -94,6 +97,7 @@ struct Scalars {         // device-resident per-evaluation scalars
   unsigned long long step;   // MD steps taken (counter of the thermostat's random numbers)
   unsigned red_count;        // blocks done in the current fused reduction (reset by its last block)
   unsigned red_pad;
+  double dipole[3];          // dipole moment of the cores and D0, e Angstrom
 };
 void launch_fermi(cudaStream_t s, int n, const double* eps, double nocc, double beta, double* f,
                   Scalars* sc);
@@ -106,6 +110,11 @@ void launch_dmu(cudaStream_t s, int n, const double* F1p, const double* eps, con
 void launch_lambda(cudaStream_t s, int n, const double* eps, const double* f, double beta, const Scalars* sc,
                    double* Lam);
 void launch_dmpt_y(cudaStream_t s, int n, const double* F1p, const double* Lam, const Scalars* sc, double* Y);
+// dipole moment of the cores and the per-spin density with packed diagonal
+// blocks Dd (10 products per atom): sum_A (Z'_A - 2 N_A) R_A - 4 sum_A D1_A D_s,p
+// (the on-site position operator of the NDDO basis), written to sc->dipole
+void launch_dipole(cudaStream_t s, const MolDev& m, const ElemTable& tab, const double* R, const double* Dd,
+                   Scalars* sc);
 // U = 2 Tr[h D] + Tr[(2D - X)(F - h)] and V_nn = sum E_pair
 void launch_energy(cudaStream_t s, int n, int npair, const double* h, const double* D,
                    const double* X, const double* F, const double* E, Scalars* sc, double* partial);

@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "df.cuh"
 #include "kernels.h"
 
 namespace kx {
@@ -193,7 +194,105 @@ __device__ __forceinline__ int mirror_xy(int p) {
   }
 }
 
-template <typename T>
+// Double-float dual number with three derivative directions: the mixed
+// path's rotation of the local blocks (C I C^T, eq. 6's two-centre integrals
+// in the molecular frame) runs on the FP32 pipe in ~48-bit arithmetic instead
+// of GB300's narrow FP64 pipe.
+struct G3 {
+  dfl v, d[3];
+};
+__device__ __forceinline__ G3 g3_zero() {
+  return G3{{0.0f, 0.0f}, {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}}};
+}
+__device__ __forceinline__ G3 g3_of(const D3& a) {
+  return G3{df_from_double(a.v), {df_from_double(a.d0), df_from_double(a.d1), df_from_double(a.d2)}};
+}
+__device__ __forceinline__ D3 d3_of(const G3& a) {
+  return D3{df_to_double(a.v), df_to_double(a.d[0]), df_to_double(a.d[1]), df_to_double(a.d[2])};
+}
+__device__ __forceinline__ G3 g3_mul(const G3& a, const G3& b) {
+  G3 r;
+  r.v = df_mul(a.v, b.v);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r.d[k] = df_add(df_mul(a.d[k], b.v), df_mul(a.v, b.d[k]));
+  return r;
+}
+__device__ __forceinline__ G3 g3_add(const G3& a, const G3& b) {
+  G3 r;
+  r.v = df_add(a.v, b.v);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r.d[k] = df_add(a.d[k], b.d[k]);
+  return r;
+}
+// acc += a b, the low parts gathered without renormalisation (g3_norm after
+// the last term)
+__device__ __forceinline__ void g3_acc_mul(G3& acc, const G3& a, const G3& b) {
+  df_acc_mul(acc.v, a.v, b.v);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    df_acc_mul(acc.d[k], a.d[k], b.v);
+    df_acc_mul(acc.d[k], a.v, b.d[k]);
+  }
+}
+__device__ __forceinline__ G3 g3_norm(const G3& a) {
+  return G3{df_norm(a.v), {df_norm(a.d[0]), df_norm(a.d[1]), df_norm(a.d[2])}};
+}
+
+// W = C I C^T in double-float from the local integrals as radial duals
+// (value, d/dR): promoted by d/dd_k = u_k d/dR, rotated, written as D3
+__device__ void rotate_blocks_df(const D1 (&Ir)[10][10], const D3 (&Tf)[4][4], const double* uv, int pa, int pb,
+                                 D3* Wout) {
+  G3 Tg[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) Tg[a][b] = g3_zero();
+  Tg[0][0].v = dfl{1.0f, 0.0f};
+#pragma unroll
+  for (int a = 1; a < 4; ++a)
+#pragma unroll
+    for (int b = 1; b < 4; ++b) Tg[a][b] = g3_of(Tf[a][b]);
+  const dfl ug[3] = {df_from_double(uv[0]), df_from_double(uv[1]), df_from_double(uv[2])};
+  G3 I[10][10];
+  for (int p = 0; p < 10; ++p)
+    for (int q = 0; q < 10; ++q) {
+      I[p][q] = g3_zero();
+      if (p < pa && q < pb && c_prod_cls[p] == c_prod_cls[q]) {
+        const dfl dr = df_from_double(Ir[p][q].d);
+        I[p][q].v = df_from_double(Ir[p][q].v);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) I[p][q].d[k] = df_mul(dr, ug[k]);
+      }
+    }
+  G3 C[10][10];
+  for (int p = 0; p < 10; ++p) {
+    const int mu = c_prod_mu[p], nu = c_prod_nu[p];
+    for (int pp = c_grp_lo[p]; pp < c_grp_hi[p]; ++pp) {
+      const int m2 = c_prod_mu[pp], n2 = c_prod_nu[pp];
+      if (m2 == n2)
+        C[p][pp] = g3_mul(Tg[mu][m2], Tg[nu][m2]);
+      else
+        C[p][pp] = g3_add(g3_mul(Tg[mu][m2], Tg[nu][n2]), g3_mul(Tg[mu][n2], Tg[nu][m2]));
+    }
+  }
+  G3 X[10][10];
+  for (int pp = 0; pp < pa; ++pp)
+    for (int q = 0; q < pb; ++q) {
+      G3 acc = g3_zero();
+      for (int qq = c_grp_lo[q]; qq < c_grp_hi[q]; ++qq)
+        if (c_prod_cls[qq] == c_prod_cls[pp]) g3_acc_mul(acc, I[pp][qq], C[q][qq]);
+      X[pp][q] = g3_norm(acc);
+    }
+  for (int p = 0; p < 10; ++p)
+    for (int q = 0; q < 10; ++q) {
+      G3 acc = g3_zero();
+      if (p < pa && q < pb)
+        for (int pp = c_grp_lo[p]; pp < c_grp_hi[p]; ++pp) g3_acc_mul(acc, C[p][pp], X[pp][q]);
+      Wout[p * 10 + q] = d3_of(g3_norm(acc));
+    }
+}
+
+template <bool DFROT, typename T>
 __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T* Wout /*100*/,
                            T* Sout /*16*/, T* Eout) {
   typedef typename Radial<T>::type Tr;
@@ -233,26 +332,33 @@ __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T
   // local integrals: the distinct ones (rows ss, sz, xx, zz of the sigma/
   // delta class, sx and xz of the pi class) from the charge sets, the rest by
   // the x <-> y mirror and the rotational-invariance relation for (xy|xy)
-  T I[10][10];
+  Tr Ir[10][10];
   for (int p = 0; p < 10; ++p)
-    for (int q = 0; q < 10; ++q) I[p][q] = cst<T>(0.0);
+    for (int q = 0; q < 10; ++q) Ir[p][q] = cst<Tr>(0.0);
   for (int p = 0; p < pa; ++p) {
     if (p == 2 || p == 5 || p == 7 || p == 9) continue;        // mirrored or derived below
     for (int q = 0; q < pb; ++q) {
       if (c_prod_cls[p] != c_prod_cls[q]) continue;
       if (c_prod_cls[p] == 1 && (q == 2 || q == 9)) continue;
-      I[p][q] = Radial<T>::promote(local_integral<Tr>(p, q, ea, eb, Rr), uv);
+      Ir[p][q] = local_integral<Tr>(p, q, ea, eb, Rr);
     }
   }
   if (pa == 10) {
     for (int q = 0; q < pb; ++q) {
       const int mq = mirror_xy(q);
-      if (c_prod_cls[q] == 0) I[5][q] = I[4][mq];
-      if (c_prod_cls[q] == 2) { I[2][q] = I[1][mq]; I[9][q] = I[8][mq]; }
+      if (c_prod_cls[q] == 0) Ir[5][q] = Ir[4][mq];
+      if (c_prod_cls[q] == 2) { Ir[2][q] = Ir[1][mq]; Ir[9][q] = Ir[8][mq]; }
     }
-    if (pb == 10) I[7][7] = 0.5 * (I[4][4] - I[4][5]);
+    if (pb == 10) Ir[7][7] = 0.5 * (Ir[4][4] - Ir[4][5]);
   }
 
+  if constexpr (DFROT) {
+    rotate_blocks_df(Ir, Tf, uv, pa, pb, Wout);
+  } else {
+  T I[10][10];
+  for (int p = 0; p < 10; ++p)
+    for (int q = 0; q < 10; ++q)
+      I[p][q] = (c_prod_cls[p] == c_prod_cls[q]) ? Radial<T>::promote(Ir[p][q], uv) : cst<T>(0.0);
   // product transform C[p][p'] (block diagonal over ss / sp / pp groups)
   T C[10][10];
   for (int p = 0; p < 10; ++p) {
@@ -270,7 +376,8 @@ __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T
   for (int pp = 0; pp < pa; ++pp)
     for (int q = 0; q < pb; ++q) {
       T acc = cst<T>(0.0);
-      for (int qq = c_grp_lo[q]; qq < c_grp_hi[q]; ++qq) acc += I[pp][qq] * C[q][qq];
+      for (int qq = c_grp_lo[q]; qq < c_grp_hi[q]; ++qq)
+        if (c_prod_cls[qq] == c_prod_cls[pp]) acc += I[pp][qq] * C[q][qq];   // other classes: I = 0
       X[pp][q] = acc;
     }
   for (int p = 0; p < 10; ++p)
@@ -280,6 +387,7 @@ __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T
         for (int pp = c_grp_lo[p]; pp < c_grp_hi[p]; ++pp) acc += C[p][pp] * X[pp][q];
       Wout[p * 10 + q] = acc;
     }
+  }
 
   // overlaps in the local frame (functions of R), then rotated
   T Sl[4][4];
@@ -301,13 +409,14 @@ __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T
     Sl[1][1] = spp;
     Sl[2][2] = spp;
   }
+  // only (s, s), (s, z), (z, s), (z, z), (x, x), (y, y) are nonzero in the local frame
+  const int nzA[6] = {0, 3, 0, 3, 1, 2}, nzB[6] = {0, 0, 3, 3, 1, 2};
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 4; ++b) {
       T acc = cst<T>(0.0);
       if (a < ea.norb && b < eb.norb)
-        for (int a2 = 0; a2 < 4; ++a2)
-          for (int b2 = 0; b2 < 4; ++b2)
-            acc += Tf[a][a2] * Tf[b][b2] * Sl[a2][b2];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) acc += Tf[a][nzA[t]] * Tf[b][nzB[t]] * Sl[nzA[t]][nzB[t]];
       Sout[a * 4 + b] = acc;
     }
 
@@ -335,12 +444,13 @@ __global__ void pair_values_kernel(int npair, const int* __restrict__ pA, const 
   const Elem& ea = tab.e[elem[A]];
   const Elem& eb = tab.e[elem[B]];
   double w[100], s[16], e;
-  pair_block<double>(d, ea, eb, w, s, &e);
+  pair_block<false, double>(d, ea, eb, w, s, &e);
   for (int k = 0; k < 100; ++k) W[(size_t)k * npair + t] = w[k];
   for (int k = 0; k < 16; ++k) S[(size_t)k * npair + t] = s[k];
   E[t] = e;
 }
 
+template <bool DFROT>
 __global__ void pair_derivs_kernel(int npair, const int* __restrict__ pA, const int* __restrict__ pB,
                                    const int* __restrict__ elem, const double* __restrict__ R,
                                    ElemTable tab, double* __restrict__ W, double* __restrict__ S,
@@ -353,7 +463,7 @@ __global__ void pair_derivs_kernel(int npair, const int* __restrict__ pA, const 
   const Elem& ea = tab.e[elem[A]];
   const Elem& eb = tab.e[elem[B]];
   D3 w[100], s[16], e;
-  pair_block<D3>(d, ea, eb, w, s, &e);
+  pair_block<DFROT, D3>(d, ea, eb, w, s, &e);
   size_t np = (size_t)npair;
   for (int k = 0; k < 100; ++k) {
     W[k * np + t] = w[k].v;
@@ -452,10 +562,12 @@ void launch_pair_values(cudaStream_t s, int npair, const int* pA, const int* pB,
 
 void launch_pair_derivs(cudaStream_t s, int npair, const int* pA, const int* pB, const int* elem,
                         const double* R, const ElemTable& tab, double* W, double* S, double* E,
-                        double* dW, double* dS, double* dE) {
+                        double* dW, double* dS, double* dE, bool df_rotation) {
   if (npair <= 0) return;
-  pair_derivs_kernel<<<(npair + 127) / 128, 128, 0, s>>>(npair, pA, pB, elem, R, tab, W, S, E, dW,
-                                                         dS, dE);
+  if (df_rotation)
+    pair_derivs_kernel<true><<<(npair + 127) / 128, 128, 0, s>>>(npair, pA, pB, elem, R, tab, W, S, E, dW, dS, dE);
+  else
+    pair_derivs_kernel<false><<<(npair + 127) / 128, 128, 0, s>>>(npair, pA, pB, elem, R, tab, W, S, E, dW, dS, dE);
   count_launch();
 }
 

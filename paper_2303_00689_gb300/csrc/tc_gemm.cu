@@ -608,18 +608,28 @@ __device__ __forceinline__ void slice_digits(double x, int e, int slices, __nv_b
       X = (long long)((M + (1ULL << (-sh - 1))) >> (-sh));
   }
   if (bh >> 31) X = -X;
+  // digits from the least significant (slice slices-1) up; unrolled over the
+  // maximum slice count so that the digits stay in registers
   int dig[kTcMaxSlices];
-  for (int a = slices - 1; a > 0; --a) {
-    int r = (int)(X & 0xFF);
-    if (r >= 128) r -= 256;
-    dig[a] = r;
-    X = (X - r) >> 8;
+#pragma unroll
+  for (int a = kTcMaxSlices - 1; a > 0; --a) {
+    if (a < slices) {
+      int r = (int)(X & 0xFF);
+      if (r >= 128) r -= 256;
+      dig[a] = r;
+      X = (X - r) >> 8;
+    } else {
+      dig[a] = 0;
+    }
   }
   dig[0] = (int)X;
-  for (int a = 0; a < slices; ++a) {
-    const int k = e - 7 - 8 * a;                           // slice scale 2^k
-    const float p2 = (k >= -126 && k <= 127) ? __int_as_float((k + 127) << 23) : 0.0f;
-    v[a] = __float2bfloat16_rn((float)dig[a] * p2);
+#pragma unroll
+  for (int a = 0; a < kTcMaxSlices; ++a) {
+    if (a < slices) {
+      const int k = e - 7 - 8 * a;                         // slice scale 2^k
+      const float p2 = (k >= -126 && k <= 127) ? __int_as_float((k + 127) << 23) : 0.0f;
+      v[a] = __float2bfloat16_rn((float)dig[a] * p2);
+    }
   }
 }
 
@@ -627,7 +637,9 @@ __device__ __forceinline__ void slice_value(double x, int e, int slices, __nv_bf
                                             size_t t) {
   __nv_bfloat16 v[kTcMaxSlices];
   slice_digits(x, e, slices, v);
-  for (int a = 0; a < slices; ++a) out[a * stride + t] = v[a];
+#pragma unroll
+  for (int a = 0; a < kTcMaxSlices; ++a)
+    if (a < slices) out[a * stride + t] = v[a];
 }
 
 // FP64 -> fixed-point BF16 slices relative to the row exponent; ld-padded rows
@@ -643,7 +655,9 @@ __global__ void split_bf16_kernel(int n, const double* __restrict__ X, int ld, i
   if (j < n) x = transpose ? X[(size_t)j * n + i] : X[(size_t)i * n + j];
   __nv_bfloat16 v[kTcMaxSlices];
   slice_digits(x, ex[i], slices, v);
-  for (int a = 0; a < slices; ++a) P[a][t] = v[a];
+#pragma unroll
+  for (int a = 0; a < kTcMaxSlices; ++a)
+    if (a < slices) P[a][t] = v[a];
 }
 
 // same slicing as split_bf16_kernel, slices at base + a * stride (no pointer table)
@@ -754,14 +768,17 @@ __global__ void __launch_bounds__(kSqThreads) split_rows_sq_kernel(int n, const 
     __nv_bfloat16 v[4][kTcMaxSlices];
 #pragma unroll
     for (int c = 0; c < 4; ++c) slice_digits((k0 + c < n) ? x[k0 + c] : 0.0, e, slices, v[c]);
-    for (int a = 0; a < slices; ++a) {
-      __nv_bfloat162 lo2, hi2;
-      lo2.x = v[0][a]; lo2.y = v[1][a];
-      hi2.x = v[2][a]; hi2.y = v[3][a];
-      uint2 w;
-      w.x = *(const uint32_t*)&lo2;
-      w.y = *(const uint32_t*)&hi2;
-      *(uint2*)(base + a * stride + (size_t)r * ld + k0) = w;
+#pragma unroll
+    for (int a = 0; a < kTcMaxSlices; ++a) {
+      if (a < slices) {
+        __nv_bfloat162 lo2, hi2;
+        lo2.x = v[0][a]; lo2.y = v[1][a];
+        hi2.x = v[2][a]; hi2.y = v[3][a];
+        uint2 w;
+        w.x = *(const uint32_t*)&lo2;
+        w.y = *(const uint32_t*)&hi2;
+        *(uint2*)(base + a * stride + (size_t)r * ld + k0) = w;
+      }
     }
   }
 }

@@ -27,10 +27,25 @@ def _perturbed(D, seed, scale=1e-3):
     return D + Y + Y.T
 
 
-@pytest.mark.parametrize("kind", ["c4h6", "carbon100", "carbon200"])
+def _organic(natoms, odd):
+    """An organic molecule (C/N/O/H) with an odd or even number of orbitals."""
+    rng = np.random.default_rng(np.random.SeedSequence([91, natoms]))
+    for _ in range(200):
+        mol = synth.organic_molecule(rng, natoms)
+        n = int(sum(1 if z == 1 else 4 for z in mol.Z))
+        if n % 2 == int(odd):
+            return mol
+    raise RuntimeError("no molecule of that parity drawn")
+
+
+@pytest.mark.parametrize("kind", ["c4h6", "carbon100", "carbon200", "organic9-odd", "organic40-odd",
+                                  "organic40-even", "organic120-odd"])
 def test_mixed_evaluation_matches_oracle(kind):
     if kind == "c4h6":
         mol = synth.c4h6(1)
+    elif kind.startswith("organic"):
+        size, parity = kind[7:].split("-")
+        mol = _organic(int(size), parity == "odd")
     else:
         mol = synth.carbon_packing(seed=7, natoms=int(kind[6:]))
     sysm = oracle_system(mol)
@@ -42,10 +57,17 @@ def test_mixed_evaluation_matches_oracle(kind):
         D = kx.sim_get_matrix(h, kx.SIM_MAT_D0)
         K = kx.sim_get_matrix(h, kx.SIM_MAT_KERNEL)
         _, _, F, _ = kx.sim_get_state(h, sysm.N)
+        Q = kx.sim_get_matrix(h, kx.SIM_MAT_Q)
+        Fk = kx.sim_get_matrix(h, kx.SIM_MAT_FOCK)
+        eps = kx.sim_get_vector(h, 0)
         assert np.array_equal(D, D.T)
         assert max_abs(D, ev["D"]) < 1e-6
         assert max_abs(F, ev["forces"]) < 1e-3
         assert max_abs(K, ev["K"]) < 1e-3 * np.abs(ev["K"]).max()
+        # eigenpairs of the mixed eigensolver (odd and even n: the tensor-core
+        # back-transformation must have run, not only the tridiagonal vectors)
+        assert np.abs(Fk @ Q - Q * eps).max() < 1e-6 * np.abs(Fk).max()
+        assert np.abs(Q.T @ Q - np.eye(sysm.n)).max() < 1e-6
     finally:
         kx.sim_destroy(h)
 
