@@ -936,6 +936,124 @@ __global__ void __launch_bounds__(32) invit_df_kernel(int n, const dfl* __restri
   dfl* __restrict__ Z = (dfl*)Zout;      // iterates in place of the FP64 output
 #define LU(a, r) a[(size_t)(r) * n + L]
 #define ZC(r, c) Z[(size_t)(r) * n + (c)]
+  if (end == L + 1 && n > 1) {
+    // An eigenvalue alone in its cluster (the common case): the same two
+    // inverse-iteration steps with the passes fused.  Step 1 solves from the
+    // start vector without storing it, its backward sweep tracks max|x|;
+    // step 2 reads x scaled by 1/max (inverse iteration is linear, the scale
+    // only keeps the values in range), its backward sweep accumulates ||x||^2;
+    // one last pass writes x / ||x|| in FP64.  Six sweeps of n instead of 15.
+    const dfl lam = df_from_double(ev[L]);
+    dfl a = df_sub(ldg_df(d), lam), u = df_from_double(e[0]);
+    for (int r = 0; r < n - 1; ++r) {
+      const dfl b = df_from_double(e[r]);
+      const dfl dn = df_sub(ldg_df(d + r + 1), lam);
+      const dfl un = (r < n - 2) ? df_from_double(e[r + 1]) : dfl{0.0f, 0.0f};
+      if (df_abs_hi(a) >= df_abs_hi(b)) {
+        LU(pv, r) = 0;
+        if (df_abs_hi(a) < tiny.hi) a = (a.hi >= 0.0f) ? tiny : df_neg(tiny);
+        const dfl ra = df_recip(a);
+        const dfl f = df_mul(b, ra);
+        LU(dl, r) = f;
+        LU(rdd, r) = ra;
+        LU(du, r) = u;
+        LU(du2, r) = dfl{0.0f, 0.0f};
+        a = df_sub(dn, df_mul(f, u));
+        u = un;
+      } else {
+        LU(pv, r) = 1;
+        const dfl rb = df_recip(b);
+        const dfl f = df_mul(a, rb);
+        LU(rdd, r) = rb;
+        LU(dl, r) = f;
+        LU(du, r) = dn;
+        const dfl na = df_sub(u, df_mul(f, dn));
+        if (r < n - 2) {
+          LU(du2, r) = un;
+          u = df_neg(df_mul(f, un));
+        } else {
+          LU(du2, r) = dfl{0.0f, 0.0f};
+        }
+        a = na;
+      }
+    }
+    if (df_abs_hi(a) < tiny.hi) a = (a.hi >= 0.0f) ? tiny : df_neg(tiny);
+    LU(rdd, n - 1) = df_recip(a);
+    dfl scl = {1.0f, 0.0f};
+    dfl nrm = {0.0f, 0.0f};
+    for (int it = 0; it < 2; ++it) {
+      // forward (L with pivots); step 1 takes the start vector, step 2 the scaled x
+      dfl cur = (it == 0) ? df_from_double(start_value(0, L)) : df_mul(ZC(0, L), scl);
+      for (int r0 = 0; r0 < n - 1; r0 += kIvB) {
+        dfl nx[kIvB], fv[kIvB];
+        int pf[kIvB];
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 + q;
+          if (r < n - 1) {
+            nx[q] = (it == 0) ? df_from_double(start_value(r + 1, L)) : df_mul(ZC(r + 1, L), scl);
+            fv[q] = LU(dl, r);
+            pf[q] = LU(pv, r);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 + q;
+          if (r < n - 1) {
+            if (pf[q] == 0) {
+              ZC(r, L) = cur;
+              cur = df_sub(nx[q], df_mul(fv[q], cur));
+            } else {
+              ZC(r, L) = nx[q];
+              cur = df_sub(cur, df_mul(fv[q], nx[q]));
+            }
+          }
+        }
+      }
+      // backward (U, three diagonals, reciprocal pivots), with max|x| or ||x||^2
+      float mx = 0.0f;
+      dfl z2 = df_mul(cur, LU(rdd, n - 1));
+      ZC(n - 1, L) = z2;
+      mx = fmaxf(mx, df_abs_hi(z2));
+      if (it == 1) df_acc_mul(nrm, z2, z2);
+      dfl z1 = z2;
+      if (n > 1) {
+        z1 = df_mul(df_sub(ZC(n - 2, L), df_mul(LU(du, n - 2), z2)), LU(rdd, n - 2));
+        ZC(n - 2, L) = z1;
+        mx = fmaxf(mx, df_abs_hi(z1));
+        if (it == 1) df_acc_mul(nrm, z1, z1);
+      }
+      for (int r0 = n - 3; r0 >= 0; r0 -= kIvB) {
+        dfl zv[kIvB], uv[kIvB], u2[kIvB], rv[kIvB];
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 - q;
+          if (r >= 0) { zv[q] = ZC(r, L); uv[q] = LU(du, r); u2[q] = LU(du2, r); rv[q] = LU(rdd, r); }
+        }
+#pragma unroll
+        for (int q = 0; q < kIvB; ++q) {
+          const int r = r0 - q;
+          if (r >= 0) {
+            const dfl x = df_mul(df_sub(df_sub(zv[q], df_mul(uv[q], z1)), df_mul(u2[q], z2)), rv[q]);
+            ZC(r, L) = x;
+            mx = fmaxf(mx, df_abs_hi(x));
+            if (it == 1) df_acc_mul(nrm, x, x);
+            z2 = z1;
+            z1 = x;
+          }
+        }
+      }
+      if (it == 0) scl = (mx > 0.0f) ? df_recip(dfl{mx, 0.0f}) : dfl{1.0f, 0.0f};
+    }
+    const double nd = ::sqrt(df_to_double(df_norm(nrm)));
+    const dfl sc = (nd > 0.0) ? df_from_double(1.0 / nd) : dfl{0.0f, 0.0f};
+#pragma unroll 8
+    for (int r = 0; r < n; ++r) {
+      const dfl z = df_mul(ZC(r, L), sc);
+      Zout[(size_t)r * n + L] = df_to_double(z);
+    }
+    return;
+  }
   double prevlam = 0.0;
   for (int j = L; j < end; ++j) {
     double lamd = ev[j];

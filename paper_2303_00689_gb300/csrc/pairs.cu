@@ -238,9 +238,107 @@ __device__ __forceinline__ G3 g3_norm(const G3& a) {
   return G3{df_norm(a.v), {df_norm(a.d[0]), df_norm(a.d[1]), df_norm(a.d[2])}};
 }
 
+// Double-float radial dual number (value, d/dR) for the local integrals.
+struct G1 {
+  dfl v, d;
+};
+__device__ __forceinline__ G1 g1_zero() { return G1{{0.0f, 0.0f}, {0.0f, 0.0f}}; }
+__device__ __forceinline__ G1 g1_sub(const G1& a, const G1& b) { return G1{df_sub(a.v, b.v), df_sub(a.d, b.d)}; }
+__device__ __forceinline__ G1 g1_half(const G1& a) {
+  return G1{{a.v.hi * 0.5f, a.v.lo * 0.5f}, {a.d.hi * 0.5f, a.d.lo * 0.5f}};
+}
+// a * q for a float q (exact product of the high part, one rounding of the low part)
+__device__ __forceinline__ dfl df_mul_f(dfl a, float q) {
+  const float p = KX_FMUL(a.hi, q);
+  float e = KX_FFMA(a.hi, q, -p);
+  e = KX_FFMA(a.lo, q, e);
+  return df_fast_two_sum(p, e);
+}
+// 1/sqrt(s), s > 0: FP32 estimate y0 and one Newton step y0 + y0 (1 - s y0^2) / 2
+// with s y0^2 in double-float (relative error ~(3/8) h^2, h = 1 - s y0^2 ~ 1e-7)
+__device__ __forceinline__ dfl df_rsqrt(dfl s) {
+  const float y0 = rsqrtf(s.hi);
+  const float p = KX_FMUL(y0, y0);
+  const dfl y2 = dfl{p, KX_FFMA(y0, y0, -p)};
+  const dfl t = df_mul(s, y2);
+  const float h = KX_FSUB(KX_FSUB(1.0f, t.hi), t.lo);
+  return df_fast_two_sum(y0, KX_FMUL(KX_FMUL(y0, h), 0.5f));
+}
+
+// point-charge multipole lengths of one element in double-float
+struct ChargeDF {
+  dfl D1, D2, rho0, rho1, rho2;
+};
+__device__ __forceinline__ ChargeDF charge_df(const Elem& e) {
+  return ChargeDF{df_from_double(e.D1), df_from_double(e.D2), df_from_double(e.rho0), df_from_double(e.rho1),
+                  df_from_double(e.rho2)};
+}
+__device__ __forceinline__ dfl df_twice(dfl a) { return dfl{a.hi * 2.0f, a.lo * 2.0f}; }
+
+// the charge sets of product_charges, positions and radii in double-float
+// (the charges themselves, 1, +-1/2 and +-1/4, are exact in FP32)
+__device__ __forceinline__ int product_charges_df(int p, const ChargeDF& c, float q[4], dfl x[4], dfl y[4],
+                                                  dfl z[4], dfl r[4]) {
+  const dfl zero = {0.0f, 0.0f};
+  for (int i = 0; i < 4; ++i) { q[i] = 0.0f; x[i] = zero; y[i] = zero; z[i] = zero; r[i] = c.rho0; }
+  const int a = c_prod_mu[p], b = c_prod_nu[p];
+  if (a == 0 && b == 0) { q[0] = 1.0f; r[0] = c.rho0; return 1; }
+  if (a == 0) {
+    dfl* c0 = (b == 1) ? x : (b == 2) ? y : z;
+    q[0] = 0.5f; c0[0] = c.D1; r[0] = c.rho1;
+    q[1] = -0.5f; c0[1] = df_neg(c.D1); r[1] = c.rho1;
+    return 2;
+  }
+  if (a == b) {
+    dfl* c0 = (a == 1) ? x : (a == 2) ? y : z;
+    q[0] = 1.0f; r[0] = c.rho0;
+    q[1] = 0.25f; c0[1] = df_twice(c.D2); r[1] = c.rho2;
+    q[2] = 0.25f; c0[2] = df_neg(df_twice(c.D2)); r[2] = c.rho2;
+    q[3] = -0.5f; r[3] = c.rho2;
+    return 4;
+  }
+  dfl* ca = (a == 1) ? x : (a == 2) ? y : z;
+  dfl* cb = (b == 1) ? x : (b == 2) ? y : z;
+  const float sa[4] = {1.0f, -1.0f, 1.0f, -1.0f};
+  const float sb[4] = {1.0f, -1.0f, -1.0f, 1.0f};
+  for (int i = 0; i < 4; ++i) {
+    q[i] = 0.25f * sa[i] * sb[i];
+    ca[i] = (sa[i] > 0.0f) ? c.D2 : df_neg(c.D2);
+    cb[i] = (sb[i] > 0.0f) ? c.D2 : df_neg(c.D2);
+    r[i] = c.rho2;
+  }
+  return 4;
+}
+
+// local_integral in double-float with d/dR: sum of q_i q_j / sqrt(dz^2 + dx^2
+// + dy^2 + (rho_i + rho_j)^2), dz = z_i - z_j - R, whose R-derivative is
+// q_i q_j dz / s^3; times e^2 (e2 in double-float)
+__device__ G1 local_integral_df(int p, int qd, const ChargeDF& ca, const ChargeDF& cb, dfl R, dfl e2) {
+  float qa[4], qb[4];
+  dfl xa[4], ya[4], za[4], ra[4], xb[4], yb[4], zb[4], rb[4];
+  const int na = product_charges_df(p, ca, qa, xa, ya, za, ra);
+  const int nb = product_charges_df(qd, cb, qb, xb, yb, zb, rb);
+  dfl v = {0.0f, 0.0f}, dv = {0.0f, 0.0f};
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < nb; ++j) {
+      const dfl dx = df_sub(xa[i], xb[j]), dy = df_sub(ya[i], yb[j]), rr = df_add(ra[i], rb[j]);
+      const dfl dz = df_sub(df_sub(za[i], zb[j]), R);
+      dfl s2 = df_mul(dz, dz);
+      s2 = df_add(s2, df_mul(dx, dx));
+      s2 = df_add(s2, df_mul(dy, dy));
+      s2 = df_add(s2, df_mul(rr, rr));
+      const dfl r = df_rsqrt(s2);
+      const dfl r3dz = df_mul(df_mul(df_mul(r, r), r), dz);
+      const float qq = qa[i] * qb[j];
+      df_acc(v, df_mul_f(r, qq));
+      df_acc(dv, df_mul_f(r3dz, qq));
+    }
+  return G1{df_mul(df_norm(v), e2), df_mul(df_norm(dv), e2)};
+}
+
 // W = C I C^T in double-float from the local integrals as radial duals
 // (value, d/dR): promoted by d/dd_k = u_k d/dR, rotated, written as D3
-__device__ void rotate_blocks_df(const D1 (&Ir)[10][10], const D3 (&Tf)[4][4], const double* uv, int pa, int pb,
+__device__ void rotate_blocks_df(const G1 (&Ir)[10][10], const D3 (&Tf)[4][4], const double* uv, int pa, int pb,
                                  D3* Wout) {
   G3 Tg[4][4];
 #pragma unroll
@@ -258,10 +356,9 @@ __device__ void rotate_blocks_df(const D1 (&Ir)[10][10], const D3 (&Tf)[4][4], c
     for (int q = 0; q < 10; ++q) {
       I[p][q] = g3_zero();
       if (p < pa && q < pb && c_prod_cls[p] == c_prod_cls[q]) {
-        const dfl dr = df_from_double(Ir[p][q].d);
-        I[p][q].v = df_from_double(Ir[p][q].v);
+        I[p][q].v = Ir[p][q].v;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) I[p][q].d[k] = df_mul(dr, ug[k]);
+        for (int k = 0; k < 3; ++k) I[p][q].d[k] = df_mul(Ir[p][q].d, ug[k]);
       }
     }
   G3 C[10][10];
@@ -332,6 +429,31 @@ __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T
   // local integrals: the distinct ones (rows ss, sz, xx, zz of the sigma/
   // delta class, sx and xz of the pi class) from the charge sets, the rest by
   // the x <-> y mirror and the rotational-invariance relation for (xy|xy)
+  if constexpr (DFROT) {
+    // local integrals and the rotation in double-float (mixed path)
+    const ChargeDF ca = charge_df(ea), cb = charge_df(eb);
+    const dfl Rd = df_from_double(val(R)), e2 = df_from_double(kE2);
+    G1 Ig[10][10];
+    for (int p = 0; p < 10; ++p)
+      for (int q = 0; q < 10; ++q) Ig[p][q] = g1_zero();
+    for (int p = 0; p < pa; ++p) {
+      if (p == 2 || p == 5 || p == 7 || p == 9) continue;        // mirrored or derived below
+      for (int q = 0; q < pb; ++q) {
+        if (c_prod_cls[p] != c_prod_cls[q]) continue;
+        if (c_prod_cls[p] == 1 && (q == 2 || q == 9)) continue;
+        Ig[p][q] = local_integral_df(p, q, ca, cb, Rd, e2);
+      }
+    }
+    if (pa == 10) {
+      for (int q = 0; q < pb; ++q) {
+        const int mq = mirror_xy(q);
+        if (c_prod_cls[q] == 0) Ig[5][q] = Ig[4][mq];
+        if (c_prod_cls[q] == 2) { Ig[2][q] = Ig[1][mq]; Ig[9][q] = Ig[8][mq]; }
+      }
+      if (pb == 10) Ig[7][7] = g1_half(g1_sub(Ig[4][4], Ig[4][5]));
+    }
+    rotate_blocks_df(Ig, Tf, uv, pa, pb, Wout);
+  } else {
   Tr Ir[10][10];
   for (int p = 0; p < 10; ++p)
     for (int q = 0; q < 10; ++q) Ir[p][q] = cst<Tr>(0.0);
@@ -352,9 +474,6 @@ __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T
     if (pb == 10) Ir[7][7] = 0.5 * (Ir[4][4] - Ir[4][5]);
   }
 
-  if constexpr (DFROT) {
-    rotate_blocks_df(Ir, Tf, uv, pa, pb, Wout);
-  } else {
   T I[10][10];
   for (int p = 0; p < 10; ++p)
     for (int q = 0; q < 10; ++q)
