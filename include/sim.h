@@ -256,6 +256,9 @@ int sim_batch_step(sim_handle* const* handles, int count, int nsteps);
 typedef struct sim_batch sim_batch;
 int sim_batch_create(sim_handle* const* handles, int count, sim_batch** out);
 int sim_batch_run(sim_batch* b, int nsteps);
+/* Number of co-resident groups the batch's graph runs one after the other
+ * (1 when every member's eigensolver grid fits on the device together). */
+int sim_batch_groups(const sim_batch* b);
 void sim_batch_destroy(sim_batch* b);
 
 /* Bytes of device memory sim_create allocates for this molecule/config. */
@@ -420,13 +423,16 @@ int sim_tc_gemm_noalloc(int n, const double* A, const double* B, int terms, int 
  * memory; synchronous. */
 int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sym, double* C);
 
-/* sim_debug_tc_gemm_grouped -- the same 3-slice product (terms = 6) computed
- * the way the mixed path's DMPT products of eq. 36 are: all slices of a
- * 64-deep k-tile staged together, the weight-1 slice product summed exactly
- * per 512-K chunk and the lower-weight ones in FP32, so C is within ~2^-26 of
- * sum_k |A_ik||B_jk| of the exact 6-term slice product (not bitwise equal).
- * Arguments, memory and errors as sim_debug_tc_gemm. */
-int sim_debug_tc_gemm_grouped(int n, const double* A, const double* B, int sym, double* C);
+/* sim_debug_tc_gemm_grouped -- the 3-slice (slices = 3, terms 6) or 4-slice
+ * (slices = 4, terms 10) product computed the way the mixed path computes the
+ * DMPT products of eq. 36 (3 slices) and the density product of eq. 19 and
+ * the back-transformation (4 slices): all slices of a k-tile staged together,
+ * the weight-1 slice product summed exactly per 512-K chunk and the
+ * lower-weight ones in FP32, so C is within ~2^-26 (3 slices) or ~2^-28
+ * (4 slices) of sum_k |A_ik||B_jk| of the exact slice product (not bitwise
+ * equal).  Other slice counts: SIM_EINVAL.  Arguments, memory and errors as
+ * sim_debug_tc_gemm. */
+int sim_debug_tc_gemm_grouped(int n, const double* A, const double* B, int slices, int sym, double* C);
 
 /* sim_measure_peak -- FMA throughput of `device` in TFLOP/s (2 flops per FMA),
  * kind 0: FP64, kind 1: FP32; 8 independent chains per thread on 8 blocks of

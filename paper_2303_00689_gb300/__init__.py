@@ -31,7 +31,7 @@ EXPORTED = (
     "sim_tc_gemm_noalloc", "sim_records", "sim_wait", "sim_enable_graphs", "sim_batch_step",
     "sim_estimate_bytes", "sim_server_create", "sim_submit", "sim_poll", "sim_server_stats_get",
     "sim_server_drain", "sim_server_destroy", "sim_save", "sim_load", "sim_batch_create", "sim_batch_run",
-    "sim_batch_destroy", "sim_measure_peak", "sim_debug_barrier_limit", "sim_debug_wait_expiry",
+    "sim_batch_destroy", "sim_batch_groups", "sim_measure_peak", "sim_debug_barrier_limit", "sim_debug_wait_expiry",
 )
 
 
@@ -132,7 +132,7 @@ def lib():
         L.sim_destroy.argtypes = [C.c_void_p]
         L.sim_destroy.restype = None
         L.sim_debug_tc_gemm.argtypes = [C.c_int, dp, dp, C.c_int, C.c_int, dp]
-        L.sim_debug_tc_gemm_grouped.argtypes = [C.c_int, dp, dp, C.c_int, dp]
+        L.sim_debug_tc_gemm_grouped.argtypes = [C.c_int, dp, dp, C.c_int, C.c_int, dp]
         L.sim_tc_gemm_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                           C.c_void_p]
         L.sim_records.argtypes = [C.c_void_p, P(sim_step_result), C.c_int]
@@ -144,6 +144,7 @@ def lib():
         L.sim_batch_run.argtypes = [C.c_void_p, C.c_int]
         L.sim_batch_destroy.argtypes = [C.c_void_p]
         L.sim_batch_destroy.restype = None
+        L.sim_batch_groups.argtypes = [C.c_void_p]
         L.sim_load.argtypes = [C.c_char_p, C.c_int, C.c_void_p, P(C.c_void_p)]
         L.sim_wait.argtypes = [C.c_void_p]
         L.sim_enable_graphs.argtypes = [C.c_void_p, C.c_int]
@@ -325,12 +326,12 @@ def sim_debug_tc_gemm(A, B, terms=1, sym=False):
     return out
 
 
-def sim_debug_tc_gemm_grouped(A, B, sym=False):
+def sim_debug_tc_gemm_grouped(A, B, sym=False, slices=3):
     A = _f64(A)
     B = _f64(B)
     n = A.shape[0]
     out = np.empty((n, n))
-    _check(lib().sim_debug_tc_gemm_grouped(n, _dptr(A), _dptr(B), 1 if sym else 0, _dptr(out)))
+    _check(lib().sim_debug_tc_gemm_grouped(n, _dptr(A), _dptr(B), int(slices), 1 if sym else 0, _dptr(out)))
     return out
 
 
@@ -378,6 +379,10 @@ def sim_batch_create(handles):
 
 def sim_batch_run(b, nsteps):
     _check(lib().sim_batch_run(b, int(nsteps)))
+
+
+def sim_batch_groups(b):
+    return int(lib().sim_batch_groups(b))
 
 
 def sim_batch_destroy(b):

@@ -230,9 +230,10 @@ static void density(sim_handle* h) {
   int n = h->n;
   launch_scale_columns(s, n, h->Q, h->f, h->Qs);
   if (mixed(h)) {
-    // four fixed-point BF16 slices, ten slice products (32 bits per row scale)
+    // four fixed-point BF16 slices, ten slice products (32 bits per row scale),
+    // all slices of a k-tile staged together (tc_gemm_grouped4)
     tc_split(s, h->tw, kSlotQs, h->Qs, 4, 0);
-    tc_gemm(s, h->tw, kSlotQs, kSlotQs, 10, 1.0, h->D, 1);
+    tc_gemm_grouped4(s, h->tw, kSlotQs, kSlotQs, 1.0, h->D, 1);
   } else {
     dgemm(s, 0, 1, n, n, n, 1.0, h->Qs, n, h->Qs, n, 0.0, h->D, n, 1);
   }
@@ -1072,6 +1073,8 @@ static int batch_capture(sim_batch* b, int p) {
   return SIM_OK;
 }
 
+int sim_batch_groups(const sim_batch* b) { return b ? (int)b->group_end.size() : 0; }
+
 int sim_batch_create(sim_handle* const* hs, int count, sim_batch** out) {
   if (!hs || count < 1 || !out) return fail(SIM_EINVAL, "bad batch arguments");
   *out = nullptr;
@@ -1377,6 +1380,7 @@ int sim_phase_times(sim_handle* h, double* ms, long long* launches, double* work
 // Test hooks: C = sum of BF16-piece products of A and B^T on the tensor cores
 // (terms 1, 3, 6, 10: the exact per-segment kernel; grouped: the DMPT's 3-slice kernel).
 static int debug_tc_gemm(int n, const double* A, const double* B, int terms, int sym, bool grouped, double* C) {
+  if (grouped && terms != 6 && terms != 10) return fail(SIM_EINVAL, "grouped products take 3 or 4 slices");
   if (n < 1 || !A || !B || !C || (terms != 1 && terms != 3 && terms != 6 && terms != 10))
     return fail(SIM_EINVAL, "bad argument");
   if (!tc_available()) return fail(SIM_EINVAL, "tensor-map entry point unavailable");
@@ -1401,8 +1405,10 @@ static int debug_tc_gemm(int n, const double* A, const double* B, int terms, int
     cudaMemset(dC, 0, nn * sizeof(double));
     tc_split(s, w, kSlotT0, dA, pieces, 0);
     tc_split(s, w, kSlotT1, dB, pieces, 0);
-    if (grouped)
+    if (grouped && terms == 6)
       tc_gemm_grouped(s, w, kSlotT0, kSlotT1, 1.0, dC, sym);
+    else if (grouped)
+      tc_gemm_grouped4(s, w, kSlotT0, kSlotT1, 1.0, dC, sym);
     else
       tc_gemm(s, w, kSlotT0, kSlotT1, terms, 1.0, dC, sym);
     int err = 0;
@@ -1421,8 +1427,9 @@ int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sy
   return debug_tc_gemm(n, A, B, terms, sym, false, C);
 }
 
-int sim_debug_tc_gemm_grouped(int n, const double* A, const double* B, int sym, double* C) {
-  return debug_tc_gemm(n, A, B, 6, sym, true, C);
+int sim_debug_tc_gemm_grouped(int n, const double* A, const double* B, int slices, int sym, double* C) {
+  if (slices != 3 && slices != 4) return fail(SIM_EINVAL, "slices must be 3 or 4");
+  return debug_tc_gemm(n, A, B, slices == 3 ? 6 : 10, sym, true, C);
 }
 
 void sim_destroy(sim_handle* h) {

@@ -1388,7 +1388,8 @@ void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w, double rel_tol, 
   count_launch();
   if (df_path) {
     const long long thr = (long long)n * kMsLanes;
-    bisect_df_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(n, d_dfl, e2_dfl, w.scal, rel_tol, eps);
+    // one warp (4 eigenvalues) per block, so the n / 4 blocks spread over all SMs
+    bisect_df_kernel<<<(unsigned)((thr + 31) / 32), 32, 0, s>>>(n, d_dfl, e2_dfl, w.scal, rel_tol, eps);
   } else {
     bisect_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e2, w.scal, df, e2f, rel_tol, eps);   // spread over all SMs
   }
@@ -1584,13 +1585,13 @@ static int eig_backtransform_tc(cudaStream_t s, int n, double* Q, EigWork& w, co
     const int ldm = tc_ld(m);
     double* Zs = Zt + c0;                                // n x m, ld n
     tc_split_rows(s, n, m, Zs, n, 4, sZ, ldm, stride);
-    const int parts = tc_gemm_rc_splitk(s, n, kb, m, sZ, ldm, stride, sc.vs + (size_t)b * sc.vs_blk, ldm,
-                                        sc.vs_slice, 10, 1.0, sc.part, kBtBlockTc, kBtSplitK, err);   // U parts
+    const int parts = tc_gemm_grouped_rc_splitk(s, n, kb, m, sZ, ldm, stride, sc.vs + (size_t)b * sc.vs_blk, ldm,
+                                                sc.vs_slice, 1.0, sc.part, kBtBlockTc, kBtSplitK, err);   // U parts
     if (parts <= 0) return -1;
     const int ldk = tc_ld(kb);                           // U slices fit the slot: kb <= n
     tc_reduce_split_rows(s, n, kb, sc.part, parts, kBtBlockTc, 4, sU, ldk, stride);
-    if (tc_gemm_rc(s, n, m, kb, sU, ldk, stride, sc.ys + (size_t)b * sc.ys_blk, kBtBlockTc, sc.ys_slice, 10, -1.0,
-                   Zs, n, 1, err) != 0)                                                      // Zs -= U Y_b
+    if (tc_gemm_grouped_rc(s, n, m, kb, sU, ldk, stride, sc.ys + (size_t)b * sc.ys_blk, kBtBlockTc, sc.ys_slice,
+                           -1.0, Zs, n, 1, err) != 0)                                        // Zs -= U Y_b
       return -1;
   }
   transpose_sq(s, n, Zt, Q);

@@ -346,47 +346,88 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Slice-grouped product of two 3-slice operands (the DMPT products of eq. 36).
-// Same tile, warps and bounded waits as tc_gemm_kernel, but one pipeline stage
-// holds all three slices of A and of B for one 64-deep k-tile (96 KB), and
-// the six kept slice products of that k-tile are issued from it: every byte
-// brought into shared memory feeds twice the tensor-core work of the
-// per-segment kernel.  Two accumulators per TMEM buffer:
-//   acc0  : A0 B0, summed exactly over a 512-K chunk (as in tc_gemm_kernel);
-//   acc12 : A0 B1 + A1 B0 + A0 B2 + A1 B1 + A2 B0, weights 2^-8 and 2^-16 of
-//           acc0's, summed in FP32 over the chunk.
-// Both are folded into the double-float registers after every chunk.  The
-// FP32 rounding of acc12 is at most ~2^-26 of sum |a||b| per entry, below the
-// 2^-20 truncation of three slices, so the result is the 3-slice product to
-// within that bound rather than bitwise the sum of its slice products.
-// TMEM: 4 x 128 columns (acc0 and acc12, double-buffered).
-constexpr int kGSlices = 3;
-constexpr int kGStages = 2;
-constexpr int kGStageBytes = 2 * kGSlices * kTileBytesA;                 // 96 KB
-constexpr int kGSmemBytes = kGStages * kGStageBytes + 1024 + 256;
-static_assert(kBM * (kBN + 1) * (int)sizeof(double) <= kGStages * kGStageBytes, "output tile fits the stages");
+// the same for 64-byte swizzled K-major tiles (8-row atoms of 512 B)
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
+  d |= (uint64_t)(512 >> 4) << 32;                 // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)4 << 61;                          // layout: 64B swizzle
+  return d;
+}
 
+// Slice-grouped products of S-slice operands (S = 3: the DMPT products of
+// eq. 36; S = 4: the density product of eq. 19 and the back-transformation).
+// Same tile, warps and bounded waits as tc_gemm_kernel, but one pipeline stage
+// holds all S slices of A and of B for one BK-deep k-tile, and the S(S+1)/2
+// kept slice products of that k-tile are issued from it: every byte brought
+// into shared memory feeds S(S+1)/(2S) times the tensor work of the
+// per-segment kernel.  Two accumulators per TMEM buffer:
+//   acc0 : A0 B0, summed exactly over a 512-K chunk (as in tc_gemm_kernel);
+//   acc1 : every product A_a B_b with 1 <= a + b < S (weights 2^-8 ... of
+//          acc0's), smallest weights first, summed in FP32 over the chunk.
+// Both are folded into the double-float registers after every chunk.  The
+// FP32 rounding of acc1 is ~2^-(24 + 7) of sum |a||b| per addition, so the
+// result is the S-slice product to within ~2^-26 (S = 3) or ~2^-28 (S = 4)
+// of sum_k |a_ik||b_jk|, below or at the truncation of the slices, rather
+// than bitwise the sum of its slice products.
+// Layouts: BK = 64 with 128-byte swizzled boxes (2 stages of 96 KB for S = 3),
+// BK = 32 with 64-byte swizzled boxes (3 stages of 64 KB for S = 4); the
+// tensor maps passed in must use the matching box and swizzle.
+// Split-K (kt_split > 0): CTA z takes k-tiles [z kt_split, (z + 1) kt_split)
+// and writes its partial product to C + z c_zstride.  beta != 0 adds to C.
+// The output tile goes through shared memory (the stages are idle by then).
+// TMEM: 4 x 128 columns (acc0 and acc1, double-buffered).
+template <int S, int BK>
+struct GroupedCfg {
+  static constexpr int kTile = kBM * BK * 2;                 // one slice tile of A or B
+  static constexpr int kStageBytes = 2 * S * kTile;
+  static constexpr int kStages = (192 * 1024) / kStageBytes;
+  static constexpr int kChunkTiles = 512 / BK;               // k-tiles per exact chunk
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+  static_assert(kBM == kBN, "A and B tiles share one size");
+  static_assert(kBM * (kBN + 1) * (int)sizeof(double) <= kStages * kStageBytes, "output tile fits the stages");
+  static_assert(kStages >= 2, "at least two stages");
+};
+
+template <int BK>
+__device__ __forceinline__ uint64_t grouped_desc(uint32_t addr) {
+  if constexpr (BK == 64)
+    return smem_desc(addr);
+  else
+    return smem_desc_sw64(addr);
+}
+
+template <int S, int BK>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_gemm_grouped_kernel(const __grid_constant__ TcMaps maps, int n, double alpha, double* __restrict__ C,
-                           int ldc, int sym, int* err, const int* gate) {
+    tc_gemm_grouped_kernel(const __grid_constant__ TcMaps maps, int M, int N, int K, double alpha,
+                           double* __restrict__ C, int ldc, int sym, int beta, int* err, const int* gate,
+                           int kt_split, long long c_zstride) {
+  using Cfg = GroupedCfg<S, BK>;
+  constexpr int T = Cfg::kTile, kStages = Cfg::kStages, kStageBytes = Cfg::kStageBytes;
   if (gate && *gate == 0) return;      // whole CTA, before any barrier or TMEM use
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (sym && bi > bj) return;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(base + kGStages * kGStageBytes);
-  uint64_t* empty = full + kGStages;
-  uint64_t* acc_full = empty + kGStages;
+  uint64_t* full = (uint64_t*)(base + kStages * kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* acc_full = empty + kStages;
   uint64_t* acc_empty = acc_full + 2;
   uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = bi * kBM, n0 = bj * kBN;
-  const int ktiles = (n + kBK - 1) / kBK;
-  const int nchunks = (ktiles + kChunk - 1) / kChunk;
+  const int ktiles_all = (K + BK - 1) / BK;
+  const int kt0 = (kt_split > 0) ? (int)blockIdx.z * kt_split : 0;
+  int ktiles = (kt_split > 0) ? min(kt_split, ktiles_all - kt0) : ktiles_all;
+  if (ktiles < 0) ktiles = 0;
+  C += (long long)blockIdx.z * c_zstride;
+  const int nchunks = (ktiles + Cfg::kChunkTiles - 1) / Cfg::kChunkTiles;
 
   if (threadIdx.x == 0) {
-    for (int st = 0; st < kGStages; ++st) {
+    for (int st = 0; st < kStages; ++st) {
       mbar_init(&full[st], 1);
       mbar_init(&empty[st], 1);
     }
@@ -409,26 +450,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // TMA producer: the three slices of A and of B of k-tile `it` into one stage
+      // TMA producer: the S slices of A and of B of k-tile `it` into one stage
       int issued = 0;
       bool ok = true;
       for (int it = 0; it < ktiles && ok; ++it) {
-        const int st = it % kGStages;
-        const uint32_t ph = (uint32_t)(it / kGStages) & 1u;
+        const int st = it % kStages;
+        const uint32_t ph = (uint32_t)(it / kStages) & 1u;
         if (!mbar_wait(&empty[st], ph ^ 1u, err)) { ok = false; break; }
-        uint8_t* sbase = base + st * kGStageBytes;
-        mbar_expect_tx(&full[st], kGStageBytes);
+        uint8_t* sbase = base + st * kStageBytes;
+        mbar_expect_tx(&full[st], kStageBytes);
 #pragma unroll
-        for (int a = 0; a < kGSlices; ++a) {
-          tma_load_2d(sbase + a * kTileBytesA, &maps.a[a], &full[st], it * kBK, m0);
-          tma_load_2d(sbase + (kGSlices + a) * kTileBytesA, &maps.b[a], &full[st], it * kBK, n0);
+        for (int a = 0; a < S; ++a) {
+          tma_load_2d(sbase + a * T, &maps.a[a], &full[st], (kt0 + it) * BK, m0);
+          tma_load_2d(sbase + (S + a) * T, &maps.b[a], &full[st], (kt0 + it) * BK, n0);
         }
         issued = it + 1;
       }
       if (!ok) {
-        for (int it = (issued > kGStages ? issued - kGStages : 0); it < issued; ++it) {
-          const int st = it % kGStages;
-          const uint32_t ph = (uint32_t)(it / kGStages) & 1u;
+        for (int it = (issued > kStages ? issued - kStages : 0); it < issued; ++it) {
+          const int st = it % kStages;
+          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
           for (long long w = 0; w < kWaitLimit && !mbar_try(&full[st], ph); ++w) {
           }
         }
@@ -443,27 +484,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!mbar_wait(&acc_empty[b], ((uint32_t)(c >> 1) & 1u) ^ 1u, err)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d0 = tmem + (uint32_t)(b * kBN);
-        const uint32_t d12 = tmem + (uint32_t)((2 + b) * kBN);
-        const int it0 = c * kChunk;
-        const int it1 = (it0 + kChunk < ktiles) ? it0 + kChunk : ktiles;
+        const uint32_t d1 = tmem + (uint32_t)((2 + b) * kBN);
+        const int it0 = c * Cfg::kChunkTiles;
+        const int it1 = (it0 + Cfg::kChunkTiles < ktiles) ? it0 + Cfg::kChunkTiles : ktiles;
         for (int it = it0; it < it1; ++it) {
-          const int st = it % kGStages;
-          const uint32_t ph = (uint32_t)(it / kGStages) & 1u;
+          const int st = it % kStages;
+          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
           if (!mbar_wait(&full[st], ph, err)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t sa = smem_u32(base + st * kGStageBytes);
-          const uint32_t sb = sa + kGSlices * kTileBytesA;
+          const uint32_t sa = smem_u32(base + st * kStageBytes);
+          const uint32_t sb = sa + S * T;
 #pragma unroll
-          for (int k = 0; k < kBK / 16; ++k) {
-            const uint32_t first = (it > it0 || k > 0) ? 1u : 0u;
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint32_t acc = (it > it0 || k > 0) ? 1u : 0u;
             // weight 1: A0 B0
-            umma_bf16(d0, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, first);
-            // weights 2^-16 then 2^-8 (smallest first)
-            umma_bf16(d12, smem_desc(sa + 2 * kTileBytesA + k * 32), smem_desc(sb + k * 32), idesc, first);
-            umma_bf16(d12, smem_desc(sa + kTileBytesA + k * 32), smem_desc(sb + kTileBytesA + k * 32), idesc, 1u);
-            umma_bf16(d12, smem_desc(sa + k * 32), smem_desc(sb + 2 * kTileBytesA + k * 32), idesc, 1u);
-            umma_bf16(d12, smem_desc(sa + kTileBytesA + k * 32), smem_desc(sb + k * 32), idesc, 1u);
-            umma_bf16(d12, smem_desc(sa + k * 32), smem_desc(sb + kTileBytesA + k * 32), idesc, 1u);
+            umma_bf16(d0, grouped_desc<BK>(sa + k * 32), grouped_desc<BK>(sb + k * 32), idesc, acc);
+            // weights 2^-8(S-1) ... 2^-8, smallest first; the first one starts acc1 in a new chunk
+#pragma unroll
+            for (int dsum = S - 1; dsum >= 1; --dsum)
+#pragma unroll
+              for (int a = dsum; a >= 0; --a) {
+                const uint32_t acc1 = (dsum == S - 1 && a == dsum) ? acc : 1u;
+                umma_bf16(d1, grouped_desc<BK>(sa + a * T + k * 32), grouped_desc<BK>(sb + (dsum - a) * T + k * 32),
+                          idesc, acc1);
+              }
           }
           umma_commit(&empty[st]);
         }
@@ -499,8 +543,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
-    // The tile goes through shared memory (the pipeline stages are idle once
-    // the last chunk has been read): the thread's 32 values at constant
+    // the tile through shared memory: the thread's 32 values at constant
     // offsets, then row-contiguous stores of the tile and, for a symmetric
     // result, of its transpose.  Every epilogue warp reaches the named
     // barrier; the global stores run only when no wait of any CTA expired.
@@ -517,14 +560,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int idx = t; idx < kBM * kBN; idx += kEpiWarps * 32) {
         const int rr = idx / kBN, cc = idx - rr * kBN;
         const int row = m0 + rr, col = n0 + cc;
-        if (row < n && col < n && !(sym && row > col)) C[(size_t)row * ldc + col] = tile[rr * kLdT + cc];
+        if (row < M && col < N && !(sym && row > col)) {
+          const size_t at = (size_t)row * ldc + col;
+          C[at] = beta ? C[at] + tile[rr * kLdT + cc] : tile[rr * kLdT + cc];
+        }
       }
       if (sym) {
         // C[col][row] for row < col: rows of the output are columns of the tile
         for (int idx = t; idx < kBM * kBN; idx += kEpiWarps * 32) {
           const int cr = idx / kBM, rc = idx - cr * kBM;   // output row n0 + cr, column m0 + rc
           const int row = m0 + rc, col = n0 + cr;
-          if (row < n && col < n && row < col) C[(size_t)col * ldc + row] = tile[rc * kLdT + cr];
+          if (row < M && col < N && row < col) {
+            const size_t at = (size_t)col * ldc + row;
+            C[at] = beta ? C[at] + tile[rc * kLdT + cr] : tile[rc * kLdT + cr];
+          }
         }
       }
     }
@@ -730,8 +779,34 @@ __device__ __forceinline__ void split_row_warp(const RowSplit& q, int r, int sli
     m = (t > m) ? t : m;
   }
   const int e = exponent_of_max(m);
-  for (int k = lane; k < q.ld; k += 32)
-    slice_value((k < q.cols) ? x[k] : 0.0, e, slices, q.base, q.stride, (size_t)r * q.ld + k);
+  // eight consecutive columns per lane and step: all eight loads are issued
+  // before the slicing and its stores (the stores may alias nothing the loads
+  // read, but the compiler cannot know that), and each slice gets two aligned
+  // 8-byte stores (ld is a multiple of 8)
+  __nv_bfloat16* out = q.base + (size_t)r * q.ld;
+  for (int k0 = 8 * lane; k0 < q.ld; k0 += 256) {
+    double xv[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) xv[c] = (k0 + c < q.cols) ? x[k0 + c] : 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      __nv_bfloat16 v[4][kTcMaxSlices];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) slice_digits(xv[4 * h + c], e, slices, v[c]);
+#pragma unroll
+      for (int a = 0; a < kTcMaxSlices; ++a) {
+        if (a < slices) {
+          __nv_bfloat162 lo2, hi2;
+          lo2.x = v[0][a]; lo2.y = v[1][a];
+          hi2.x = v[2][a]; hi2.y = v[3][a];
+          uint2 w;
+          w.x = *(const uint32_t*)&lo2;
+          w.y = *(const uint32_t*)&hi2;
+          *(uint2*)(out + a * q.stride + k0 + 4 * h) = w;
+        }
+      }
+    }
+  }
 }
 
 // One pass per row of a square n x n operand, one block of kSqThreads per row:
@@ -876,6 +951,7 @@ struct TcBuffers {
   __nv_bfloat16* piece[kTcPieceSlots][kTcMaxSlices];
   __nv_bfloat16** dpieces;            // device copy of the slice pointers, per slot
   CUtensorMap map[kTcPieceSlots][kTcMaxSlices];
+  CUtensorMap map64[kTcPieceSlots][kTcMaxSlices];   // 32-wide boxes, 64-byte swizzle (grouped 4-slice kernel)
   int* ex;                            // per-row exponents, one array per slot
   int* err;
   bool maps_ok;
@@ -888,6 +964,21 @@ size_t tc_work_bytes(int n) {
   size_t one = ((size_t)n * ld * 2 + 1023) & ~(size_t)1023;
   size_t exb = (((size_t)kTcPieceSlots * n * sizeof(int)) + 1023) & ~(size_t)1023;
   return 2048 + exb + 1024 + (size_t)kTcPieceSlots * kTcMaxSlices * one + 256;
+}
+
+// rows x cols BF16 operand (row length ld), boxes of `bk` columns x kBM rows:
+// bk = 64 with the 128-byte swizzle, bk = 32 with the 64-byte swizzle
+static bool make_map_rc_box(CUtensorMap* m, void* ptr, int rows, int cols, int ld, int bk) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)kBM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 static bool make_map_rc(CUtensorMap* m, void* ptr, int rows, int cols, int ld) {
@@ -934,6 +1025,7 @@ void tc_work_bind(TcWork& w, void* base, int n) {
       tb->piece[s][k] = (__nv_bfloat16*)p;
       p += one;
       tb->maps_ok = tb->maps_ok && make_map(&tb->map[s][k], tb->piece[s][k], n, tb->ld);
+      tb->maps_ok = tb->maps_ok && make_map_rc_box(&tb->map64[s][k], tb->piece[s][k], n, n, tb->ld, 32);
     }
   w.base = tb;
   w.bytes = tc_work_bytes(n);
@@ -1005,23 +1097,79 @@ void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, d
   count_launch();
 }
 
+template <int S, int BK>
+static void grouped_attribute() {
+  static PerDeviceOnce flag;
+  once_per_device(flag, [] {
+    return cudaFuncSetAttribute(tc_gemm_grouped_kernel<S, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                GroupedCfg<S, BK>::kSmem) == cudaSuccess;
+  });
+}
+
+template <int S, int BK>
+static void grouped_launch(cudaStream_t s, const TcMaps& maps, int M, int N, int K, double alpha, double* C, int ldc,
+                           int sym, int beta, int* err, const int* gate, int kt_split, int z, long long zstride) {
+  grouped_attribute<S, BK>();
+  dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, z);
+  tc_gemm_grouped_kernel<S, BK><<<grid, kThreads, GroupedCfg<S, BK>::kSmem, s>>>(
+      maps, M, N, K, alpha, C, ldc, sym, beta, err, gate, kt_split, zstride);
+  count_launch();
+}
+
 void tc_gemm_grouped(cudaStream_t s, const TcWork& w, int slotA, int slotB, double alpha, double* C, int sym,
                      const int* gate) {
   TcBuffers* tb = (TcBuffers*)w.base;
-  static PerDeviceOnce flag;
-  once_per_device(flag, [] {
-    return cudaFuncSetAttribute(tc_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemBytes) ==
-           cudaSuccess;
-  });
   TcMaps maps;
   for (int k = 0; k < kTcMaxSlices; ++k) {
     maps.a[k] = tb->map[slotA][k];
     maps.b[k] = tb->map[slotB][k];
   }
   const int n = tb->n;
-  dim3 grid((n + kBN - 1) / kBN, (n + kBM - 1) / kBM);
-  tc_gemm_grouped_kernel<<<grid, kThreads, kGSmemBytes, s>>>(maps, n, alpha, C, n, sym, tb->err, gate);
-  count_launch();
+  grouped_launch<3, 64>(s, maps, n, n, n, alpha, C, n, sym, 0, tb->err, gate, 0, 1, 0);
+}
+
+void tc_gemm_grouped4(cudaStream_t s, const TcWork& w, int slotA, int slotB, double alpha, double* C, int sym,
+                      const int* gate) {
+  TcBuffers* tb = (TcBuffers*)w.base;
+  TcMaps maps;
+  for (int k = 0; k < kTcMaxSlices; ++k) {
+    maps.a[k] = tb->map64[slotA][k];
+    maps.b[k] = tb->map64[slotB][k];
+  }
+  const int n = tb->n;
+  grouped_launch<4, 32>(s, maps, n, n, n, alpha, C, n, sym, 0, tb->err, gate, 0, 1, 0);
+}
+
+static bool grouped_rc_maps(TcMaps* maps, int M, int N, int K, const __nv_bfloat16* Abase, int lda, size_t astride,
+                            const __nv_bfloat16* Bbase, int ldb, size_t bstride) {
+  for (int a = 0; a < kTcMaxSlices; ++a) {
+    if (!make_map_rc_box(&maps->a[a], (void*)(Abase + a * astride), M, K, lda, 32)) return false;
+    if (!make_map_rc_box(&maps->b[a], (void*)(Bbase + a * bstride), N, K, ldb, 32)) return false;
+  }
+  return true;
+}
+
+int tc_gemm_grouped_rc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, int lda, size_t astride,
+                       const __nv_bfloat16* Bbase, int ldb, size_t bstride, double alpha, double* C, int ldc,
+                       int beta, int* err) {
+  TcMaps maps;
+  if (!grouped_rc_maps(&maps, M, N, K, Abase, lda, astride, Bbase, ldb, bstride)) return -1;
+  grouped_launch<4, 32>(s, maps, M, N, K, alpha, C, ldc, 0, beta, err, nullptr, 0, 1, 0);
+  return 0;
+}
+
+int tc_gemm_grouped_rc_splitk(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, int lda,
+                              size_t astride, const __nv_bfloat16* Bbase, int ldb, size_t bstride, double alpha,
+                              double* P, int ldp, int splits, int* err) {
+  TcMaps maps;
+  if (!grouped_rc_maps(&maps, M, N, K, Abase, lda, astride, Bbase, ldb, bstride)) return -1;
+  constexpr int kCh = GroupedCfg<4, 32>::kChunkTiles;
+  const int ktiles = (K + 31) / 32;
+  int per = (ktiles + splits - 1) / splits;
+  per = ((per + kCh - 1) / kCh) * kCh;                   // whole exact-sum chunks
+  const int z = (ktiles + per - 1) / per;
+  grouped_launch<4, 32>(s, maps, M, N, K, alpha, P, ldp, 0, 0, err, nullptr, per, z, (long long)M * ldp);
+  return z;
 }
 
 int tc_ld(int n) { return ld_for(n); }

@@ -34,6 +34,18 @@ void tc_gemm(cudaStream_t s, const TcWork& w, int slotA, int slotB, int terms, d
 // in FP32; within 2^-26 of sum |a||b| of the exact 6-term slice product
 void tc_gemm_grouped(cudaStream_t s, const TcWork& w, int slotA, int slotB, double alpha, double* C, int sym,
                      const int* gate = nullptr);
+// the 4-slice product (terms 10) the same way (density product): within ~2^-28 of
+// sum |a||b| of the exact 10-term slice product
+void tc_gemm_grouped4(cudaStream_t s, const TcWork& w, int slotA, int slotB, double alpha, double* C, int sym,
+                      const int* gate = nullptr);
+// general shapes with 4 slices (back-transformation); the same operands and
+// partial-product layout as tc_gemm_rc / tc_gemm_rc_splitk; < 0 on a tensor-map error
+int tc_gemm_grouped_rc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, int lda, size_t astride,
+                       const __nv_bfloat16* Bbase, int ldb, size_t bstride, double alpha, double* C, int ldc,
+                       int beta, int* err);
+int tc_gemm_grouped_rc_splitk(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Abase, int lda,
+                              size_t astride, const __nv_bfloat16* Bbase, int ldb, size_t bstride, double alpha,
+                              double* P, int ldp, int splits, int* err);
 
 // Building blocks on caller-provided buffers (used by the allocation-free entry point)
 int tc_ld(int n);                                                   // padded slice row length

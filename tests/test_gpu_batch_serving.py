@@ -187,6 +187,34 @@ def test_server_trajectory_matches_oracle():
     assert max_abs([x["E_tot"] for x in r["records"]], E) < 1e-7
 
 
+def test_whole_batch_graph_with_several_groups_equals_individual_steps():
+    """Three 600-atom carbon packings (n = 2400): each persistent eigensolver
+    grid takes one block on each of the 152 SMs (at most two such blocks fit
+    on an SM), so the three do not fit on the device at once and the batch
+    graph runs them as at least two groups one after the other (fork/join
+    across groups); results bitwise equal to stepping each alone."""
+    mols = [synth.carbon_packing(seed=40 + i, natoms=600) for i in range(3)]
+    cfg = _cfg(precision=kx.SIM_PREC_MIXED, Te=3000.0)
+    Vs = [synth.maxwell_boltzmann(m.Z, 300.0, seed=60 + i) for i, m in enumerate(mols)]
+    P0s = [0.5 * np.eye(4 * m.natoms) for m in mols]
+    hs_b = [kx.sim_create(cfg, _table(), m.Z, m.R, V=v, P0=p) for m, v, p in zip(mols, Vs, P0s)]
+    hs_i = [kx.sim_create(cfg, _table(), m.Z, m.R, V=v, P0=p) for m, v, p in zip(mols, Vs, P0s)]
+    b = kx.sim_batch_create(hs_b)
+    try:
+        assert kx.sim_batch_groups(b) >= 2
+        kx.sim_batch_run(b, 3)
+        for h in hs_i:
+            kx.sim_step(h, 3)
+        for m, hb, hi in zip(mols, hs_b, hs_i):
+            assert kx.sim_records(hb, 3) == kx.sim_records(hi, 3)
+            for a, c in zip(_state(hb, m.natoms), _state(hi, m.natoms)):
+                assert np.array_equal(a, c)
+    finally:
+        kx.sim_batch_destroy(b)
+        for h in hs_b + hs_i:
+            kx.sim_destroy(h)
+
+
 def test_whole_batch_graph_equals_individual_steps():
     """One CUDA graph per batch step (every molecule a branch): records and
     states bitwise equal to stepping each molecule alone, across the X ring."""

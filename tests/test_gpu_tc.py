@@ -91,7 +91,7 @@ def test_grouped_product_is_the_three_slice_product(n, sym):
     rng = np.random.default_rng(n + 7 * sym)
     A = rng.normal(size=(n, n)) * np.exp(rng.normal(size=(n, 1)))
     B = A if sym else rng.normal(size=(n, n))
-    C = kx.sim_debug_tc_gemm_grouped(A, B, sym=sym)
+    C = kx.sim_debug_tc_gemm_grouped(A, B, sym=sym, slices=3)
     pa, pb = slices(A, 3), slices(B, 3)
     ref = sum(pa[i] @ pb[j].T for i, j in kept_pairs(3))
     scale = np.abs(A) @ np.abs(B).T
@@ -99,5 +99,40 @@ def test_grouped_product_is_the_three_slice_product(n, sym):
     err_exact = np.max(np.abs(C - A @ B.T) / scale)
     assert err_slices < 2.0 ** -24, err_slices
     assert err_exact < 2.0 ** -20, err_exact
+    print(f"\nn {n} sym {sym}: 3-slice grouped vs slice product {np.log2(err_slices):.1f}, "
+          f"vs FP64 product {np.log2(err_exact):.1f}")
     if sym:
         assert np.array_equal(C, C.T)
+
+
+@pytest.mark.parametrize("n", [64, 128, 200, 333, 700, 1100])
+@pytest.mark.parametrize("sym", [False, True])
+def test_grouped_product_is_the_four_slice_product(n, sym):
+    """The 4-slice grouped kernel (density product, back-transformation): the
+    exact 10-term slice product to within 2^-24 of sum |a||b| and the FP64
+    product likewise.  The bound is set by the tensor core's FP32
+    accumulation of the lower-weight group over a 512-K chunk (measured up to
+    ~2^-25.6 at n = 333), far above the 4-slice truncation (~2^-32) but far
+    below the density bar of the path."""
+    rng = np.random.default_rng(3 * n + sym)
+    A = rng.normal(size=(n, n)) * np.exp(rng.normal(size=(n, 1)))
+    B = A if sym else rng.normal(size=(n, n))
+    C = kx.sim_debug_tc_gemm_grouped(A, B, sym=sym, slices=4)
+    pa, pb = slices(A, 4), slices(B, 4)
+    ref = sum(pa[i] @ pb[j].T for i, j in kept_pairs(4))
+    scale = np.abs(A) @ np.abs(B).T
+    err_slices = np.max(np.abs(C - ref) / scale)
+    err_exact = np.max(np.abs(C - A @ B.T) / scale)
+    assert err_slices < 2.0 ** -24, err_slices
+    assert err_exact < 2.0 ** -24, err_exact
+    print(f"\nn {n} sym {sym}: 4-slice grouped vs slice product {np.log2(err_slices):.1f} (log2 of the max "
+          f"relative error), vs FP64 product {np.log2(err_exact):.1f}")
+    if sym:
+        assert np.array_equal(C, C.T)
+
+
+def test_grouped_product_rejects_other_slice_counts():
+    A = np.eye(64)
+    with pytest.raises(kx.SimError) as e:
+        kx.sim_debug_tc_gemm_grouped(A, A, slices=2)
+    assert e.value.code == kx.SIM_EINVAL
