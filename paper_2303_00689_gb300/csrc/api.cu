@@ -68,6 +68,12 @@ struct sim_handle {
   int dev = 0, sms = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // side stream for work that does not feed the next kernels of the step:
+  // the Fermi occupations (during inverse iteration and back-transformation)
+  // and energy, forces and dipole (during the Krylov kernel); forked from and
+  // joined to `stream` by events, so graph capture records both branches
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev[2] = {}, join_ev[2] = {};
   sim_config cfg;
   ElemTable tab;
   int N = 0, n = 0, npair = 0, nocc = 0, mmax = 0;
@@ -91,6 +97,7 @@ struct sim_handle {
   double* Vk[16] = {};
   double* Wk[16] = {};
   double *red = nullptr, *coef = nullptr;
+  double* red2 = nullptr;           // reduction workspace of the side stream (energy)
   Scalars* sc = nullptr;
   sim_step_result* rec = nullptr;   // device per-step records (ring of kRecCap)
   int* rec_idx = nullptr;           // device: index of the next record in rec[]
@@ -276,7 +283,23 @@ static void dmpt(sim_handle* h, const double* F1, double* D1) {
   dgemm(s, 0, 1, n, n, n, 1.0, h->T1, n, h->Q, n, 0.0, D1, n, 1, g);         // D1 = T1 Q^T
 }
 
-static int eig(sim_handle* h) {
+// fork k: work issued on h->side after this point follows everything issued
+// on h->stream so far; join k: h->stream waits for the side work issued since
+static void fork_side(sim_handle* h, int k) {
+  cudaEventRecord(h->fork_ev[k], h->stream);
+  cudaStreamWaitEvent(h->side, h->fork_ev[k], 0);
+}
+static void join_side(sim_handle* h, int k) {
+  cudaEventRecord(h->join_ev[k], h->side);
+  cudaStreamWaitEvent(h->stream, h->join_ev[k], 0);
+}
+// side work only outside phase profiling (whose events time the main stream)
+static bool concurrent(const sim_handle* h) { return h->side && !h->prof; }
+
+// eigenpairs of the Fock matrix; with fermi_side, the Fermi occupations and
+// mu (eq. 8; they need the eigenvalues only) run on the side stream while the
+// eigenvectors are formed, and the caller joins before the density
+static int eig(sim_handle* h, bool fermi_side = false) {
   phase_begin(h, PH_TRIDIAG);
   int st = eig_tridiagonalize(h->stream, h->n, h->Fock, h->ew, &h->sc->status, h->sms, mixed(h));
   phase_end(h);
@@ -284,6 +307,10 @@ static int eig(sim_handle* h) {
   phase_begin(h, PH_BISECT);
   eig_bisect(h->stream, h->n, h->eps, h->ew, 1e-12, mixed(h));
   phase_end(h);
+  if (fermi_side) {
+    fork_side(h, 0);
+    launch_fermi(h->side, h->n, h->eps, (double)h->nocc, h->beta, h->f, h->sc);
+  }
   phase_begin(h, PH_TRIEIG);
   eig_vectors(h->stream, h->n, h->eps, h->Q, h->ew, mixed(h));
   phase_end(h);
@@ -351,19 +378,33 @@ static int evaluate(sim_handle* h, bool krylov = true, bool pairs_ready = false)
   launch_pack_diag(s, m, X, h->Pd);
   launch_build_fock(s, m, pd, h->tab, X, h->Pd, h->h, h->Fock);
   phase_end(h);
-  int rc = eig(h);
-  if (rc) return rc;
+  const bool conc = concurrent(h);
+  int rc = eig(h, conc);
+  if (rc) {
+    if (conc) join_side(h, 0);
+    return rc;
+  }
   phase_begin(h, PH_DENSITY);
-  launch_fermi(s, n, h->eps, (double)h->nocc, h->beta, h->f, h->sc);
+  if (conc)
+    join_side(h, 0);
+  else
+    launch_fermi(s, n, h->eps, (double)h->nocc, h->beta, h->f, h->sc);
   density(h);
   phase_end(h);
+  // energy, forces and dipole read D0 and write nothing the Krylov kernel
+  // reads: side stream, own reduction workspace
+  cudaStream_t fs = conc ? h->side : s;
+  if (conc) fork_side(h, 1);
   phase_begin(h, PH_FORCES);
-  launch_energy(s, n, h->npair, h->h, h->D, X, h->Fock, h->E, h->sc, h->red);
-  launch_pack_diag(s, m, h->D, h->Dd);
-  launch_forces(s, m, pd, h->tab, h->D, X, h->Dd, h->Pd, h->g, h->F);
-  launch_dipole(s, m, h->tab, h->R, h->Dd, h->sc);
+  launch_energy(fs, n, h->npair, h->h, h->D, X, h->Fock, h->E, h->sc, h->red2);
+  launch_pack_diag(fs, m, h->D, h->Dd);
+  launch_forces(fs, m, pd, h->tab, h->D, X, h->Dd, h->Pd, h->g, h->F);
+  launch_dipole(fs, m, h->tab, h->R, h->Dd, h->sc);
   phase_end(h);
-  if (!krylov) return SIM_OK;
+  if (!krylov) {
+    if (conc) join_side(h, 1);
+    return SIM_OK;
+  }
   if (h->cfg.kernel == SIM_KERNEL_XL) {
     phase_begin(h, PH_KRY_BLAS);
     launch_scaled_residual(s, nn, h->D, X, h->cfg.xl_c, h->W0, h->K, h->sc, h->red);   // -c (D0 - X)
@@ -371,6 +412,7 @@ static int evaluate(sim_handle* h, bool krylov = true, bool pairs_ready = false)
   } else {
     krylov_kernel(h, X);   // K (D0 - X), eqs. 31-34
   }
+  if (conc) join_side(h, 1);
   phase_begin(h, PH_KRY_BLAS);
   launch_check_finite(s, (size_t)3 * h->N, h->F, h->sc);
   launch_check_finite(s, nn, h->K, h->sc);
@@ -614,6 +656,7 @@ static void layout(sim_handle* h, Arena& a) {
   h->Pd = a.take<double>(10 * (size_t)h->N);
   h->Vd = a.take<double>(10 * (size_t)h->N);
   h->red = a.take<double>(kReduceWorkDoubles);
+  h->red2 = a.take<double>(kReduceWorkDoubles);
   h->coef = a.take<double>(64);
   h->sc = a.take<Scalars>(1);
   h->rec = a.take<sim_step_result>(kRecCap);
@@ -813,6 +856,17 @@ int sim_create(const sim_config* cfg, const sim_param_table* table, int natoms, 
     }
     h->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    h->side = nullptr;
+  }
+  for (int k = 0; k < 2 && h->side; ++k)
+    if (cudaEventCreateWithFlags(&h->fork_ev[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      sim_destroy(h);
+      return fail(SIM_EINTERNAL, "event creation failed");
+    }
   Arena sizing{nullptr, 0, 0};
   layout(h, sizing);
   h->arena_bytes = sizing.off + 256;
@@ -1444,6 +1498,14 @@ void sim_destroy(sim_handle* h) {
   if (h->arena) {
     cudaFreeAsync(h->arena, h->stream);
     cudaStreamSynchronize(h->stream);
+  }
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (h->fork_ev[k]) cudaEventDestroy(h->fork_ev[k]);
+    if (h->join_ev[k]) cudaEventDestroy(h->join_ev[k]);
   }
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
