@@ -54,6 +54,20 @@ __host__ __device__ __forceinline__ dfl df_from_double(double x) {
   return dfl{hi, lo};
 }
 __host__ __device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
+// FP32 -> FP64 by integer operations (exact for normal numbers; subnormal FP32
+// values, below 2^-126, become zero; infinities and NaN take the conversion
+// instruction): keeps the conversion off GB300's narrow FP64 pipe
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xFFu;
+  if (ex == 0xFFu) return (double)f;
+  unsigned long long b = (unsigned long long)(u & 0x80000000u) << 32;
+  if (ex != 0) b |= ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+// hi + lo as a double with one FP64 addition (the two conversions by integer operations)
+__device__ __forceinline__ double df_to_double_fast(dfl a) { return f2d_int(a.hi) + f2d_int(a.lo); }
 __host__ __device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.hi, -a.lo}; }
 
 // a + b; absolute error of order 2^-48 (|a| + |b|)

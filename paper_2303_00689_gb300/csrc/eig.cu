@@ -552,14 +552,16 @@ __global__ void __launch_bounds__(kTriThreadsDf) tridiag_df_kernel(int n, dfl* _
 // Gershgorin interval, squared off-diagonals, pivmin; one block
 __global__ void gersh_kernel(int n, const double* __restrict__ d, const double* __restrict__ e,
                              double* __restrict__ e2, double* __restrict__ scal, float* __restrict__ df,
-                             float* __restrict__ e2f, dfl* __restrict__ d_dfl, dfl* __restrict__ e2_dfl) {
+                             float* __restrict__ e2f, dfl* __restrict__ d_dfl, dfl* __restrict__ e2_dfl,
+                             dfl* __restrict__ e_dfl) {
   double lo = 1e300, hi = -1e300, em = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double r = 0.0;
     df[i] = (float)d[i];                 // FP32 copies for the coarse phase (no per-step conversions)
     e2f[i] = 0.0f;
-    d_dfl[i] = df_from_double(d[i]);     // double-float copies for the multisection (mixed path)
-    e2_dfl[i] = dfl{0.0f, 0.0f};
+    d_dfl[i] = df_from_double(d[i]);     // double-float copies for the multisection and the
+    e2_dfl[i] = dfl{0.0f, 0.0f};         // inverse iteration (mixed path)
+    e_dfl[i] = (i < n - 1) ? df_from_double(e[i]) : dfl{0.0f, 0.0f};
     if (i > 0) r += fabs(e[i - 1]);
     if (i < n - 1) {
       r += fabs(e[i]);
@@ -749,10 +751,18 @@ __global__ void cluster_kernel(int n, const double* __restrict__ ev, const doubl
   clus[i] = (i == 0 || !(ev[i] - ev[i - 1] <= ctol)) ? 1 : 0;
 }
 
-__device__ __forceinline__ double start_value(int row, int col) {
+__device__ __forceinline__ unsigned start_hash(int row, int col) {
   unsigned h = (unsigned)row * 0x9E3779B1u ^ ((unsigned)col * 0x85EBCA77u + 0x165667B1u);
   h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
-  return ((double)(h & 0xFFFFF) / 524288.0) - 1.0 + 1e-3;
+  return h;
+}
+__device__ __forceinline__ double start_value(int row, int col) {
+  return ((double)(start_hash(row, col) & 0xFFFFF) / 524288.0) - 1.0 + 1e-3;
+}
+// the same pseudo-random start entry in FP32 arithmetic (a start vector only
+// needs a component along the eigenvector, not FP64 values)
+__device__ __forceinline__ float start_value_f(int row, int col) {
+  return __fadd_rn(__fmul_rn((float)(start_hash(row, col) & 0xFFFFF), 0x1p-19f), -0.999f);
 }
 
 // inverse iteration; one thread per cluster leader; lu: 5 x n x n workspace.
@@ -916,6 +926,7 @@ __device__ __forceinline__ float df_abs_hi(dfl a) { return fabsf(a.hi); }
 // every access a whole 32-byte sector and limit divergence at the pivots.
 constexpr int kIvLanes = 4;
 __global__ void __launch_bounds__(32) invit_df_kernel(int n, const dfl* __restrict__ d, const double* __restrict__ e,
+                                                    const dfl* __restrict__ edf,
                                                     const double* __restrict__ ev, const double* __restrict__ scal,
                                                     const int* __restrict__ clus, dfl* __restrict__ lu,
                                                     double* __restrict__ Zout) {
@@ -943,12 +954,14 @@ __global__ void __launch_bounds__(32) invit_df_kernel(int n, const dfl* __restri
     // step 2 reads x scaled by 1/max (inverse iteration is linear, the scale
     // only keeps the values in range), its backward sweep accumulates ||x||^2;
     // one last pass writes x / ||x|| in FP64.  Six sweeps of n instead of 15.
+    // no FP64 instruction per row: GB300 issues one FP64 warp instruction per
+    // ~76 cycles per scheduler, which would put the FP64 pipe on the chain
     const dfl lam = df_from_double(ev[L]);
-    dfl a = df_sub(ldg_df(d), lam), u = df_from_double(e[0]);
+    dfl a = df_sub(ldg_df(d), lam), u = ldg_df(edf);
     for (int r = 0; r < n - 1; ++r) {
-      const dfl b = df_from_double(e[r]);
+      const dfl b = ldg_df(edf + r);
       const dfl dn = df_sub(ldg_df(d + r + 1), lam);
-      const dfl un = (r < n - 2) ? df_from_double(e[r + 1]) : dfl{0.0f, 0.0f};
+      const dfl un = (r < n - 2) ? ldg_df(edf + r + 1) : dfl{0.0f, 0.0f};
       if (df_abs_hi(a) >= df_abs_hi(b)) {
         LU(pv, r) = 0;
         if (df_abs_hi(a) < tiny.hi) a = (a.hi >= 0.0f) ? tiny : df_neg(tiny);
@@ -983,7 +996,7 @@ __global__ void __launch_bounds__(32) invit_df_kernel(int n, const dfl* __restri
     dfl nrm = {0.0f, 0.0f};
     for (int it = 0; it < 2; ++it) {
       // forward (L with pivots); step 1 takes the start vector, step 2 the scaled x
-      dfl cur = (it == 0) ? df_from_double(start_value(0, L)) : df_mul(ZC(0, L), scl);
+      dfl cur = (it == 0) ? dfl{start_value_f(0, L), 0.0f} : df_mul(ZC(0, L), scl);
       for (int r0 = 0; r0 < n - 1; r0 += kIvB) {
         dfl nx[kIvB], fv[kIvB];
         int pf[kIvB];
@@ -991,7 +1004,7 @@ __global__ void __launch_bounds__(32) invit_df_kernel(int n, const dfl* __restri
         for (int q = 0; q < kIvB; ++q) {
           const int r = r0 + q;
           if (r < n - 1) {
-            nx[q] = (it == 0) ? df_from_double(start_value(r + 1, L)) : df_mul(ZC(r + 1, L), scl);
+            nx[q] = (it == 0) ? dfl{start_value_f(r + 1, L), 0.0f} : df_mul(ZC(r + 1, L), scl);
             fv[q] = LU(dl, r);
             pf[q] = LU(pv, r);
           }
@@ -1050,7 +1063,7 @@ __global__ void __launch_bounds__(32) invit_df_kernel(int n, const dfl* __restri
 #pragma unroll 8
     for (int r = 0; r < n; ++r) {
       const dfl z = df_mul(ZC(r, L), sc);
-      Zout[(size_t)r * n + L] = df_to_double(z);
+      Zout[(size_t)r * n + L] = df_to_double_fast(z);
     }
     return;
   }
@@ -1259,7 +1272,7 @@ static size_t eig_layout(int n, void* base, EigWork* w) {
   double* e = take(n);
   double* e2 = take(n);
   double* tau = take(n);
-  double* pbuf = take(3 * (size_t)n);
+  double* pbuf = take(4 * (size_t)n);
   double* lu = take(lu_doubles(n));
   double* Tm = take((size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc);   // T and Gram of every reflector block
   double* Gm = take((size_t)tc_blocks(n) * kBtBlockTc * kBtBlockTc);
@@ -1379,12 +1392,13 @@ int eig_tridiagonalize(cudaStream_t s, int n, const double* F, EigWork& w, int* 
 void eig_bisect(cudaStream_t s, int n, double* eps, EigWork& w, double rel_tol, bool df_path) {
   if (n <= 0) return;
   // 2. eigenvalues
-  // pbuf (3n doubles, free after the tridiagonalisation) holds the FP32 and double-float copies
+  // pbuf (4n doubles, free after the tridiagonalisation) holds the FP32 and double-float copies
   float* df = (float*)w.pbuf;
   float* e2f = df + n;
   dfl* d_dfl = (dfl*)(w.pbuf + n);
   dfl* e2_dfl = d_dfl + n;
-  gersh_kernel<<<1, 1024, 0, s>>>(n, w.d, w.e, w.e2, w.scal, df, e2f, d_dfl, e2_dfl);
+  dfl* e_dfl = e2_dfl + n;
+  gersh_kernel<<<1, 1024, 0, s>>>(n, w.d, w.e, w.e2, w.scal, df, e2f, d_dfl, e2_dfl, e_dfl);
   count_launch();
   if (df_path) {
     const long long thr = (long long)n * kMsLanes;
@@ -1403,7 +1417,9 @@ void eig_vectors(cudaStream_t s, int n, const double* eps, double* Q, EigWork& w
   count_launch();
   if (df_path) {
     const dfl* d_dfl = (const dfl*)(w.pbuf + n);     // written by eig_bisect
-    invit_df_kernel<<<(n + kIvLanes - 1) / kIvLanes, 32, 0, s>>>(n, d_dfl, w.e, eps, w.scal, w.clus, (dfl*)w.lu, Q);
+    const dfl* e_dfl = d_dfl + 2 * (size_t)n;
+    invit_df_kernel<<<(n + kIvLanes - 1) / kIvLanes, 32, 0, s>>>(n, d_dfl, w.e, e_dfl, eps, w.scal, w.clus,
+                                                                (dfl*)w.lu, Q);
   } else {
     invit_kernel<<<(n + 31) / 32, 32, 0, s>>>(n, w.d, w.e, eps, w.scal, w.clus, w.lu, Q);
   }

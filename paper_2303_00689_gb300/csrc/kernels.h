@@ -56,7 +56,7 @@ struct EigWork {
   double *A;            // n x n copy of the input (overwritten)
   double *Vst;          // n x n Householder vectors (row k = v_k)
   double *d, *e, *e2, *tau;
-  double *pbuf;         // 3 x n
+  double *pbuf;         // 4 x n
   double *lu;           // 5 x n x n inverse-iteration workspace
   double *Tm, *Gm, *Wt, *Wt2;  // back-transform panels
   unsigned* bar;        // 2 words grid barrier

@@ -208,7 +208,7 @@ __device__ __forceinline__ G3 g3_of(const D3& a) {
   return G3{df_from_double(a.v), {df_from_double(a.d0), df_from_double(a.d1), df_from_double(a.d2)}};
 }
 __device__ __forceinline__ D3 d3_of(const G3& a) {
-  return D3{df_to_double(a.v), df_to_double(a.d[0]), df_to_double(a.d[1]), df_to_double(a.d[2])};
+  return D3{df_to_double_fast(a.v), df_to_double_fast(a.d[0]), df_to_double_fast(a.d[1]), df_to_double_fast(a.d[2])};
 }
 __device__ __forceinline__ G3 g3_mul(const G3& a, const G3& b) {
   G3 r;
@@ -338,8 +338,20 @@ __device__ G1 local_integral_df(int p, int qd, const ChargeDF& ca, const ChargeD
 
 // W = C I C^T in double-float from the local integrals as radial duals
 // (value, d/dR): promoted by d/dd_k = u_k d/dR, rotated, written as D3
+// the products of one group (ss, sp, pp) and the group of product p
+__device__ __forceinline__ int grp_of(int p) { return p == 0 ? 0 : (p < 4 ? 1 : 2); }
+__device__ __forceinline__ int grp_lo(int g) { return g == 0 ? 0 : (g == 1 ? 1 : 4); }
+__device__ __forceinline__ int grp_hi(int g) { return g == 0 ? 1 : (g == 1 ? 4 : 10); }
+
+// W = C I C^T in double-float from the local integrals as radial duals
+// (value, d/dR), written straight to the pair's output columns (W[(p*10+q)*np],
+// dW[(k*100 + p*10+q)*np]).  The molecular-frame derivatives of I are u_k dI/dR,
+// so X = I C^T needs no promoted copy of I:
+//   X.v = sum I.v C.v,   X.d_k = sum I.v C.d_k + u_k sum I.d C.v;
+// C is kept block by block (at most 6 products per row) and X one product
+// group at a time, which keeps the per-thread arrays small.
 __device__ void rotate_blocks_df(const G1 (&Ir)[10][10], const D3 (&Tf)[4][4], const double* uv, int pa, int pb,
-                                 D3* Wout) {
+                                 double* __restrict__ W, double* __restrict__ dW, size_t np, int t) {
   G3 Tg[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -351,47 +363,73 @@ __device__ void rotate_blocks_df(const G1 (&Ir)[10][10], const D3 (&Tf)[4][4], c
 #pragma unroll
     for (int b = 1; b < 4; ++b) Tg[a][b] = g3_of(Tf[a][b]);
   const dfl ug[3] = {df_from_double(uv[0]), df_from_double(uv[1]), df_from_double(uv[2])};
-  G3 I[10][10];
-  for (int p = 0; p < 10; ++p)
-    for (int q = 0; q < 10; ++q) {
-      I[p][q] = g3_zero();
-      if (p < pa && q < pb && c_prod_cls[p] == c_prod_cls[q]) {
-        I[p][q].v = Ir[p][q].v;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) I[p][q].d[k] = df_mul(Ir[p][q].d, ug[k]);
-      }
-    }
-  G3 C[10][10];
+  // C[p][pp] for pp in the group of p, at Cb[p][pp - grp_lo]
+  G3 Cb[10][6];
   for (int p = 0; p < 10; ++p) {
     const int mu = c_prod_mu[p], nu = c_prod_nu[p];
-    for (int pp = c_grp_lo[p]; pp < c_grp_hi[p]; ++pp) {
+    const int g = grp_of(p), lo = grp_lo(g);
+    for (int pp = lo; pp < grp_hi(g); ++pp) {
       const int m2 = c_prod_mu[pp], n2 = c_prod_nu[pp];
       if (m2 == n2)
-        C[p][pp] = g3_mul(Tg[mu][m2], Tg[nu][m2]);
+        Cb[p][pp - lo] = g3_mul(Tg[mu][m2], Tg[nu][m2]);
       else
-        C[p][pp] = g3_add(g3_mul(Tg[mu][m2], Tg[nu][n2]), g3_mul(Tg[mu][n2], Tg[nu][m2]));
+        Cb[p][pp - lo] = g3_add(g3_mul(Tg[mu][m2], Tg[nu][n2]), g3_mul(Tg[mu][n2], Tg[nu][m2]));
     }
   }
-  G3 X[10][10];
-  for (int pp = 0; pp < pa; ++pp)
-    for (int q = 0; q < pb; ++q) {
-      G3 acc = g3_zero();
-      for (int qq = c_grp_lo[q]; qq < c_grp_hi[q]; ++qq)
-        if (c_prod_cls[qq] == c_prod_cls[pp]) g3_acc_mul(acc, I[pp][qq], C[q][qq]);
-      X[pp][q] = g3_norm(acc);
-    }
-  for (int p = 0; p < 10; ++p)
+  const int ngrp = (pa == 10) ? 3 : 1;
+  for (int g = 0; g < ngrp; ++g) {
+    const int lo = grp_lo(g), hi = grp_hi(g);
+    G3 Xg[6][10];                       // X[pp][q] for pp in group g
+    for (int pp = lo; pp < hi; ++pp)
+      for (int q = 0; q < pb; ++q) {
+        G3 acc = g3_zero();
+        dfl sd = {0.0f, 0.0f};
+        const int gq = grp_of(q), qlo = grp_lo(gq);
+        for (int qq = qlo; qq < grp_hi(gq); ++qq) {
+          if (c_prod_cls[qq] != c_prod_cls[pp]) continue;          // I = 0 between classes
+          const G1& iv = Ir[pp][qq];
+          const G3& c = Cb[q][qq - qlo];
+          df_acc_mul(acc.v, iv.v, c.v);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) df_acc_mul(acc.d[k], iv.v, c.d[k]);
+          df_acc_mul(sd, iv.d, c.v);
+        }
+        sd = df_norm(sd);
+        G3 x = g3_norm(acc);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x.d[k] = df_add(x.d[k], df_mul(ug[k], sd));
+        Xg[pp - lo][q] = x;
+      }
+    for (int p = lo; p < hi; ++p)
+      for (int q = 0; q < 10; ++q) {
+        G3 acc = g3_zero();
+        if (q < pb)
+          for (int pp = lo; pp < hi; ++pp) g3_acc_mul(acc, Cb[p][pp - lo], Xg[pp - lo][q]);
+        const D3 w = d3_of(g3_norm(acc));
+        const size_t ix = (size_t)(p * 10 + q) * np + t;
+        W[ix] = w.v;
+        dW[ix] = w.d0;
+        dW[100 * np + ix] = w.d1;
+        dW[200 * np + ix] = w.d2;
+      }
+  }
+  // products the partner's group structure leaves out (hydrogen on A: p >= 1)
+  for (int p = (ngrp == 1 ? 1 : 10); p < 10; ++p)
     for (int q = 0; q < 10; ++q) {
-      G3 acc = g3_zero();
-      if (p < pa && q < pb)
-        for (int pp = c_grp_lo[p]; pp < c_grp_hi[p]; ++pp) g3_acc_mul(acc, C[p][pp], X[pp][q]);
-      Wout[p * 10 + q] = d3_of(g3_norm(acc));
+      const size_t ix = (size_t)(p * 10 + q) * np + t;
+      W[ix] = 0.0;
+      dW[ix] = 0.0;
+      dW[100 * np + ix] = 0.0;
+      dW[200 * np + ix] = 0.0;
     }
 }
 
+// DFROT (dual numbers only): W and dW go straight to Wg / dWg (column t of
+// stride np) and Wout is not used
 template <bool DFROT, typename T>
 __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T* Wout /*100*/,
-                           T* Sout /*16*/, T* Eout) {
+                           T* Sout /*16*/, T* Eout, double* Wg = nullptr, double* dWg = nullptr, size_t np = 0,
+                           int t = 0) {
   typedef typename Radial<T>::type Tr;
   T d[3];
   for (int k = 0; k < 3; ++k) d[k] = seed<T>(dvec[k], k);
@@ -452,7 +490,7 @@ __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T
       }
       if (pb == 10) Ig[7][7] = g1_half(g1_sub(Ig[4][4], Ig[4][5]));
     }
-    rotate_blocks_df(Ig, Tf, uv, pa, pb, Wout);
+    rotate_blocks_df(Ig, Tf, uv, pa, pb, Wg, dWg, np, t);
   } else {
   Tr Ir[10][10];
   for (int p = 0; p < 10; ++p)
@@ -581,14 +619,19 @@ __global__ void pair_derivs_kernel(int npair, const int* __restrict__ pA, const 
   double d[3] = {R[3 * B] - R[3 * A], R[3 * B + 1] - R[3 * A + 1], R[3 * B + 2] - R[3 * A + 2]};
   const Elem& ea = tab.e[elem[A]];
   const Elem& eb = tab.e[elem[B]];
-  D3 w[100], s[16], e;
-  pair_block<DFROT, D3>(d, ea, eb, w, s, &e);
   size_t np = (size_t)npair;
-  for (int k = 0; k < 100; ++k) {
-    W[k * np + t] = w[k].v;
-    dW[(0 * 100 + k) * np + t] = w[k].d0;
-    dW[(1 * 100 + k) * np + t] = w[k].d1;
-    dW[(2 * 100 + k) * np + t] = w[k].d2;
+  D3 s[16], e;
+  if constexpr (DFROT) {
+    pair_block<true, D3>(d, ea, eb, nullptr, s, &e, W, dW, np, t);
+  } else {
+    D3 w[100];
+    pair_block<false, D3>(d, ea, eb, w, s, &e);
+    for (int k = 0; k < 100; ++k) {
+      W[k * np + t] = w[k].v;
+      dW[(0 * 100 + k) * np + t] = w[k].d0;
+      dW[(1 * 100 + k) * np + t] = w[k].d1;
+      dW[(2 * 100 + k) * np + t] = w[k].d2;
+    }
   }
   for (int k = 0; k < 16; ++k) {
     S[k * np + t] = s[k].v;
