@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(kTriThreadsDf) tridiag_df_kernel(int n, dfl* _
     for (int j = k + 1 + tid; j < n; j += T) {
       const dfl v = (j == k + 1) ? dfl{1.0f, 0.0f} : df_mul(VC[j], scale_df);
       VC[j] = v;
-      if (j % G == (int)blockIdx.x) Vst[(size_t)k * n + j] = df_to_double(v);
+      if (j % G == (int)blockIdx.x) Vst[(size_t)k * n + j] = df_to_double_fast(v);
     }
     if (!grid_wait(bar, (unsigned)(k + 1) * (unsigned)G, status)) return;
   }
@@ -1190,7 +1190,7 @@ __global__ void __launch_bounds__(32) invit_df_kernel(int n, const dfl* __restri
   for (int j = L; j < end; ++j)
     for (int r = 0; r < n; ++r) {
       const dfl z = ZC(r, j);
-      Zout[(size_t)r * n + j] = df_to_double(z);
+      Zout[(size_t)r * n + j] = df_to_double_fast(z);
     }
 #undef LU
 #undef ZC
@@ -1487,7 +1487,7 @@ __global__ void __launch_bounds__(256) gram_df_kernel(int n, int nref, const dou
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int j = tj * TL + jj + q;
-    if (i < kb && j < kb) Gall[(size_t)b * KB * KB + (size_t)i * KB + j] = df_to_double(df_norm(acc[q]));
+    if (i < kb && j < kb) Gall[(size_t)b * KB * KB + (size_t)i * KB + j] = df_to_double_fast(df_norm(acc[q]));
   }
 }
 
@@ -1531,7 +1531,7 @@ __global__ void __launch_bounds__(256) y_df_kernel(int n, int nref, const double
   if (l < m) {
     double* out = YT + (size_t)b * n * KB + (size_t)l * KB;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) out[jb + q] = (jb + q < kb) ? df_to_double(df_norm(acc[q])) : 0.0;
+    for (int q = 0; q < 32; ++q) out[jb + q] = (jb + q < kb) ? df_to_double_fast(df_norm(acc[q])) : 0.0;
   }
 }
 

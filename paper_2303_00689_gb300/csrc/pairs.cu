@@ -546,36 +546,37 @@ __device__ void pair_block(const double* dvec, const Elem& ea, const Elem& eb, T
     }
   }
 
-  // overlaps in the local frame (functions of R), then rotated
-  T Sl[4][4];
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b) Sl[a][b] = cst<T>(0.0);
-  Sl[0][0] = Radial<T>::promote(
+  // overlaps in the local frame (functions of R), then in the molecular frame.
+  // The local p_x', p_y' overlaps are equal (pi) and the frame (x', y', u) is
+  // orthonormal, so x'_a x'_b + y'_a y'_b = delta_ab - u_a u_b and
+  //   S_ss = s, S_s,pb = (s|sigma) u_b, S_pa,s = (sigma|s) u_a,
+  //   S_pa,pb = pi delta_ab + (sigma - pi) u_a u_b:
+  // the molecular-frame overlaps depend on u alone (no x', y').
+  const T zero = cst<T>(0.0);
+  for (int k = 0; k < 16; ++k) Sout[k] = zero;
+  Sout[0] = Radial<T>::promote(
       sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[0], ea.sto_nrm[0], 0, eb.nprin, eb.zeta[0], eb.sto_nrm[0], 0), uv);
-  if (ea.norb == 4)
-    Sl[3][0] = Radial<T>::promote(
+  if (ea.norb == 4) {
+    const T szs = Radial<T>::promote(
         sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[1], ea.sto_nrm[1], 1, eb.nprin, eb.zeta[0], eb.sto_nrm[0], 0), uv);
-  if (eb.norb == 4)
-    Sl[0][3] = Radial<T>::promote(
-        sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[0], ea.sto_nrm[0], 0, eb.nprin, eb.zeta[1], eb.sto_nrm[1], 1), uv);
-  if (ea.norb == 4 && eb.norb == 4) {
-    Sl[3][3] = Radial<T>::promote(
-        sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[1], ea.sto_nrm[1], 1, eb.nprin, eb.zeta[1], eb.sto_nrm[1], 1), uv);
-    T spp = Radial<T>::promote(
-        sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[1], ea.sto_nrm[1], 2, eb.nprin, eb.zeta[1], eb.sto_nrm[1], 2), uv);
-    Sl[1][1] = spp;
-    Sl[2][2] = spp;
+    for (int a = 1; a < 4; ++a) Sout[a * 4] = szs * u[a - 1];
   }
-  // only (s, s), (s, z), (z, s), (z, z), (x, x), (y, y) are nonzero in the local frame
-  const int nzA[6] = {0, 3, 0, 3, 1, 2}, nzB[6] = {0, 0, 3, 3, 1, 2};
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b) {
-      T acc = cst<T>(0.0);
-      if (a < ea.norb && b < eb.norb)
-#pragma unroll
-        for (int t = 0; t < 6; ++t) acc += Tf[a][nzA[t]] * Tf[b][nzB[t]] * Sl[nzA[t]][nzB[t]];
-      Sout[a * 4 + b] = acc;
+  if (eb.norb == 4) {
+    const T ssz = Radial<T>::promote(
+        sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[0], ea.sto_nrm[0], 0, eb.nprin, eb.zeta[1], eb.sto_nrm[1], 1), uv);
+    for (int b = 1; b < 4; ++b) Sout[b] = ssz * u[b - 1];
+  }
+  if (ea.norb == 4 && eb.norb == 4) {
+    const T szz = Radial<T>::promote(
+        sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[1], ea.sto_nrm[1], 1, eb.nprin, eb.zeta[1], eb.sto_nrm[1], 1), uv);
+    const T spp = Radial<T>::promote(
+        sto_overlap<Tr>(Rr, ea.nprin, ea.zeta[1], ea.sto_nrm[1], 2, eb.nprin, eb.zeta[1], eb.sto_nrm[1], 2), uv);
+    const T dsp = szz - spp;
+    for (int a = 1; a < 4; ++a) {
+      const T da = dsp * u[a - 1];
+      for (int b = 1; b < 4; ++b) Sout[a * 4 + b] = (a == b) ? da * u[b - 1] + spp : da * u[b - 1];
     }
+  }
 
   // core-core repulsion (a function of R)
   const Tr gss = local_integral<Tr>(0, 0, ea, eb, Rr);
