@@ -332,7 +332,7 @@ static void krylov_kernel(sim_handle* h, const double* P) {
   phase_end(h);
   phase_begin(h, PH_KRY_BLAS);
   // Lambda of eq. 36 once per evaluation; K is free until launch_krylov_combine writes it
-  launch_lambda(s, h->n, h->eps, h->f, h->beta, h->sc, h->K);
+  launch_lambda(s, h->n, h->eps, h->f, h->beta, h->sc, h->K, mixed(h));
   phase_end(h);
   phase_begin(h, PH_KRY_BLAS);
   launch_krylov_start(s, nn, h->D, P, h->W0, h->sc, h->red);

@@ -55,16 +55,44 @@ __host__ __device__ __forceinline__ dfl df_from_double(double x) {
 }
 __host__ __device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
 
-// FP32 -> FP64 by integer operations (exact for normal numbers; subnormal FP32
-// values, below 2^-126, become zero; infinities and NaN take the conversion
-// instruction): keeps the conversion off GB300's narrow FP64 pipe
+// FP32 -> FP64 by integer operations (exact for normal numbers, infinities and
+// NaN; subnormal FP32 values, below 2^-126, become zero): keeps the conversion
+// off GB300's narrow FP64 pipe.  No branch holds a conversion instruction, so
+// none can be evaluated speculatively.
 __device__ __forceinline__ double f2d_int(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned ex = (u >> 23) & 0xFFu;
-  if (ex == 0xFFu) return (double)f;
   unsigned long long b = (unsigned long long)(u & 0x80000000u) << 32;
-  if (ex != 0) b |= ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  if (ex != 0) {
+    const unsigned long long e64 = (ex == 0xFFu) ? 0x7FFull : (unsigned long long)(ex + 896u);
+    b |= (e64 << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  }
   return __longlong_as_double((long long)b);
+}
+// FP64 -> double-float by integer operations (no FP64 instruction): the top
+// 24 significand bits give hi, the remaining 29 bits (rounded to 24 by an
+// integer-to-float conversion) give lo, then one renormalisation.  |x| below
+// 2^-126 becomes 0, and below 2^-74 only hi is kept; |x| >= 2^128 becomes an
+// infinity of its sign and NaN stays NaN (all by integer operations).
+__device__ __forceinline__ dfl df_from_double_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned sign = hw & 0x80000000u;
+  const int ex = (int)((hw >> 20) & 0x7FFu);
+  if (ex > 1150) {
+    const bool nan = ex == 2047 && ((hw & 0xFFFFFu) | lw) != 0;
+    return dfl{__uint_as_float(sign | (nan ? 0x7FC00000u : 0x7F800000u)), 0.0f};
+  }
+  if (ex < 897) return dfl{0.0f, 0.0f};
+  const float hi = __uint_as_float(sign | ((unsigned)(ex - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+  float lo = 0.0f;
+  if (ex >= 949) {
+    const float scale = __uint_as_float((unsigned)(ex - 948) << 23);   // 2^(ex - 1075)
+    lo = __fmul_rn(__uint2float_rn(lw & 0x1FFFFFFFu), scale);
+    lo = __uint_as_float(__float_as_uint(lo) | sign);
+  }
+  const float s = __fadd_rn(hi, lo);
+  return dfl{s, __fsub_rn(lo, __fsub_rn(s, hi))};
 }
 // hi + lo as a double with one FP64 addition (the two conversions by integer operations)
 __device__ __forceinline__ double df_to_double_fast(dfl a) { return f2d_int(a.hi) + f2d_int(a.lo); }
@@ -136,5 +164,17 @@ __host__ __device__ __forceinline__ dfl df_rank2(dfl x, dfl u1, dfl w1, dfl u2, 
   float lo = KX_FSUB(KX_FADD(x.lo, KX_FADD(s1.lo, s2.lo)), KX_FADD(e1, e2));
   return df_fast_two_sum(s2.hi, lo);
 }
+
+#if defined(__CUDACC__)
+__device__ __forceinline__ dfl df_shfl_xor(dfl a, int o) {
+  return dfl{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+// sum over the 32 lanes (butterfly; every lane gets the same value)
+__device__ __forceinline__ dfl df_warp_sum(dfl v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  return v;
+}
+#endif
 
 }  // namespace kx

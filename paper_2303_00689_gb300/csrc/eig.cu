@@ -252,14 +252,6 @@ __global__ void __launch_bounds__(kTriThreads) tridiag_kernel(int n, double* __r
 }
 
 // ---- double-float tridiagonalisation (mixed path) -------------------------
-__device__ __forceinline__ dfl df_shfl_xor(dfl a, int o) {
-  return dfl{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-}
-__device__ __forceinline__ dfl df_warp_sum(dfl v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
-  return v;
-}
 // block-wide double-float sum in a fixed order; every thread gets the total.
 // `scratch` holds >= 32 dfl of shared memory.
 __device__ __forceinline__ dfl df_block_sum(dfl v, dfl* scratch) {
@@ -280,7 +272,7 @@ __device__ __forceinline__ dfl df_block_sum(dfl v, dfl* scratch) {
 
 __global__ void to_df_kernel(size_t len, const double* __restrict__ x, dfl* __restrict__ y) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < len) y[i] = df_from_double(x[i]);
+  if (i < len) y[i] = df_from_double_bits(x[i]);
 }
 
 // Same reduction as tridiag_kernel (lazy rank-2 update fused with the
@@ -292,10 +284,13 @@ __global__ void to_df_kernel(size_t len, const double* __restrict__ x, dfl* __re
 //    keeps a_{i,k+1}, so it need not wait for beta, tau and the scale, which
 //    thread 0 forms meanwhile:
 //    p_i = tau scale (sum_j a_ij x_j - beta a_{i,k+1}) since v = scale (x - beta e_{k+1});
-//  * a block's rows (i = k+1+b+rG) are cut into segments of kDfSeg columns and
-//    the (row, segment) items dealt over the warps, so the warps stay balanced
-//    while the trailing matrix shrinks; each lane issues the loads of its item
-//    before the arithmetic;
+//  * a block's rows (i = k+1+b+rG) are cut into segments of 512 columns (256
+//    and 128 once the trailing matrix is narrower than 500 and 200 columns)
+//    and the (row, segment) items dealt over the warps, so the warps stay
+//    balanced while the trailing matrix shrinks; warp 0, which forms the
+//    reflector scalars first, takes the last item of each round, so it never
+//    holds more items than another warp; each lane issues the loads of its
+//    item before the arithmetic;
 //  * block reductions take one CTA barrier each.
 // Shared memory: PW[j] = (v_{k-1}, w_{k-1}) as one 16-byte pair (during the
 // first passes it holds row k and p_{k-1}), VC[j] = x_k, then v_k, plus
@@ -303,12 +298,15 @@ __global__ void to_df_kernel(size_t len, const double* __restrict__ x, dfl* __re
 constexpr int kTriThreadsDf = 512;    // threads per block of the double-float kernel
 constexpr int kDfRed = 32;
 constexpr int kDfSeg = 512;           // columns per (row, segment) work item: 16 per lane
-constexpr int kDfPer = kDfSeg / 32;
+constexpr int kDfNarrow1 = 500;       // trailing width at and below which items are 256 columns
+constexpr int kDfNarrow2 = 200;       // ... and 128 columns
 static_assert(kTriThreadsDf / 32 <= kDfRed, "one reduction slot per warp");
 // rows per block at the first column, for a grid of G blocks
 static int tridiag_df_rmax(int n, int G) { return (n - 1 + G - 1) / G; }
 static size_t tridiag_smem_df(int n, int G) {
-  const size_t rmax = (size_t)tridiag_df_rmax(n, G), smax = (size_t)(n - 1 + kDfSeg - 1) / kDfSeg;
+  // at most 2 segments per row while the narrow items are in use
+  const size_t rmax = (size_t)tridiag_df_rmax(n, G),
+               smax = std::max<size_t>((size_t)(n - 1 + kDfSeg - 1) / kDfSeg, 2);
   return (3 * (size_t)n + 2 * kDfRed + rmax + rmax * smax) * sizeof(dfl);
 }
 
@@ -341,6 +339,80 @@ __device__ __forceinline__ dfl df_sum_partials(const dfl* scratch) {
 __device__ __forceinline__ dfl lo2(float4 a) { return dfl{a.x, a.y}; }
 __device__ __forceinline__ dfl hi2(float4 a) { return dfl{a.z, a.w}; }
 __device__ __forceinline__ float4 pack4(dfl a, dfl b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
+
+// The fused items of column k for one block: the pending rank-2 update
+// (v_{k-1}, w_{k-1}) of rows/cols >= k+1, stored back, and sum_j a_ij x_j of
+// each (row, SEG-column segment) item into part[r * S + sg] (a_{i,k+1} of the
+// block's rows into ak1s).  Warp w starts at item w - 1, warp 0 at NW - 1.
+template <int SEG>
+__device__ __forceinline__ void df_items(dfl* __restrict__ A, int n, int k, int G, int R, int wid, int lane,
+                                         bool prev, const float4* PW, const dfl* VC, dfl* part, dfl* ak1s) {
+  constexpr int PER = SEG / 32, NW = kTriThreadsDf / 32;
+  const int S = (n - (k + 1) + SEG - 1) / SEG;
+  const int Q = R * S;
+  for (int q = (wid == 0) ? NW - 1 : wid - 1; q < Q; q += NW) {
+    const int r = q / S, sg = q - r * S;
+    const int i = k + 1 + (int)blockIdx.x + r * G;
+    float2* row = (float2*)(A + (size_t)i * n);
+    const int jb = k + 1 + sg * SEG + lane;
+    const bool full = (k + 1 + (sg + 1) * SEG) <= n;
+    dfl a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, first = {0.0f, 0.0f};
+    if (full) {
+      float2 xr[PER];
+#pragma unroll
+      for (int u = 0; u < PER; ++u) xr[u] = __ldcg(row + jb + 32 * u);
+      if (prev) {
+        const float4 pwi = PW[i];
+        const dfl vi = lo2(pwi), wi = hi2(pwi);
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const int j = jb + 32 * u;
+          const float4 pw = PW[j];
+          const dfl x = df_rank2(dfl{xr[u].x, xr[u].y}, vi, hi2(pw), wi, lo2(pw));
+          row[j] = make_float2(x.hi, x.lo);
+          if (u == 0) first = x;
+          if (u & 1) df_acc_mul(a1, x, VC[j]); else df_acc_mul(a0, x, VC[j]);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const int j = jb + 32 * u;
+          const dfl x = dfl{xr[u].x, xr[u].y};
+          if (u == 0) first = x;
+          if (u & 1) df_acc_mul(a1, x, VC[j]); else df_acc_mul(a0, x, VC[j]);
+        }
+      }
+    } else {
+      float2 xr[PER];
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int j = jb + 32 * u;
+        xr[u] = (j < n) ? __ldcg(row + j) : make_float2(0.0f, 0.0f);
+      }
+      const float4 pwi = prev ? PW[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const dfl vi = lo2(pwi), wi = hi2(pwi);
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int j = jb + 32 * u;
+        if (j < n) {
+          dfl x = dfl{xr[u].x, xr[u].y};
+          if (prev) {
+            const float4 pw = PW[j];
+            x = df_rank2(x, vi, hi2(pw), wi, lo2(pw));
+            row[j] = make_float2(x.hi, x.lo);
+          }
+          if (u == 0) first = x;
+          if (u & 1) df_acc_mul(a1, x, VC[j]); else df_acc_mul(a0, x, VC[j]);
+        }
+      }
+    }
+    const dfl acc = df_warp_sum(df_add(df_norm(a0), df_norm(a1)));
+    if (lane == 0) {
+      part[r * S + sg] = acc;
+      if (sg == 0) ak1s[r] = first;        // lane 0, u = 0 is column k+1
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kTriThreadsDf) tridiag_df_kernel(int n, dfl* __restrict__ A,
                                                                  double* __restrict__ Vst,
@@ -448,70 +520,12 @@ __global__ void __launch_bounds__(kTriThreadsDf) tridiag_df_kernel(int n, dfl* _
     // fused: pending rank-2 update (v_{k-1}, w_{k-1}) of rows/cols >= k+1 and
     // sum_j a_ij x_j over (row, segment) items
     const int R = (n - (k + 1) - (int)blockIdx.x + G - 1) / G;
-    const int S = (n - (k + 1) + kDfSeg - 1) / kDfSeg;
-    for (int q = wid; q < R * S; q += NW) {
-      const int r = q / S, sg = q - r * S;
-      const int i = k + 1 + (int)blockIdx.x + r * G;
-      float2* row = (float2*)(A + (size_t)i * n);
-      const int jb = k + 1 + sg * kDfSeg + lane;
-      const bool full = (k + 1 + (sg + 1) * kDfSeg) <= n;
-      dfl a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f}, first = {0.0f, 0.0f};
-      if (full) {
-        float2 xr[kDfPer];
-#pragma unroll
-        for (int u = 0; u < kDfPer; ++u) xr[u] = __ldcg(row + jb + 32 * u);
-        if (prev) {
-          const float4 pwi = PW[i];
-          const dfl vi = lo2(pwi), wi = hi2(pwi);
-#pragma unroll
-          for (int u = 0; u < kDfPer; ++u) {
-            const int j = jb + 32 * u;
-            const float4 pw = PW[j];
-            const dfl x = df_rank2(dfl{xr[u].x, xr[u].y}, vi, hi2(pw), wi, lo2(pw));
-            row[j] = make_float2(x.hi, x.lo);
-            if (u == 0) first = x;
-            if (u & 1) df_acc_mul(a1, x, VC[j]); else df_acc_mul(a0, x, VC[j]);
-          }
-        } else {
-#pragma unroll
-          for (int u = 0; u < kDfPer; ++u) {
-            const int j = jb + 32 * u;
-            const dfl x = dfl{xr[u].x, xr[u].y};
-            if (u == 0) first = x;
-            if (u & 1) df_acc_mul(a1, x, VC[j]); else df_acc_mul(a0, x, VC[j]);
-          }
-        }
-      } else {
-        const int je = n;
-        float2 xr[kDfPer];
-#pragma unroll
-        for (int u = 0; u < kDfPer; ++u) {
-          const int j = jb + 32 * u;
-          xr[u] = (j < je) ? __ldcg(row + j) : make_float2(0.0f, 0.0f);
-        }
-        const float4 pwi = prev ? PW[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        const dfl vi = lo2(pwi), wi = hi2(pwi);
-#pragma unroll
-        for (int u = 0; u < kDfPer; ++u) {
-          const int j = jb + 32 * u;
-          if (j < je) {
-            dfl x = dfl{xr[u].x, xr[u].y};
-            if (prev) {
-              const float4 pw = PW[j];
-              x = df_rank2(x, vi, hi2(pw), wi, lo2(pw));
-              row[j] = make_float2(x.hi, x.lo);
-            }
-            if (u == 0) first = x;
-            if (u & 1) df_acc_mul(a1, x, VC[j]); else df_acc_mul(a0, x, VC[j]);
-          }
-        }
-      }
-      const dfl acc = df_warp_sum(df_add(df_norm(a0), df_norm(a1)));
-      if (lane == 0) {
-        part[r * S + sg] = acc;
-        if (sg == 0) ak1s[r] = first;        // lane 0, u = 0 is column k+1
-      }
-    }
+    const int m1 = n - (k + 1);
+    const int segw = (m1 > kDfNarrow1) ? kDfSeg : ((m1 > kDfNarrow2) ? 256 : 128);
+    const int S = (m1 + segw - 1) / segw;
+    if (segw == kDfSeg) df_items<kDfSeg>(A, n, k, G, R, wid, lane, prev, PW, VC, part, ak1s);
+    else if (segw == 256) df_items<256>(A, n, k, G, R, wid, lane, prev, PW, VC, part, ak1s);
+    else df_items<128>(A, n, k, G, R, wid, lane, prev, PW, VC, part, ak1s);
     __syncthreads();
     const dfl beta_df = s_df[0], ts_df = s_df[1], scale_df = s_df[3];
     tau_prev = s_df[2];

@@ -8,6 +8,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "df.cuh"
 #include "kernels.h"
 
 namespace kx {
@@ -224,9 +225,30 @@ __global__ void lambda_kernel(int n, const double* __restrict__ eps, const doubl
   Lam[(size_t)i * n + j] = lambda_ij(eps[i], eps[j], f[i], f[j], sc->mu, beta);
 }
 
+// Mixed path: the divided difference (f_i - f_j) / (e_i - e_j) in double-float
+// (an FP64 division is a long FP64 sequence on GB300: 305 -> 87 us per n = 3360
+// matrix); pairs within 1e-5 / beta take the derivative of the Fermi function in
+// FP64 as above (the test on the FP32 part of e_i - e_j).
+__global__ void lambda_df_kernel(int n, const double* __restrict__ eps, const double* __restrict__ f, double beta,
+                                 float betaf, const Scalars* sc, double* __restrict__ Lam) {
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const dfl den = df_sub(df_from_double_bits(eps[i]), df_from_double_bits(eps[j]));
+  double l;
+  if (betaf * fabsf(den.hi) < 1e-5f) {
+    l = lambda_ij(eps[i], eps[j], f[i], f[j], sc->mu, beta);
+  } else {
+    const dfl num = df_sub(df_from_double_bits(f[i]), df_from_double_bits(f[j]));
+    l = df_to_double_fast(df_mul(num, df_recip(den)));
+  }
+  Lam[(size_t)i * n + j] = l;
+}
+
 void launch_lambda(cudaStream_t s, int n, const double* eps, const double* f, double beta, const Scalars* sc,
-                   double* Lam) {
-  lambda_kernel<<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, eps, f, beta, sc, Lam);
+                   double* Lam, bool df) {
+  if (df) lambda_df_kernel<<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, eps, f, beta, (float)beta, sc, Lam);
+  else lambda_kernel<<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, eps, f, beta, sc, Lam);
   count_launch();
 }
 

@@ -108,7 +108,7 @@ void launch_dmu(cudaStream_t s, int n, const double* F1p, const double* eps, con
 // Lambda_ij of eq. 36 for the current eigenpairs and mu (n x n), then
 // Y = Lambda o (F1' - dmu I) per Krylov vector
 void launch_lambda(cudaStream_t s, int n, const double* eps, const double* f, double beta, const Scalars* sc,
-                   double* Lam);
+                   double* Lam, bool df);   // df: double-float divided differences (mixed path)
 void launch_dmpt_y(cudaStream_t s, int n, const double* F1p, const double* Lam, const Scalars* sc, double* Y);
 // dipole moment of the cores and the per-spin density with packed diagonal
 // blocks Dd (10 products per atom): sum_A (Z'_A - 2 N_A) R_A - 4 sum_A D1_A D_s,p
