@@ -47,7 +47,7 @@ DF_OPS_PER_FMA = 13.0
 # DRAM bytes (read + write) of one tridiag_df_kernel launch at n = 3360 from one
 # ncu capture of the bench's profile run (dram__bytes_read.sum 1.018e9 +
 # dram__bytes_write.sum 3.868e10; a one-pass metric set, kernel unchanged since)
-TRIDIAG_TRAFFIC = {"bytes": 1017753856 + 38678435584,
+TRIDIAG_TRAFFIC = {"bytes": 1102843648 + 39244797440,
                    "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one tridiag_df_kernel launch "
                              "of bench.py --profile-run at n = 3360"}
 
