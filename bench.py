@@ -201,7 +201,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
-    peaks = {"fp64_tflops": kx.sim_measure_peak(0, local), "fp32_tflops": kx.sim_measure_peak(1, local)}
+    peaks = {"fp64_tflops": kx.sim_measure_peak(0, local), "fp32_tflops": kx.sim_measure_peak(1, local),
+             "l2_rw_tbs": kx.sim_measure_peak(2, local)}
     mol, V, table = _inputs()
     N = mol.natoms
     prec = kx.SIM_PREC_FP64 if args.precision == "fp64" else kx.SIM_PREC_MIXED
@@ -273,7 +274,7 @@ def run_ours(args):
     # ---- dominant phase roofline -----------------------------------------------
     name, ph = max(phases.items(), key=lambda kv: kv[1]["ms"])
     per_launch_s = ph["ms"] / max(1, ph["launches"]) / 1e3
-    roof = _roofline(name, ph, per_launch_s, peaks, prec == kx.SIM_PREC_MIXED)
+    roof = _roofline(name, ph, per_launch_s, peaks, prec == kx.SIM_PREC_MIXED, int(X0.shape[0]))
 
     def stats(key):
         v = np.array([r[key] for r in recs], dtype=float)
@@ -333,8 +334,8 @@ def _dump_state(kx, h, N):
     return d
 
 
-def _roofline(name, ph, per_launch_s, peaks, mixed):
-    """Roofline entry of the dominant phase; peaks measured in this run."""
+def _roofline(name, ph, per_launch_s, peaks, mixed, n):
+    """Roofline entry of the dominant phase; peaks measured in this run (n: orbitals)."""
     meas = _peaks()
     work = ph["work"]
     if name == "eig_tridiag" and mixed:
@@ -350,7 +351,8 @@ def _roofline(name, ph, per_launch_s, peaks, mixed):
                                "FP32 instructions per double-float multiply-add",
                 "fp64_frac": achieved / peaks["fp64_tflops"],
                 "fp64_note": "the same algorithmic flops against the measured FP64 FMA rate "
-                             f"{peaks['fp64_tflops']:.2f} TFLOP/s"}
+                             f"{peaks['fp64_tflops']:.2f} TFLOP/s",
+                "l2": _tridiag_l2(n, per_launch_s, peaks)}
     if name in ("eig_tridiag", "eig_backtransform", "density_gemm"):
         achieved = work / per_launch_s / 1e12
         peak = peaks["fp64_tflops"]
@@ -365,6 +367,19 @@ def _roofline(name, ph, per_launch_s, peaks, mixed):
     peak = meas.get("hbm_gbs", 6792.1)
     return {"kernel_phase": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else 0.0, "traffic": None, "peak_source": "measured HBM copy"}
+
+
+def _tridiag_l2(n, per_launch_s, peaks):
+    """The work items' L2 traffic: every column reads and writes the trailing
+    (n-k-1) x (n-k-1) double-float matrix once (16 B per element), against the
+    L2 read + write rate measured with the kernel's launch shape."""
+    m = np.arange(2, n, dtype=np.float64)
+    bytes_ = 16.0 * float(np.sum(m * m))
+    achieved = bytes_ / per_launch_s / 1e12
+    peak = peaks["l2_rw_tbs"]
+    return {"bytes_per_launch": bytes_, "achieved": achieved, "peak": peak, "unit": "TB/s", "frac": achieved / peak,
+            "peak_source": "sim_measure_peak kind 2: 90 MB L2-resident buffer read and written back, one block "
+                           "of 512 threads per SM"}
 
 
 def _fp64_context(kx, mol, V, table, X0, steps=2):

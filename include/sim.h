@@ -434,11 +434,14 @@ int sim_debug_tc_gemm(int n, const double* A, const double* B, int terms, int sy
  * sim_debug_tc_gemm. */
 int sim_debug_tc_gemm_grouped(int n, const double* A, const double* B, int slices, int sym, double* C);
 
-/* sim_measure_peak -- FMA throughput of `device` in TFLOP/s (2 flops per FMA),
- * kind 0: FP64, kind 1: FP32; 8 independent chains per thread on 8 blocks of
- * 256 threads per SM, timed with CUDA events after a warm-up launch.  The
- * denominators of the arithmetic-bound roofline fractions (no counterpart in
- * the paper).  Allocates 16 bytes; synchronous. */
+/* sim_measure_peak -- kind 0: FP64, kind 1: FP32 FMA throughput of `device`
+ * in TFLOP/s (2 flops per FMA; 8 independent chains per thread on 8 blocks of
+ * 256 threads per SM; allocates 16 bytes); kind 2: L2 read + write rate in
+ * TB/s of a 90 MB L2-resident buffer read and written back 20 times by one
+ * block of 512 threads per SM (the double-float tridiagonalisation's launch
+ * shape; allocates 90 MB).  Timed with CUDA events after a warm-up launch.
+ * The denominators of the roofline fractions (no counterpart in the paper).
+ * Other kinds: SIM_EINVAL.  Synchronous. */
 int sim_measure_peak(int device, int kind, double* tflops);
 
 /* Failure-path test hooks (no counterpart in the paper).

@@ -458,7 +458,7 @@ class Server:
 
 
 def sim_measure_peak(kind, device=0):
-    """FMA throughput in TFLOP/s: kind 0 FP64, kind 1 FP32."""
+    """kind 0 / 1: FP64 / FP32 FMA throughput in TFLOP/s; kind 2: L2 read + write TB/s."""
     out = C.c_double(0.0)
     _check(lib().sim_measure_peak(int(device), int(kind), C.byref(out)))
     return out.value
